@@ -1,0 +1,105 @@
+"""Point-based agglomeration by a deterministic R-tree bisection.
+
+Section 3 (Definition of an R-tree of order (m, M)) and Section 4 (point-based
+agglomeration: an R-tree whose leaves are the fine support points; each
+point is owned by exactly one box).  The paper builds its tree by R*-tree
+insertion (Boost.Geometry) with M = 2m and skips the leaf level (Section 6).
+Insertion heuristics are not reproducible between two codes, so this
+reading replaces them by a bulk-loaded, balanced bisection tree that keeps
+what the method needs: nested axis-aligned boxes, a fan-out of 2^d between
+consecutive agglomerated levels (so H/h doubles per level, as in the
+structured-mesh tables), and unique ownership of every point.
+
+Rule (identical in the CUDA library's host code):
+  D = smallest t >= 0 with ceil(n / 2^t) <= leaf_size.
+  Every node above depth D is split in two:
+    1. MBR of the node's points (exact min / max);
+    2. axis a = argmax_a (max_a - min_a), ties to the smallest a;
+    3. order the node's points by the key
+       (x_a, x_{(a+1) mod d}, ..., x_{(a+d-1) mod d}, original index);
+    4. left child = first ceil(|S|/2) points, right child = the rest.
+  Level l (l = 1 .. L-1) agglomerates are the nodes at depth D - d (l-1),
+  numbered left to right.  Level 0 is the fine level.
+The permutation lists the points in final tree order (leaves left to right,
+inside a leaf in the order of its parent's split key).
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Partition:
+    n: int
+    dim: int
+    depth: int                   # D
+    levels: int                  # L (fine level included)
+    perm: np.ndarray             # perm[k] = original index of the k-th point in tree order
+    box_offsets: list            # box_offsets[l] (l >= 1): start of each level-l box in tree order (nbox_l + 1)
+    box_of_point: list           # box_of_point[l][i] for original i (l >= 1)
+    mbr_lo: list                 # mbr_lo[l] (nbox_l, d)
+    mbr_hi: list
+
+    def nboxes(self, level: int) -> int:
+        return len(self.box_offsets[level]) - 1
+
+
+class DepthError(ValueError):
+    pass
+
+
+def tree_depth(n: int, leaf_size: int) -> int:
+    t = 0
+    while -(-n // (1 << t)) > leaf_size:
+        t += 1
+    return t
+
+
+def _split_key_order(x: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """Order of the points idx (original indices) by the split rule's key."""
+    pts = x[idx]
+    d = x.shape[1]
+    ext = pts.max(axis=0) - pts.min(axis=0)
+    a = int(np.argmax(ext))          # first maximum: ties go to the smallest axis
+    keys = [idx] + [pts[:, (a + k) % d] for k in reversed(range(d))]
+    # np.lexsort sorts by the LAST key first: primary x_a, then x_{a+1}, ..., then original index
+    return idx[np.lexsort(keys)]
+
+
+def rtree_partition(coords: np.ndarray, leaf_size: int, levels: int) -> Partition:
+    x = np.ascontiguousarray(coords, dtype=np.float64)
+    n, d = x.shape
+    if levels < 2:
+        raise ValueError("need at least two levels (fine + coarsest)")
+    if leaf_size < 1 or n < 1:
+        raise ValueError("empty problem or leaf_size < 1")
+    D = tree_depth(n, leaf_size)
+    if D - d * (levels - 2) < 0:
+        raise DepthError(f"tree depth {D} too shallow for {levels} levels in {d}D")
+    # nodes at the current depth: list of index arrays, left to right
+    nodes = [np.arange(n, dtype=np.int64)]
+    for _ in range(D):
+        nxt = []
+        for idx in nodes:
+            order = _split_key_order(x, idx)
+            h = -(-len(order) // 2)
+            nxt.append(order[:h])
+            nxt.append(order[h:])
+        nodes = nxt
+    perm = np.concatenate(nodes) if nodes else np.zeros(0, np.int64)
+    leaf_sizes = np.array([len(v) for v in nodes], np.int64)
+    leaf_off = np.concatenate(([0], np.cumsum(leaf_sizes)))
+    box_offsets, box_of_point, lo, hi = [None], [None], [None], [None]
+    for lev in range(1, levels):
+        stride = 1 << (d * (lev - 1))
+        off = leaf_off[::stride]
+        nb = len(off) - 1
+        bop = np.empty(n, np.int64)
+        blo = np.empty((nb, d)); bhi = np.empty((nb, d))
+        for B in range(nb):
+            members = perm[off[B]:off[B + 1]]
+            bop[members] = B
+            blo[B] = x[members].min(axis=0)
+            bhi[B] = x[members].max(axis=0)
+        box_offsets.append(off); box_of_point.append(bop); lo.append(blo); hi.append(bhi)
+    return Partition(n, d, D, levels, perm, box_offsets, box_of_point, lo, hi)

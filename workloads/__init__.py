@@ -1,0 +1,139 @@
+"""Seeded synthetic finite-element workloads (inputs only).
+
+Builds the Poisson systems the R-tree multilevel solver is applied to: the
+model problem of Section 2 (eqs. (poisson), (weakform), (discweakform)),
+continuous Q_p Lagrange elements on a structured, optionally perturbed
+[0,1]^d mesh, Dirichlet nodes eliminated.  This module holds none of the
+multilevel method's arithmetic; the CPU oracle and the GPU library both
+consume what it returns, and neither is imported here.
+
+The C assembler (``fem.c``) is compiled on first use into ``_build/`` next
+to this file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libfem.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile fem.c into _build/libfem.so (gcc, OpenMP, no fast-math)."""
+    src = os.path.join(_HERE, "fem.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(_SO), exist_ok=True)
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+                               "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.fem_sizes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, i64p]
+        lib.fem_sizes.restype = ctypes.c_int
+        lib.fem_assemble.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 6
+        lib.fem_assemble.restype = ctypes.c_int
+        lib.fem_l2_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.c_void_p]
+        lib.fem_l2_error.restype = ctypes.c_double
+        lib.fem_gll01.argtypes = [ctypes.c_int, ctypes.c_void_p]
+        lib.fem_gll01.restype = None
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Problem:
+    """A free-DoF system A u = b with support-point coordinates."""
+    dim: int
+    N: int
+    p: int
+    perturb: float
+    seed: int
+    coords: np.ndarray      # (n, dim) float64, C-contiguous
+    rowptr: np.ndarray      # (n+1,) int64
+    colidx: np.ndarray      # (nnz,) int32, ascending within a row
+    vals: np.ndarray        # (nnz,) float64, bitwise symmetric
+    b: np.ndarray           # (n,) float64 load vector
+    u_exact: np.ndarray     # (n,) float64 nodal values of the manufactured solution (zeros if f = 1)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.rowptr.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.shape[0])
+
+    def scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.vals, self.colidx, self.rowptr), shape=(self.n, self.n))
+
+
+def sizes(dim: int, N: int, p: int) -> tuple[int, int]:
+    lib = _load()
+    n = ctypes.c_int64(); nnz = ctypes.c_int64()
+    if lib.fem_sizes(dim, N, p, ctypes.byref(n), ctypes.byref(nnz)) != 0:
+        raise ValueError("bad mesh parameters")
+    return int(n.value), int(nnz.value)
+
+
+def poisson(dim: int, N: int, p: int, perturb: float = 0.0, seed: int = 0, kappa_modes: int = 0,
+            rhs: str = "sine") -> Problem:
+    """Assemble -div(kappa grad u) = f on [0,1]^dim, Q_p on an N^dim mesh.
+
+    perturb: interior vertices move by U(-perturb*h, perturb*h) in each component (h = 1/N).
+    kappa_modes: number of seeded random Fourier modes of g = log kappa (unit variance); 0 -> kappa = 1.
+    rhs: "sine" (manufactured u = prod sin(pi x_a)) or "one" (f = 1).
+    """
+    lib = _load()
+    n, nnz = sizes(dim, N, p)
+    coords = np.empty((n, dim), np.float64)
+    rowptr = np.empty(n + 1, np.int64)
+    colidx = np.empty(nnz, np.int32)
+    vals = np.empty(nnz, np.float64)
+    b = np.empty(n, np.float64)
+    uex = np.empty(n, np.float64)
+    kind = {"sine": 0, "one": 1}[rhs]
+    rc = lib.fem_assemble(dim, N, p, float(perturb), int(seed) & (2**64 - 1), int(kappa_modes), kind,
+                          coords.ctypes.data, rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data,
+                          b.ctypes.data, uex.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"fem_assemble failed ({rc})")
+    return Problem(dim, N, p, perturb, seed, coords, rowptr, colidx, vals, b, uex,
+                   meta={"kappa_modes": kappa_modes, "rhs": rhs})
+
+
+def l2_error(prob: Problem, u: np.ndarray) -> float:
+    """L2 error of the FE function with free coefficients u against prod sin(pi x_a)."""
+    lib = _load()
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return float(lib.fem_l2_error(prob.dim, prob.N, prob.p, float(prob.perturb), int(prob.seed) & (2**64 - 1),
+                                  u.ctypes.data))
+
+
+def gll01(p: int) -> np.ndarray:
+    """GLL nodes on [0,1] used for the fine support points."""
+    x = np.empty(p + 1, np.float64)
+    _load().fem_gll01(p, x.ctypes.data)
+    return x
+
+
+def gaussian(n: int, seed: int, count: int = 1) -> np.ndarray:
+    """Seeded standard-normal vectors (n,) or (count, n), float64."""
+    g = np.random.default_rng(seed).standard_normal((count, n))
+    return g[0] if count == 1 else g
