@@ -1,0 +1,184 @@
+/*
+ * r3mg.h — C ABI of the B300 (sm_103a) R-tree algebraic-geometric multilevel
+ * preconditioned conjugate-gradient solver.
+ *
+ * Method: R3MG-C ("a high-order algebraic-geometric multilevel preconditioner
+ * for continuous finite element discretizations").  Support points are
+ * partitioned by an R-tree into axis-aligned boxes (Section 3; Section 4,
+ * point-based agglomeration); on each box the tensor space Q^{p'} is
+ * interpolated at the points the box owns, giving a sparse prolongation P
+ * (Section 4; Section 5, eq. (localinterpolation)); the level operators are
+ * inherited, A_{l+1} = P^T A_l P (Section 1, Section 4); one V-cycle with a
+ * Chebyshev-Jacobi smoother (Section 5, Remark on the smoother; Section 6)
+ * preconditions CG (Section 4, Section 6).  The coarsest level is solved by
+ * a dense Cholesky factorisation (the paper uses a sparse direct solver).
+ *
+ * Conventions for every entry point
+ *   - Status codes only; nothing throws or exits across this boundary.  On
+ *     failure r3mg_last_error() describes the cause.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the current device.  Inputs are borrowed for the call
+ *     only (copied or reformatted); outputs go to caller buffers.
+ *   - Vectors use the caller's numbering of the free DoFs; the tree order
+ *     used internally is never exposed except by r3mg_partition.
+ *   - All device work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream).  Calls that return host values synchronise it.
+ *   - A hierarchy owns all its device memory until r3mg_destroy.  A
+ *     hierarchy is not thread-safe: calls on one hierarchy must not overlap.
+ */
+#ifndef R3MG_H
+#define R3MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct r3mg_hierarchy r3mg_hierarchy;
+
+typedef enum {
+  R3MG_OK = 0,
+  R3MG_E_ARG = 1,          /* invalid argument, malformed CSR, non-finite input */
+  R3MG_E_CUDA = 2,         /* a CUDA runtime call failed */
+  R3MG_E_OOM = 3,          /* device or host allocation failed */
+  R3MG_E_DEPTH = 4,        /* bisection tree too shallow for the requested levels */
+  R3MG_E_UNISOLVENT = 5,   /* a box's points cannot carry Q^{p'} (Section 4, Remark on (m, M)) */
+  R3MG_E_NOT_SPD = 6,      /* non-positive diagonal or Cholesky pivot */
+  R3MG_E_NOCONV = 7,       /* PCG reached maxit */
+  R3MG_E_BREAKDOWN = 8,    /* p^T A p <= 0 or non-finite CG scalar */
+  R3MG_E_LIMIT = 9,        /* an internal size limit was exceeded (e.g. window > 65535 points) */
+  R3MG_E_TIMEOUT = 10      /* a bounded device wait expired */
+} r3mg_status;
+
+typedef struct {
+  int leaf_size;        /* maximum fine points per level-1 box; must be >= (pprime+1)^dim */
+  int pprime;           /* coarse polynomial degree p' >= 0 (0 = Nicolaides space, Section 1) */
+  int levels;           /* L >= 2 levels counting the fine level (the paper's "lvls") */
+  int cheb_degree;      /* Chebyshev degree k >= 1 (Section 6: 3) */
+  int sweeps;           /* pre- and post-smoothing sweeps (Section 6: 2) */
+  int lanczos_steps;    /* Lanczos steps for lambda_max(D^-1 A_l) (Section 6) */
+  double eig_safety;    /* upper interval end = eig_safety * Ritz estimate (1.1) */
+  double eig_ratio;     /* lower interval end = upper / eig_ratio (30) */
+  int precision;        /* 0: FP64 V-cycle inside FP64 PCG; 1: FP32 V-cycle inside FP64 flexible CG */
+  int group_lanes;      /* lanes per matrix row in the level kernels (4, 8, 16, 32); 0 = automatic */
+  uint64_t seed;        /* splitmix64 seed of the Lanczos start vectors (level l uses seed + l) */
+} r3mg_params;
+
+/* Fill `p` with the defaults: leaf 64, p' 1, 3 levels, degree 3, 2 sweeps,
+ * 10 Lanczos steps, 1.1, 30, FP64, automatic lanes, seed 0x5EED. */
+void r3mg_default_params(r3mg_params* p);
+
+/*
+ * Host-only R-tree bisection of n points (Section 3, Definition of the
+ * R-tree; Section 4, point-based agglomeration), read as a balanced,
+ * bulk-loaded bisection tree: depth D = smallest t with ceil(n/2^t) <=
+ * leaf_size; every node is split at ceil(|S|/2) after ordering its points by
+ * (x_a, x_{a+1}, ..., original index), a = axis of the longest MBR extent
+ * (ties to the smaller axis).  Needs no GPU.
+ *   coords_host: n*dim doubles, row-major (point i at coords[i*dim .. i*dim+dim-1]).
+ *   perm_out (host, n): perm_out[k] = caller index of the k-th point in tree order.
+ *   leaf_offsets_out (host, 2^D + 1 entries, may be NULL): start of each leaf in tree order.
+ *   depth_out (may be NULL): D.
+ * Errors: R3MG_E_ARG (n < 1, dim not 2/3, leaf < 2, non-finite coordinate),
+ *         R3MG_E_DEPTH (D - dim*(levels-2) < 0).
+ */
+r3mg_status r3mg_partition(int64_t n, int dim, const double* coords_host, int leaf_size, int levels,
+                           int64_t* perm_out, int64_t* leaf_offsets_out, int* depth_out);
+
+/*
+ * Build the hierarchy for the free-DoF system A (CSR, host memory) whose
+ * support points are coords_host (n x dim, host).  Performs the partition
+ * and the symbolic analysis on the host, then on the device: the P values
+ * (box Q^{p'} basis at owned points, Section 4), the Galerkin products
+ * A_{l+1} = P^T A_l P (Sections 1, 4), Lanczos estimates of
+ * lambda_max(D_l^{-1} A_l) (Section 6) and the coarsest Cholesky factor.
+ *   rowptr_host (n+1, int64), colidx_host (nnz, int32, 0-based), vals_host (nnz):
+ *     a symmetric matrix with a positive diagonal stored in every row;
+ *     column order inside a row is free.
+ *   params: see r3mg_params; NULL = defaults.
+ *   out: receives the hierarchy (NULL on failure).
+ * Errors: R3MG_E_ARG, R3MG_E_DEPTH, R3MG_E_UNISOLVENT, R3MG_E_NOT_SPD,
+ *         R3MG_E_LIMIT, R3MG_E_OOM, R3MG_E_CUDA.  The stream is synchronised.
+ */
+r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_host,
+                       const int32_t* colidx_host, const double* vals_host, const r3mg_params* params,
+                       void* stream, r3mg_hierarchy** out);
+
+/*
+ * Replace the matrix values (same pattern as at setup, CSR order, device
+ * memory, nnz doubles) and redo every numeric setup step: P is unchanged,
+ * the Galerkin levels, smoother intervals and coarsest factor are rebuilt.
+ * Errors: R3MG_E_NOT_SPD, R3MG_E_CUDA.  The stream is synchronised.
+ */
+r3mg_status r3mg_update_values(r3mg_hierarchy* h, const double* vals_dev, void* stream);
+
+/*
+ * z = M^{-1} r: one V-cycle (Section 4) applied to r (device, n doubles,
+ * caller numbering); z (device, n doubles) may not alias r.  Uses the
+ * precision chosen at setup (an FP32 V-cycle converts r to FP32 and z back).
+ * Asynchronous: no host synchronisation.
+ */
+r3mg_status r3mg_vcycle(r3mg_hierarchy* h, const double* r_dev, double* z_dev, void* stream);
+
+/*
+ * Solve A x = b with CG preconditioned by one V-cycle per iteration
+ * (Section 4, Section 6).  FP64 V-cycle: Hestenes-Stiefel PCG.  FP32 V-cycle:
+ * flexible CG (Notay) with FP64 vectors, dot products and scalars.
+ * Stops when ||b - A x||_2 <= rtol ||b||_2 (the recursive residual, confirmed
+ * by an FP64 recomputation of the true residual before returning success).
+ *   b_dev (device, n), x_dev (device, n): in = initial guess, out = solution.
+ *   iters_out: completed updates of x; relres_out: final ||r||/||b||.
+ * Errors: R3MG_E_NOCONV (maxit reached; x holds the last iterate),
+ *         R3MG_E_BREAKDOWN, R3MG_E_CUDA.  Synchronises the stream.
+ */
+r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit,
+                     int* iters_out, double* relres_out, void* stream);
+
+/* As r3mg_pcg with b_host / x_host in host memory: the host->device copy of b
+ * and x0 and the device->host copy of x happen inside the call. */
+r3mg_status r3mg_pcg_host(r3mg_hierarchy* h, const double* b_host, double* x_host, double rtol, int maxit,
+                          int* iters_out, double* relres_out, void* stream);
+
+/*
+ * y = A_l x on level l, FP64, in level numbering (level 0: caller numbering
+ * of the free DoFs; level l >= 1: coarse DoF box*b + q, boxes numbered left
+ * to right in the tree).  x_dev, y_dev: device, n_l doubles.  Asynchronous.
+ */
+r3mg_status r3mg_level_apply(r3mg_hierarchy* h, int level, const double* x_dev, double* y_dev, void* stream);
+
+/* Level sizes: n_out[l] rows, nnz_out[l] stored values (padding excluded),
+ * nbox_out[l] boxes (level 0: number of level-1 boxes), lam_out[l] upper
+ * Chebyshev interval end (0 on the coarsest level).  Arrays hold `levels`
+ * entries; any may be NULL. */
+r3mg_status r3mg_info(const r3mg_hierarchy* h, int* levels_out, int* depth_out, int64_t* n_out, int64_t* nnz_out,
+                      int64_t* nbox_out, double* lam_out);
+
+/* box_of_point_host (n, host): level-l box of every fine point, caller numbering, 1 <= l < L. */
+r3mg_status r3mg_get_agglomerates(const r3mg_hierarchy* h, int level, int64_t* box_of_point_host);
+
+/* Block adjacency of A_l (l >= 1; level 1 derives from A's structure):
+ * nbr_ptr_host (nbox_l + 1), nbr_host (nbr_ptr[nbox_l]) sorted per box.
+ * Call once with nbr_host = NULL to read nbr_ptr only. */
+r3mg_status r3mg_get_level_pattern(const r3mg_hierarchy* h, int level, int64_t* nbr_ptr_host, int64_t* nbr_host);
+
+/* Values of A_l (l >= 1), FP64, host: for box B, neighbour slot s (as in
+ * r3mg_get_level_pattern), the b x b block at
+ * vals_host[(nbr_ptr[B] + s) * b * b + q' * b + q] = A_l[(B,q'), (nbr_s, q)]. Synchronises. */
+r3mg_status r3mg_get_level_blocks(r3mg_hierarchy* h, int level, double* vals_host);
+
+/* P values: level 0: p_host (n x b, caller numbering) row i = phi_{box(i),q}(x_i);
+ * level l >= 1: p_host (nbox_l x b x b), block c = P~[(c,q'), (parent(c), q)]. Synchronises. */
+r3mg_status r3mg_get_prolongation(r3mg_hierarchy* h, int level, double* p_host);
+
+/* Message of the last failure on h (or of the last failed r3mg_setup /
+ * r3mg_partition in this thread when h is NULL).  Never NULL. */
+const char* r3mg_last_error(const r3mg_hierarchy* h);
+
+/* Free all device and host memory of h (NULL is a no-op). */
+void r3mg_destroy(r3mg_hierarchy* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

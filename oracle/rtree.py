@@ -71,8 +71,9 @@ def rtree_partition(coords: np.ndarray, leaf_size: int, levels: int) -> Partitio
     n, d = x.shape
     if levels < 2:
         raise ValueError("need at least two levels (fine + coarsest)")
-    if leaf_size < 1 or n < 1:
-        raise ValueError("empty problem or leaf_size < 1")
+    if leaf_size < 2 or n < 1:
+        # leaf_size 1 would allow empty leaves (n < 2^D); every box must own a point
+        raise ValueError("empty problem or leaf_size < 2")
     D = tree_depth(n, leaf_size)
     if D - d * (levels - 2) < 0:
         raise DepthError(f"tree depth {D} too shallow for {levels} levels in {d}D")

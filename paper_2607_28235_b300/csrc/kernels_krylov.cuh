@@ -1,0 +1,163 @@
+// Krylov vector kernels: permutation to and from tree order, the CG / flexible-CG updates
+// (FP64 vectors and scalars), V-cycle entry/exit conversions, deterministic reductions.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace r3mg {
+
+enum Scal : int {
+  S_PQ = 0, S_RR, S_RZ, S_RZNEW, S_ZQ, S_PR, S_ALPHA, S_BETA, S_BB, S_TMP, S_COUNT = 16
+};
+enum Fin : int { FIN_NONE = 0, FIN_ALPHA_PCG, FIN_ALPHA_FCG, FIN_BETA_PCG, FIN_BETA_FCG };
+
+constexpr int kVecBlocks = 148 * 4;   // grid of the vector kernels (4 CTAs per SM)
+constexpr int kVecThreads = 256;
+
+template <typename S, typename D>
+__global__ void k_gather_perm(const S* __restrict__ src, const int64_t* __restrict__ perm, D* __restrict__ dst, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = (D)src[perm[k]];
+}
+
+template <typename S, typename D>
+__global__ void k_scatter_perm(const S* __restrict__ src, const int64_t* __restrict__ perm, D* __restrict__ dst, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[k]] = (D)src[k];
+}
+
+__device__ __forceinline__ void store_partial(double v, double* part) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+    part[blockIdx.x] = s;
+  }
+}
+
+// r = b - y, partial ||r||^2, and (optionally) ||b||^2 into part2.
+__global__ void k_residual(const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r,
+                           int64_t n, double* part, double* part2) {
+  double s = 0.0, s2 = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[k] - y[k];
+    r[k] = v;
+    s += v * v;
+    s2 += b[k] * b[k];
+  }
+  store_partial(s, part);
+  if (part2) { __syncthreads(); store_partial(s2, part2); }
+}
+
+// V-cycle entry on level 0: vr = r, vx = 0, vd = c0 dinv r (first Chebyshev update).
+template <typename T>
+__device__ __forceinline__ void vc_init_row(int64_t k, double rk, T* vr, T* vx, T* vd, const T* dinv, T c0) {
+  const T rt = (T)rk;
+  vr[k] = rt;
+  vx[k] = T(0);
+  vd[k] = c0 * dinv[k] * rt;
+}
+
+template <typename T>
+__global__ void k_vc_init(const double* __restrict__ r, int64_t n, T* vr, T* vx, T* vd, const T* __restrict__ dinv, T c0) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    vc_init_row(k, r[k], vr, vx, vd, dinv, c0);
+}
+
+// x += alpha p; r -= alpha q; partial ||r||^2; V-cycle entry from the new r.
+template <typename T>
+__global__ void k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                            const double* __restrict__ q, const double* __restrict__ scal, int64_t n, double* part,
+                            T* vr, T* vx, T* vd, const T* __restrict__ dinv, T c0) {
+  const double alpha = scal[S_ALPHA];
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    x[k] += alpha * p[k];
+    const double rk = r[k] - alpha * q[k];
+    r[k] = rk;
+    s += rk * rk;
+    vc_init_row(k, rk, vr, vx, vd, dinv, c0);
+  }
+  store_partial(s, part);
+}
+
+// z = vx + vd (final Chebyshev update of level 0); partial z . w.
+template <typename T>
+__global__ void k_vc_final_dot(const T* __restrict__ vx, const T* __restrict__ vd, double* __restrict__ z,
+                               const double* __restrict__ w, int64_t n, double* part) {
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double zk = (double)vx[k] + (double)vd[k];
+    z[k] = zk;
+    if (w) s += zk * w[k];
+  }
+  if (part) store_partial(s, part);
+}
+
+// PCG: p = z + beta p.  FCG: p = z - beta p and partial p . r (next alpha's numerator).
+__global__ void k_p_update(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ r,
+                           const double* __restrict__ scal, int64_t n, int fcg, double* part) {
+  const double beta = scal[S_BETA];
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double pk = fcg ? z[k] - beta * p[k] : z[k] + beta * p[k];
+    p[k] = pk;
+    s += pk * r[k];
+  }
+  if (part) store_partial(s, part);
+}
+
+// Deterministic single-CTA sum of `m` partials into scal[slot], then the scalar finish step.
+__global__ void k_reduce(const double* __restrict__ part, int m, double* scal, int slot, int fin, int* status) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) s += part[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    scal[slot] = t;
+    if (fin == FIN_ALPHA_PCG || fin == FIN_ALPHA_FCG) {
+      const double num = (fin == FIN_ALPHA_PCG) ? scal[S_RZ] : scal[S_PR];
+      if (!(t > 0.0) || !isfinite(num)) { if (status) atomicExch(status, 1); scal[S_ALPHA] = 0.0; }
+      else scal[S_ALPHA] = num / t;
+    } else if (fin == FIN_BETA_PCG) {
+      scal[S_BETA] = t / scal[S_RZ];
+      scal[S_RZ] = t;
+    } else if (fin == FIN_BETA_FCG) {
+      scal[S_BETA] = t / scal[S_PQ];
+    }
+  }
+}
+
+// y = dinv * x (Jacobi) for the Lanczos estimate; partial x . y.
+__global__ void k_jacobi_dot(const double* __restrict__ dinv, const double* __restrict__ x, double* __restrict__ y,
+                             int64_t n, double* part) {
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = dinv[k] * x[k];
+    y[k] = v;
+    s += v * x[k];
+  }
+  store_partial(s, part);
+}
+
+// y = x + a * y
+__global__ void k_xpay(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = x[k] + a * y[k];
+}
+
+// y += a * x
+__global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] += a * x[k];
+}
+
+}  // namespace r3mg

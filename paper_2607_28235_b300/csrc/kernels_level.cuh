@@ -1,0 +1,197 @@
+// Level operator kernels: windowed sparse / block-dense row products with fused epilogues.
+//
+// One CTA handles one box at a time (grid-stride over boxes).  The box's window -- the
+// concatenation of the input vector over its neighbour boxes (fine level: the points of the
+// level-1 neighbour boxes; coarse level l: the b coefficients of each neighbour box) -- is
+// staged once in shared memory, so the matrix stream carries 16-bit window indices on the
+// fine level and no index at all on coarse levels (dense b x b blocks stored row by row).
+// Rows of the box are spread over groups of G lanes; each lane loads 4 consecutive entries
+// per step with 16-byte vector loads; the G partial sums are combined by warp shuffles and
+// the group leader applies the epilogue (plain product, Chebyshev-Jacobi step, residual...).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace r3mg {
+
+template <typename T>
+struct LevelView {
+  int64_t nrows = 0, nbox = 0;
+  int b = 0;                          // coarse block size; 0 on the fine level
+  const int64_t* box_row = nullptr;   // fine: nbox+1 row offsets of the boxes
+  const int64_t* nbr_ptr = nullptr;   // nbox+1
+  const int64_t* nbr = nullptr;       // neighbour boxes
+  const int32_t* win_off = nullptr;   // fine: per (box, slot) window offset
+  const int64_t* slot_src = nullptr;  // fine: per (box, slot) first row of the neighbour box
+  const int32_t* win_size = nullptr;  // fine: per box window length
+  const int64_t* row_ptr = nullptr;   // nrows+1 entry offsets, multiples of 4
+  const uint16_t* idx = nullptr;      // fine: window index per entry
+  const T* vals = nullptr;
+  const T* dinv = nullptr;
+  int max_slots = 0;                  // largest neighbour count (shared-memory slot cache)
+  int win_max = 0;                    // largest window (padded to 4)
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
+    float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  static __device__ __forceinline__ void load(const double* p, double (&v)[4]) {
+    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    double2 c = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
+  }
+};
+
+__device__ __forceinline__ void load_idx4(const uint16_t* p, int (&i)[4]) {
+  uint2 a = __ldcs(reinterpret_cast<const uint2*>(p));
+  i[0] = a.x & 0xffff; i[1] = a.x >> 16; i[2] = a.y & 0xffff; i[3] = a.y >> 16;
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.  blockDim % 32 == 0.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  return s;
+}
+
+// ---------------------------------------------------------------- epilogues
+// Each gets (row, y = (A x)_row) from the group leader; `acc` is a per-thread partial sum
+// folded into one value per CTA written to `part[blockIdx.x]` when the epilogue wants it.
+
+template <typename T>
+struct EpApply {            // y_out = A x
+  T* y;
+  static constexpr bool kDot = false;
+  __device__ void operator()(int64_t r, T y_r, double&) const { y[r] = y_r; }
+};
+
+template <typename T>
+struct EpApplyDot {         // y_out = A x, partial += w . (A x)  (CG: p^T A p)
+  T* y; const T* w;
+  static constexpr bool kDot = true;
+  __device__ void operator()(int64_t r, T y_r, double& acc) const { y[r] = y_r; acc += (double)w[r] * (double)y_r; }
+};
+
+// One Chebyshev-Jacobi step (Saad, Algorithm 12.1, D^{-1}-preconditioned), with the input
+// window being the current update d:  x += d;  r -= A d;  d' = a d + c D^{-1} r.
+template <typename T>
+struct EpCheb {
+  T* x; T* r; const T* d; T* dnext; const T* dinv; T a, c;
+  static constexpr bool kDot = false;
+  __device__ void operator()(int64_t i, T y_r, double&) const {
+    const T di = d[i];
+    x[i] += di;
+    const T rn = r[i] - y_r;
+    r[i] = rn;
+    dnext[i] = a * di + c * dinv[i] * rn;
+  }
+};
+
+template <typename T, int G, bool FINE, class Ep>
+__global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __restrict__ xin, Ep ep,
+                                                    double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* win = reinterpret_cast<T*>(smem_raw);
+  int32_t* s_woff = reinterpret_cast<int32_t*>(smem_raw + sizeof(T) * L.win_max);
+  int64_t* s_src = reinterpret_cast<int64_t*>(smem_raw + sizeof(T) * L.win_max +
+                                              sizeof(int32_t) * ((L.max_slots + 1 + 1) & ~1));
+  __shared__ double red[8];
+  constexpr int NG = 256 / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x % G;
+  double acc = 0.0;
+  for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
+    const int64_t e0 = L.nbr_ptr[B];
+    const int nn = (int)(L.nbr_ptr[B + 1] - e0);
+    int W;
+    int64_t r0, r1;
+    if constexpr (FINE) {
+      for (int s = threadIdx.x; s < nn; s += blockDim.x) {
+        s_woff[s] = L.win_off[e0 + s];
+        s_src[s] = L.slot_src[e0 + s];
+      }
+      W = L.win_size[B];
+      if (threadIdx.x == 0) s_woff[nn] = W;
+      r0 = L.box_row[B];
+      r1 = L.box_row[B + 1];
+      __syncthreads();
+      for (int k = threadIdx.x; k < W; k += blockDim.x) {
+        int lo = 0, hi = nn;  // slot s with s_woff[s] <= k < s_woff[s+1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_woff[mid] <= k) lo = mid; else hi = mid;
+        }
+        win[k] = xin[s_src[lo] + (k - s_woff[lo])];
+      }
+    } else {
+      const int b = L.b;
+      W = nn * b;
+      r0 = B * b;
+      r1 = r0 + b;
+      for (int k = threadIdx.x; k < W; k += blockDim.x) {
+        const int s = k / b;
+        win[k] = xin[L.nbr[e0 + s] * b + (k - s * b)];
+      }
+    }
+    const int Wp = (W + 3) & ~3;
+    for (int k = W + threadIdx.x; k < Wp; k += blockDim.x) win[k] = T(0);
+    __syncthreads();
+    // warp-uniform trip count: every lane of a warp runs the same iterations so the
+    // group shuffles always see the full warp; rows past the box end are masked.
+    const int g_first = (threadIdx.x >> 5) * (32 / G);
+    for (int64_t base = r0; base + g_first < r1; base += NG) {
+      const int64_t row = base + g;
+      const bool ok = row < r1;
+      int64_t k0 = 0, k1 = 0;
+      if (ok) { k0 = L.row_ptr[row]; k1 = L.row_ptr[row + 1]; }
+      T s = T(0);
+      for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G) {
+        T v[4];
+        Vec4<T>::load(L.vals + k, v);
+        if constexpr (FINE) {
+          int ii[4];
+          load_idx4(L.idx + k, ii);
+          s += v[0] * win[ii[0]] + v[1] * win[ii[1]] + v[2] * win[ii[2]] + v[3] * win[ii[3]];
+        } else {
+          const int t = (int)(k - k0);
+          s += v[0] * win[t] + v[1] * win[t + 1] + v[2] * win[t + 2] + v[3] * win[t + 3];
+        }
+      }
+      s = group_sum<G>(s);
+      if (ok && lane == 0) ep(row, s, acc);
+    }
+    __syncthreads();
+  }
+  if constexpr (Ep::kDot) {
+    const double t = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+  }
+}
+
+template <typename T>
+inline size_t level_smem_bytes(const LevelView<T>& L) {
+  return sizeof(T) * (size_t)L.win_max + sizeof(int32_t) * (size_t)((L.max_slots + 1 + 1) & ~1) +
+         sizeof(int64_t) * (size_t)(L.max_slots + 1);
+}
+
+}  // namespace r3mg

@@ -1,0 +1,105 @@
+// V-cycle transfer kernels (Section 4): restriction b_{l+1} = P^T r_l fused with the
+// initialisation of the next level's smoother, prolongation d_l = P (x_{l+1} + d_{l+1}),
+// and the coarsest-level solve with the explicit inverse of the Cholesky-factored A_{L-1}.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace r3mg {
+
+// Next-level initialisation after restriction: r = b, x = 0, d = c0 * dinv * b (first
+// Chebyshev update of the zero initial guess).  On the coarsest level only r = b is written.
+template <typename T>
+struct NextInit {
+  T* r; T* x; T* d; const T* dinv; T c0;
+  __device__ void operator()(int64_t i, T bi) const {
+    r[i] = bi;
+    if (x) { x[i] = T(0); d[i] = c0 * dinv[i] * bi; }
+  }
+};
+
+// Fine -> level 1: b1[B*b + q] = sum_{i in B} P0[i][q] r[i].  One CTA per box.
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_fine(const T* __restrict__ P0, const T* __restrict__ r,
+                                                       const int64_t* __restrict__ box_row, int64_t nbox, int b,
+                                                       NextInit<T> nx) {
+  __shared__ T part[256];
+  const int per = blockDim.x / b;   // row lanes per coefficient (b <= 256)
+  const int q = threadIdx.x % b, j = threadIdx.x / b;
+  for (int64_t B = blockIdx.x; B < nbox; B += gridDim.x) {
+    T s = T(0);
+    if (j < per)
+      for (int64_t i = box_row[B] + j; i < box_row[B + 1]; i += per) s += P0[i * b + q] * r[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < b) {
+      T t = T(0);
+      for (int k = 0; k < per; ++k) t += part[k * b + threadIdx.x];
+      nx(B * b + threadIdx.x, t);
+    }
+    __syncthreads();
+  }
+}
+
+// Level l -> l+1 (l >= 1): b_{l+1}[B][q] = sum_{children c} sum_{q'} Pt[c][q'][q] r_l[c][q'].
+template <typename T>
+__global__ void k_restrict_coarse(const T* __restrict__ Pt, const T* __restrict__ r, int64_t nparent, int b, int fan,
+                                  NextInit<T> nx) {
+  const int64_t tot = nparent * b;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t B = t / b;
+    const int q = (int)(t - B * b);
+    T s = T(0);
+    for (int64_t c = B * fan; c < (B + 1) * fan; ++c)
+      for (int qp = 0; qp < b; ++qp) s += Pt[(c * b + qp) * b + q] * r[c * b + qp];
+    nx(t, s);
+  }
+}
+
+// Level 1 -> fine: d0[k] = sum_q P0[k][q] (x1 + d1)[box(k)*b + q]   (d1 may be null).
+template <typename T>
+__global__ void k_prolong_fine(const T* __restrict__ P0, const int32_t* __restrict__ box_of, const T* __restrict__ x1,
+                               const T* __restrict__ d1, int64_t n, int b, T* __restrict__ d0) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t B = box_of[k];
+    T s = T(0);
+    for (int q = 0; q < b; ++q) {
+      const T e = x1[B * b + q] + (d1 ? d1[B * b + q] : T(0));
+      s += P0[k * b + q] * e;
+    }
+    d0[k] = s;
+  }
+}
+
+// Level l+1 -> l: d_l[c][q'] = sum_q Pt[c][q'][q] (x + d)_{l+1}[parent(c)][q].
+template <typename T>
+__global__ void k_prolong_coarse(const T* __restrict__ Pt, const T* __restrict__ x1, const T* __restrict__ d1,
+                                 int64_t nchild, int b, int fan, T* __restrict__ d0) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nchild * b; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / b;
+    const int qp = (int)(t - c * b);
+    const int64_t B = c / fan;
+    T s = T(0);
+    for (int q = 0; q < b; ++q) s += Pt[(c * b + qp) * b + q] * (x1[B * b + q] + (d1 ? d1[B * b + q] : T(0)));
+    d0[t] = s;
+  }
+}
+
+// Coarsest solve x = A_c^{-1} r with the symmetric inverse formed from the Cholesky factor.
+// One warp per row, 16-byte loads along the row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_gemv(const T* __restrict__ M, int64_t ld, const T* __restrict__ r,
+                                                    int64_t nc, T* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w; row < nc; row += nw) {
+    const T* a = M + row * ld;
+    T s = T(0);
+    for (int64_t k = lane; k < nc; k += 32) s += a[k] * r[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = s;
+  }
+}
+
+}  // namespace r3mg

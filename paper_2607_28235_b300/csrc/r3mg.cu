@@ -1,0 +1,965 @@
+// libr3mg: hierarchy setup, V-cycle, PCG / flexible CG and the C ABI (include/r3mg.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels_dense.cuh"
+#include "kernels_krylov.cuh"
+#include "kernels_level.cuh"
+#include "kernels_setup.cuh"
+#include "kernels_vcycle.cuh"
+
+using namespace r3mg;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+constexpr size_t kMaxSmem = 226 * 1024;   // opt-in shared memory per CTA on sm_103a, minus static use
+
+struct Level {
+  int64_t n = 0, nbox = 0;
+  int b = 0;  // 0 on the fine level
+  int64_t *box_row = nullptr, *nbr_ptr = nullptr, *nbr = nullptr, *slot_src = nullptr, *row_ptr = nullptr,
+          *pair_box = nullptr;
+  int32_t *win_off = nullptr, *win_size = nullptr;
+  uint16_t* idx = nullptr;
+  int max_slots = 0, win_max = 0;
+  int64_t stored = 0, nnz = 0, npairs = 0;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  double lam_lo = 0.0, lam_hi = 0.0;
+  std::vector<std::pair<double, double>> pre, post;  // Chebyshev step coefficients (a, c)
+  double c0 = 0.0;                                   // 1/theta: first update of a zero guess
+  void *x = nullptr, *r = nullptr, *d[2] = {nullptr, nullptr};
+  int G = 8;
+  HostPattern pat;
+};
+
+}  // namespace
+
+struct r3mg_hierarchy {
+  r3mg_params prm{};
+  int64_t n = 0;
+  int dim = 0, L = 0, b = 1, fan = 4;
+  HostPartition part;
+  std::vector<Level> lv;
+  int64_t nnz_csr = 0;
+  int64_t *src = nullptr, *diag_src = nullptr, *perm = nullptr;
+  int32_t* box_of_tree = nullptr;
+  double* coords_tree = nullptr;
+  std::vector<double*> P64;
+  std::vector<float*> P32;
+  int64_t nc = 0, ncp = 0;
+  double* Ainv64 = nullptr;
+  float* Ainv32 = nullptr;
+  double *hb_dev = nullptr, *hx_dev = nullptr;   // device copies for r3mg_pcg_host
+  double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *cb = nullptr;
+  double *part_a = nullptr, *part_b = nullptr, *scal = nullptr;
+  int64_t npart = 0;
+  int* status = nullptr;
+  double* host_scal = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_state = 0;  // 0 untried, 1 ready, -1 unavailable
+  std::vector<void*> allocs;
+  std::string err = "no error";
+};
+
+namespace {
+
+struct Fail {
+  r3mg_status st;
+  std::string msg;
+};
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      throw Fail{e_ == cudaErrorMemoryAllocation ? R3MG_E_OOM : R3MG_E_CUDA,                       \
+                 std::string(#call) + ": " + cudaGetErrorString(e_)};                              \
+  } while (0)
+
+template <typename T>
+T* dalloc(r3mg_hierarchy* h, int64_t count) {
+  void* p = nullptr;
+  if (count <= 0) count = 1;
+  CK(cudaMalloc(&p, sizeof(T) * (size_t)count));
+  h->allocs.push_back(p);
+  return (T*)p;
+}
+
+template <typename T>
+T* upload(r3mg_hierarchy* h, const std::vector<T>& v) {
+  T* p = dalloc<T>(h, (int64_t)v.size());
+  if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->stream));
+  return p;
+}
+
+inline int grid_for(int64_t work, int threads = 256, int cap = 148 * 32) {
+  int64_t g = (work + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
+template <typename T>
+LevelView<T> view(const Level& L) {
+  LevelView<T> v;
+  v.nrows = L.n; v.nbox = L.nbox; v.b = L.b;
+  v.box_row = L.box_row; v.nbr_ptr = L.nbr_ptr; v.nbr = L.nbr; v.win_off = L.win_off; v.slot_src = L.slot_src;
+  v.win_size = L.win_size; v.row_ptr = L.row_ptr; v.idx = L.idx;
+  if constexpr (sizeof(T) == 8) { v.vals = (const T*)L.v64; v.dinv = (const T*)L.dinv64; }
+  else { v.vals = (const T*)L.v32; v.dinv = (const T*)L.dinv32; }
+  v.max_slots = L.max_slots; v.win_max = L.win_max;
+  return v;
+}
+
+template <typename T, int G, bool FINE, class Ep>
+void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s) {
+  const size_t sm = level_smem_bytes(v);
+  auto kern = level_kernel<T, G, FINE, Ep>;
+  // opt in to more than 48 KB of dynamic shared memory per instantiation (the setup's warm-up
+  // V-cycle does this before any graph capture)
+  static size_t configured = 48 * 1024;
+  if (sm > configured) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = sm;
+  }
+  const int grid = (int)std::max<int64_t>(1, v.nbox);
+  kern<<<grid, 256, sm, s>>>(v, xin, ep, part);
+  CK(cudaGetLastError());
+}
+
+template <typename T, class Ep>
+void launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t s) {
+  const LevelView<T> v = view<T>(L);
+  const bool fine = (L.b == 0);
+  switch (L.G) {
+    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s) : launch_level_g<T, 4, false>(v, xin, ep, part, s); break;
+    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s) : launch_level_g<T, 8, false>(v, xin, ep, part, s); break;
+    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s) : launch_level_g<T, 16, false>(v, xin, ep, part, s); break;
+    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s) : launch_level_g<T, 32, false>(v, xin, ep, part, s); break;
+  }
+}
+
+void read_status(r3mg_hierarchy* h, int& st) {
+  CK(cudaMemcpyAsync(&h->host_scal[15], h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(&st, &h->host_scal[15], sizeof(int));
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+}
+
+double reduce_read(r3mg_hierarchy* h, const double* part, int m, int slot, int fin = FIN_NONE) {
+  k_reduce<<<1, 1024, 0, h->stream>>>(part, m, h->scal, slot, fin, h->status);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h->host_scal[slot], &h->scal[slot], sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return h->host_scal[slot];
+}
+
+void reduce_dev(r3mg_hierarchy* h, const double* part, int m, int slot, int fin) {
+  k_reduce<<<1, 1024, 0, h->stream>>>(part, m, h->scal, slot, fin, h->status);
+  CK(cudaGetLastError());
+}
+
+int auto_lanes(double avg_row) {
+  if (avg_row >= 512) return 32;
+  if (avg_row >= 160) return 16;
+  if (avg_row >= 48) return 8;
+  return 4;
+}
+
+// Chebyshev coefficient schedule (Saad, Algorithm 12.1) split into fused steps.  Every step
+// is  x += d;  r -= A d;  d = a d + c D^{-1} r.  A sweep boundary restarts the recurrence
+// (a = 0, c = 1/theta); the last pre-smoothing step only serves the residual.
+void make_schedule(Level& L, int k, int nu) {
+  const double theta = 0.5 * (L.lam_hi + L.lam_lo), delta = 0.5 * (L.lam_hi - L.lam_lo), sigma = theta / delta;
+  L.c0 = 1.0 / theta;
+  L.pre.clear(); L.post.clear();
+  auto sweep_inner = [&](std::vector<std::pair<double, double>>& out) {
+    double rho = 1.0 / sigma;
+    for (int i = 1; i < k; ++i) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      out.emplace_back(rn * rho, 2.0 * rn / delta);
+      rho = rn;
+    }
+  };
+  for (int j = 0; j < nu; ++j) {
+    sweep_inner(L.pre);
+    L.pre.emplace_back(0.0, 1.0 / theta);
+  }
+  L.post.emplace_back(0.0, 1.0 / theta);
+  for (int j = 0; j < nu; ++j) {
+    sweep_inner(L.post);
+    if (j + 1 < nu) L.post.emplace_back(0.0, 1.0 / theta);
+  }
+}
+
+// ---------------------------------------------------------------- V-cycle
+template <typename T>
+const T* Pmat(r3mg_hierarchy* h, int l) {
+  if constexpr (sizeof(T) == 8) return (const T*)h->P64[l]; else return (const T*)h->P32[l];
+}
+template <typename T>
+const T* Ainv(r3mg_hierarchy* h) {
+  if constexpr (sizeof(T) == 8) return (const T*)h->Ainv64; else return (const T*)h->Ainv32;
+}
+template <typename T>
+const T* Dinv(const Level& L) {
+  if constexpr (sizeof(T) == 8) return (const T*)L.dinv64; else return (const T*)L.dinv32;
+}
+
+// Runs the V-cycle on the level vectors.  On entry level 0 holds x = 0, r = b,
+// d[0] = D^{-1} b / theta.  Returns the d buffer of level 0 holding the last update:
+// the result is z = x_0 + d.
+template <typename T>
+T* vcycle_body(r3mg_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  const int L = h->L;
+  std::vector<int> cur(L, 0);
+  for (int l = 0; l < L - 1; ++l) {
+    Level& A = h->lv[l];
+    T* x = (T*)A.x; T* r = (T*)A.r;
+    for (auto& ac : A.pre) {
+      T* d = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      launch_level<T>(A, d, EpCheb<T>{x, r, d, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, s);
+      cur[l] ^= 1;
+    }
+    Level& C = h->lv[l + 1];
+    const bool coarsest = (l + 1 == L - 1);
+    NextInit<T> nx{(T*)C.r, coarsest ? nullptr : (T*)C.x, coarsest ? nullptr : (T*)C.d[0], Dinv<T>(C), (T)C.c0};
+    if (l == 0)
+      k_restrict_fine<T><<<(int)std::min<int64_t>(C.nbox, 148 * 64), 256, 0, s>>>(Pmat<T>(h, 0), r, A.box_row, C.nbox, h->b, nx);
+    else
+      k_restrict_coarse<T><<<grid_for(C.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), r, C.nbox, h->b, h->fan, nx);
+    CK(cudaGetLastError());
+  }
+  {
+    Level& C = h->lv[L - 1];
+    k_dense_gemv<T><<<grid_for(h->nc * 32), 256, 0, s>>>(Ainv<T>(h), h->ncp, (const T*)C.r, h->nc, (T*)C.x);
+    CK(cudaGetLastError());
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    Level& A = h->lv[l];
+    Level& C = h->lv[l + 1];
+    const bool coarsest = (l + 1 == L - 1);
+    const T* x1 = (const T*)C.x;
+    const T* d1 = coarsest ? nullptr : (const T*)C.d[cur[l + 1]];
+    T* d = (T*)A.d[cur[l]];
+    if (l == 0)
+      k_prolong_fine<T><<<grid_for(h->n), 256, 0, s>>>(Pmat<T>(h, 0), h->box_of_tree, x1, d1, h->n, h->b, d);
+    else
+      k_prolong_coarse<T><<<grid_for(A.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), x1, d1, A.nbox, h->b, h->fan, d);
+    CK(cudaGetLastError());
+    T* x = (T*)A.x; T* r = (T*)A.r;
+    for (auto& ac : A.post) {
+      T* dd = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      launch_level<T>(A, dd, EpCheb<T>{x, r, dd, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, s);
+      cur[l] ^= 1;
+    }
+  }
+  return (T*)h->lv[0].d[cur[0]];
+}
+
+template <typename T>
+T* run_vcycle(r3mg_hierarchy* h) {
+  // capture once into a CUDA graph; the buffers never move, so the graph is reusable
+  if (h->graph_state == 0) {
+    cudaGraph_t g = nullptr;
+    T* out = nullptr;
+    bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try { out = vcycle_body<T>(h); } catch (Fail&) { ok = false; }
+      if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess) ok = false;
+    }
+    if (ok && cudaGraphInstantiate(&h->graph, g, 0) == cudaSuccess) h->graph_state = 1;
+    else { h->graph_state = -1; cudaGetLastError(); }
+    if (g) cudaGraphDestroy(g);
+    (void)out;
+  }
+  if (h->graph_state == 1) {
+    CK(cudaGraphLaunch(h->graph, h->stream));
+    // the body is deterministic: recompute which buffer holds the result without launching
+    const int steps0 = (int)(h->lv[0].pre.size() + h->lv[0].post.size());
+    return (T*)h->lv[0].d[steps0 & 1];
+  }
+  return vcycle_body<T>(h);
+}
+
+template <typename T>
+void vcycle_apply(r3mg_hierarchy* h, const double* r_tree, double* z_tree, bool use_graph = true) {
+  Level& F = h->lv[0];
+  k_vc_init<T><<<grid_for(h->n), 256, 0, h->stream>>>(r_tree, h->n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), (T)F.c0);
+  CK(cudaGetLastError());
+  T* d = use_graph ? run_vcycle<T>(h) : vcycle_body<T>(h);
+  k_vc_final_dot<T><<<grid_for(h->n), 256, 0, h->stream>>>((const T*)F.x, d, z_tree, nullptr, h->n, nullptr);
+  CK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- setup
+void lanczos(r3mg_hierarchy* h, int l) {
+  Level& A = h->lv[l];
+  const int64_t n = A.n;
+  cudaStream_t s = h->stream;
+  double *r = h->cr, *z = h->cz, *p = h->cp, *q = h->cq;
+  const int gv = grid_for(n);
+  k_splitmix_vec<<<gv, 256, 0, s>>>(h->prm.seed + (uint64_t)l, l == 0 ? h->perm : nullptr, r, n);
+  k_jacobi_dot<<<gv, 256, 0, s>>>(A.dinv64, r, z, n, h->part_a);
+  CK(cudaGetLastError());
+  double rz = reduce_read(h, h->part_a, gv, S_TMP);
+  CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> al, be;
+  const int steps = (int)std::min<int64_t>(h->prm.lanczos_steps, n);
+  for (int j = 0; j < steps; ++j) {
+    launch_level<double>(A, p, EpApplyDot<double>{q, p}, h->part_a, s);
+    const double pq = reduce_read(h, h->part_a, (int)A.nbox, S_TMP);
+    const double alpha = rz / pq;
+    k_axpy<<<gv, 256, 0, s>>>(-alpha, q, r, n);
+    k_jacobi_dot<<<gv, 256, 0, s>>>(A.dinv64, r, z, n, h->part_a);
+    CK(cudaGetLastError());
+    const double rzn = reduce_read(h, h->part_a, gv, S_TMP);
+    al.push_back(alpha);
+    const double beta = rzn / rz;
+    be.push_back(beta);
+    if (rzn == 0.0) break;
+    k_xpay<<<gv, 256, 0, s>>>(z, beta, p, n);
+    CK(cudaGetLastError());
+    rz = rzn;
+  }
+  const int k = (int)al.size();
+  std::vector<double> dg(k), off(k > 0 ? k - 1 : 0);
+  for (int j = 0; j < k; ++j) {
+    dg[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < k) off[j] = std::sqrt(be[j]) / al[j];
+  }
+  const double lmax = tridiag_max_eig(dg, off);
+  if (!(lmax > 0.0) || !std::isfinite(lmax)) throw Fail{R3MG_E_NOT_SPD, "Lanczos estimate non-positive on level " + std::to_string(l)};
+  A.lam_hi = h->prm.eig_safety * lmax;
+  A.lam_lo = A.lam_hi / h->prm.eig_ratio;
+  make_schedule(A, h->prm.cheb_degree, h->prm.sweeps);
+}
+
+void dense_coarsest(r3mg_hierarchy* h) {
+  Level& C = h->lv[h->L - 1];
+  cudaStream_t s = h->stream;
+  const int64_t nc = h->nc, ncp = h->ncp;
+  const int nb = (int)(ncp / kTile);
+  double* D = dalloc<double>(h, ncp * ncp);
+  double* Li = dalloc<double>(h, ncp * ncp);
+  CK(cudaMemsetAsync(D, 0, sizeof(double) * ncp * ncp, s));
+  CK(cudaMemsetAsync(Li, 0, sizeof(double) * ncp * ncp, s));
+  std::vector<double> one(1, 1.0);
+  for (int64_t i = nc; i < ncp; ++i) CK(cudaMemcpyAsync(D + i * ncp + i, one.data(), sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  k_blocks_to_dense<<<(int)std::min<int64_t>(nc, 65535), 256, 0, s>>>(C.nbr_ptr, C.nbr, C.row_ptr, C.v64, C.nbox, h->b, D, ncp);
+  CK(cudaGetLastError());
+  for (int k = 0; k < nb; ++k) {
+    k_potrf_diag<<<1, 256, 0, s>>>(D, ncp, k, Li, h->status);
+    if (nb - k - 1 > 0) {
+      k_trsm_panel<<<nb - k - 1, 256, 0, s>>>(D, ncp, k, Li);
+      const int m = nb - k - 1;
+      k_syrk_update<<<m * (m + 1) / 2, 256, 0, s>>>(D, ncp, k, nb);
+    }
+    CK(cudaGetLastError());
+  }
+  int st = 0;
+  read_status(h, st);
+  if (st) throw Fail{R3MG_E_NOT_SPD, "coarsest level: Cholesky pivot <= 0 (A_c not SPD)"};
+  for (int t = 1; t < nb; ++t) {
+    k_trtri_step<<<nb - t, 256, 0, s>>>(D, Li, ncp, t, nb);
+    CK(cudaGetLastError());
+  }
+  if (!h->Ainv64) h->Ainv64 = dalloc<double>(h, ncp * ncp);
+  k_lauum<<<nb * (nb + 1) / 2, 256, 0, s>>>(Li, h->Ainv64, ncp, nb);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  CK(cudaFree(D)); CK(cudaFree(Li));
+  h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)D), h->allocs.end());
+  h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)Li), h->allocs.end());
+}
+
+// Numeric setup from CSR values on the device (setup and r3mg_update_values).
+void numeric(r3mg_hierarchy* h, const double* vals_dev) {
+  cudaStream_t s = h->stream;
+  Level& F = h->lv[0];
+  k_gather_vals<<<grid_for(F.stored), 256, 0, s>>>(h->src, vals_dev, F.v64, F.stored);
+  k_dinv_fine<<<grid_for(h->n), 256, 0, s>>>(h->diag_src, vals_dev, F.dinv64, h->n, h->status);
+  CK(cudaGetLastError());
+  int st = 0;
+  read_status(h, st);
+  if (st) throw Fail{R3MG_E_NOT_SPD, "fine level: non-positive or non-finite diagonal entry"};
+  const int b = h->b;
+  // Galerkin products, level by level
+  {
+    Level& C = h->lv[1];
+    const size_t sm = sizeof(double) * 2 * kRapRows * b;
+    k_rap_fine<<<(int)std::min<int64_t>(C.npairs, 1 << 30), 256, sm, s>>>(
+        F.pair_box, F.nbr_ptr, F.nbr, F.win_off, F.box_row, F.row_ptr, F.idx, F.v64, h->P64[0], b, F.npairs, C.row_ptr,
+        C.v64);
+    CK(cudaGetLastError());
+  }
+  for (int l = 1; l + 1 < h->L; ++l) {
+    Level& A = h->lv[l];
+    Level& C = h->lv[l + 1];
+    const size_t sm = sizeof(double) * 4 * b * b;
+    if (sm > 48 * 1024) CK(cudaFuncSetAttribute(k_rap_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_rap_coarse<<<(int)std::min<int64_t>(C.npairs, 1 << 30), 256, sm, s>>>(
+        C.pair_box, C.nbr_ptr, C.nbr, A.nbr_ptr, A.nbr, A.row_ptr, A.v64, h->P64[l], b, h->fan, C.npairs, C.row_ptr, C.v64);
+    CK(cudaGetLastError());
+  }
+  for (int l = 1; l < h->L; ++l) {
+    Level& A = h->lv[l];
+    k_dinv_coarse<<<grid_for(A.n), 256, 0, s>>>(A.nbr_ptr, A.nbr, A.row_ptr, A.v64, A.dinv64, A.nbox, b, h->status);
+    CK(cudaGetLastError());
+  }
+  read_status(h, st);
+  if (st) throw Fail{R3MG_E_NOT_SPD, "coarse level: non-positive diagonal entry"};
+  for (int l = 0; l + 1 < h->L; ++l) lanczos(h, l);
+  dense_coarsest(h);
+  if (h->prm.precision == 1) {
+    for (int l = 0; l < h->L; ++l) {
+      Level& A = h->lv[l];
+      if (l + 1 < h->L) {
+        k_convert<double, float><<<grid_for(A.stored), 256, 0, s>>>(A.v64, A.v32, A.stored);
+        k_convert<double, float><<<grid_for(A.n), 256, 0, s>>>(A.dinv64, A.dinv32, A.n);
+      }
+    }
+    k_convert<double, float><<<grid_for(h->ncp * h->ncp), 256, 0, s>>>(h->Ainv64, h->Ainv32, h->ncp * h->ncp);
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(s));
+}
+
+void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const int32_t* colidx, const double* vals) {
+  const r3mg_params& prm = h->prm;
+  const int dim = h->dim;
+  cudaStream_t s = h->stream;
+  h->b = 1;
+  for (int a = 0; a < dim; ++a) h->b *= (prm.pprime + 1);
+  h->fan = 1 << dim;
+  const int b = h->b;
+  Error err;
+  if (!validate_csr(h->n, rowptr, colidx, err)) throw Fail{err.status, err.msg};
+  for (int64_t k = 0; k < rowptr[h->n]; ++k)
+    if (!std::isfinite(vals[k])) throw Fail{R3MG_E_ARG, "CSR: non-finite value"};
+  if (!partition_points(h->n, dim, coords, prm.leaf_size, prm.levels, h->part, err)) throw Fail{err.status, err.msg};
+  HostPartition& P = h->part;
+  const int L = prm.levels;
+  h->L = L;
+  // admissibility (Section 4, Remark on (m, M)): enough points and non-degenerate boxes
+  for (int64_t B = 0; B < P.nbox(1); ++B) {
+    if (P.box_off[1][B + 1] - P.box_off[1][B] < b)
+      throw Fail{R3MG_E_UNISOLVENT, "level-1 box " + std::to_string(B) + " owns fewer points than (p'+1)^d"};
+  }
+  if (prm.pprime >= 1)
+    for (int l = 1; l < L; ++l)
+      for (int64_t B = 0; B < P.nbox(l); ++B)
+        for (int a = 0; a < dim; ++a)
+          if (!(P.hi[l][B * dim + a] > P.lo[l][B * dim + a]))
+            throw Fail{R3MG_E_UNISOLVENT, "level-" + std::to_string(l) + " box " + std::to_string(B) + " has zero extent"};
+  h->lv.assign(L, Level());
+  std::vector<HostPattern> pats(L);
+  fine_pattern(P, rowptr, colidx, pats[1]);
+  for (int l = 2; l < L; ++l) coarse_pattern(pats[l - 1], h->fan, P.nbox(l), pats[l]);
+  HostFineLayout lay;
+  if (!fine_layout(P, pats[1], rowptr, colidx, lay, err)) throw Fail{err.status, err.msg};
+  h->nnz_csr = rowptr[h->n];
+  // ---- fine level
+  {
+    Level& F = h->lv[0];
+    F.n = h->n; F.nbox = P.nbox(1); F.b = 0;
+    F.box_row = upload(h, P.box_off[1]);
+    F.nbr_ptr = upload(h, pats[1].ptr);
+    F.nbr = upload(h, pats[1].nbr);
+    F.win_off = upload(h, lay.win_off);
+    F.win_size = upload(h, lay.win_size);
+    std::vector<int64_t> ss(pats[1].nbr.size()), pb(pats[1].nbr.size());
+    int ms = 0;
+    for (int64_t B = 0; B < F.nbox; ++B) {
+      ms = std::max<int>(ms, (int)(pats[1].ptr[B + 1] - pats[1].ptr[B]));
+      for (int64_t e = pats[1].ptr[B]; e < pats[1].ptr[B + 1]; ++e) { ss[e] = P.box_off[1][pats[1].nbr[e]]; pb[e] = B; }
+    }
+    F.slot_src = upload(h, ss);
+    F.pair_box = upload(h, pb);
+    F.npairs = (int64_t)pb.size();
+    F.max_slots = ms;
+    F.win_max = (lay.win_max + 3) & ~3;
+    F.row_ptr = upload(h, lay.row_ptr);
+    F.idx = upload(h, lay.idx);
+    F.stored = lay.row_ptr[h->n];
+    F.nnz = lay.nnz;
+    F.v64 = dalloc<double>(h, F.stored);
+    F.dinv64 = dalloc<double>(h, F.n);
+    F.pat = pats[1];
+    F.G = prm.group_lanes ? prm.group_lanes : auto_lanes((double)F.nnz / (double)F.n);
+    h->src = upload(h, lay.src);
+    h->diag_src = upload(h, lay.diag_src);
+    h->perm = upload(h, P.perm);
+    std::vector<int32_t> bot(h->n);
+    for (int64_t B = 0; B < F.nbox; ++B)
+      for (int64_t k = P.box_off[1][B]; k < P.box_off[1][B + 1]; ++k) bot[k] = (int32_t)B;
+    h->box_of_tree = upload(h, bot);
+    std::vector<double> ct(h->n * dim);
+    for (int64_t k = 0; k < h->n; ++k)
+      for (int a = 0; a < dim; ++a) ct[k * dim + a] = coords[P.perm[k] * dim + a];
+    h->coords_tree = upload(h, ct);
+  }
+  // ---- coarse levels (block layout)
+  for (int l = 1; l < L; ++l) {
+    Level& C = h->lv[l];
+    const HostPattern& pt = pats[l];
+    C.nbox = P.nbox(l); C.b = b; C.n = C.nbox * b;
+    C.pat = pt;
+    C.nbr_ptr = upload(h, pt.ptr);
+    C.nbr = upload(h, pt.nbr);
+    std::vector<int64_t> rp(C.n + 1, 0), pb(pt.nbr.size());
+    int ms = 0;
+    for (int64_t B = 0; B < C.nbox; ++B) {
+      const int64_t nn = pt.ptr[B + 1] - pt.ptr[B];
+      ms = std::max<int>(ms, (int)nn);
+      const int64_t len = (nn * b + kPad - 1) / kPad * kPad;
+      for (int q = 0; q < b; ++q) rp[B * b + q + 1] = rp[B * b + q] + len;
+      for (int64_t e = pt.ptr[B]; e < pt.ptr[B + 1]; ++e) pb[e] = B;
+    }
+    C.row_ptr = upload(h, rp);
+    C.pair_box = upload(h, pb);
+    C.npairs = (int64_t)pb.size();
+    C.max_slots = ms;
+    C.win_max = (ms * b + 3) & ~3;
+    C.stored = rp[C.n];
+    C.nnz = (int64_t)pt.nbr.size() * b * b;
+    C.v64 = dalloc<double>(h, C.stored);
+    CK(cudaMemsetAsync(C.v64, 0, sizeof(double) * C.stored, s));
+    C.dinv64 = dalloc<double>(h, C.n);
+    C.G = prm.group_lanes ? prm.group_lanes : auto_lanes((double)C.nnz / (double)C.n);
+  }
+  // ---- transfers (geometry only: computed once)
+  GLLTable g{};
+  g.pp = prm.pprime;
+  gll_nodes01(prm.pprime, g.z);
+  h->P64.assign(L - 1, nullptr);
+  h->P32.assign(L - 1, nullptr);
+  {
+    std::vector<double> lo = P.lo[1], hi = P.hi[1];
+    double* dlo = upload(h, lo); double* dhi = upload(h, hi);
+    h->P64[0] = dalloc<double>(h, h->n * b);
+    k_p0_eval<<<grid_for(h->n * b), 256, 0, s>>>(h->coords_tree, h->box_of_tree, dlo, dhi, g, dim, b, h->P64[0], h->n);
+    CK(cudaGetLastError());
+    if (prm.pprime >= 1) {
+      k_unisolvent<<<(int)std::min<int64_t>(P.nbox(1), 148 * 16), 128, sizeof(double) * b * b, s>>>(
+          h->P64[0], h->lv[0].box_row, P.nbox(1), b, h->status);
+      CK(cudaGetLastError());
+      int st = 0;
+      read_status(h, st);
+      if (st) throw Fail{R3MG_E_UNISOLVENT, "a level-1 box's points cannot carry Q^{p'} (rank-deficient evaluation)"};
+    }
+  }
+  for (int l = 1; l + 1 < L; ++l) {
+    double* lc = upload(h, P.lo[l]); double* hc = upload(h, P.hi[l]);
+    double* lp = upload(h, P.lo[l + 1]); double* hp = upload(h, P.hi[l + 1]);
+    h->P64[l] = dalloc<double>(h, P.nbox(l) * b * b);
+    k_ptilde_eval<<<grid_for(P.nbox(l) * b * b), 256, 0, s>>>(lc, hc, lp, hp, g, dim, b, h->fan, h->P64[l], P.nbox(l));
+    CK(cudaGetLastError());
+  }
+  // ---- coarsest and Krylov work space
+  h->nc = h->lv[L - 1].n;
+  h->ncp = (h->nc + kTile - 1) / kTile * kTile;
+  int64_t np = kVecBlocks;
+  for (int l = 0; l < L; ++l) np = std::max(np, h->lv[l].nbox);
+  np = std::max<int64_t>(np, 148 * 32);
+  h->npart = np;
+  h->part_a = dalloc<double>(h, np);
+  h->part_b = dalloc<double>(h, np);
+  h->scal = dalloc<double>(h, S_COUNT);
+  CK(cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, s));
+  int64_t nmax = h->n;
+  for (int l = 1; l < L; ++l) nmax = std::max(nmax, h->lv[l].n);
+  h->cx = dalloc<double>(h, nmax); h->cr = dalloc<double>(h, nmax); h->cp = dalloc<double>(h, nmax);
+  h->cq = dalloc<double>(h, nmax); h->cz = dalloc<double>(h, nmax); h->cb = dalloc<double>(h, nmax);
+  // V-cycle vectors in the V-cycle precision
+  const size_t es = prm.precision == 1 ? sizeof(float) : sizeof(double);
+  for (int l = 0; l < L; ++l) {
+    Level& A = h->lv[l];
+    A.x = dalloc<char>(h, A.n * es);
+    A.r = dalloc<char>(h, A.n * es);
+    if (l + 1 < L) { A.d[0] = dalloc<char>(h, A.n * es); A.d[1] = dalloc<char>(h, A.n * es); }
+  }
+  if (prm.precision == 1) {
+    for (int l = 0; l < L; ++l) {
+      Level& A = h->lv[l];
+      if (l + 1 < L) { A.v32 = dalloc<float>(h, A.stored); A.dinv32 = dalloc<float>(h, A.n); }
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+      const int64_t m = (l == 0) ? h->n * b : P.nbox(l) * b * b;
+      h->P32[l] = dalloc<float>(h, m);
+      k_convert<double, float><<<grid_for(m), 256, 0, s>>>(h->P64[l], h->P32[l], m);
+    }
+    h->Ainv32 = dalloc<float>(h, h->ncp * h->ncp);
+    CK(cudaGetLastError());
+  }
+  // ---- shared-memory limits of the level kernels
+  for (int l = 0; l + 1 < L; ++l) {
+    const size_t es2 = prm.precision == 1 ? sizeof(float) : sizeof(double);
+    const Level& A = h->lv[l];
+    const size_t need = std::max(level_smem_bytes(view<double>(A)),
+                                 es2 * (size_t)A.win_max + 12 * (size_t)(A.max_slots + 2));
+    if (need > kMaxSmem)
+      throw Fail{R3MG_E_LIMIT, "level " + std::to_string(l) + " window needs " + std::to_string(need) +
+                                   " bytes of shared memory (> 227 KB): use a smaller leaf_size"};
+  }
+  // ---- numeric setup from the caller's values
+  double* dvals = dalloc<double>(h, h->nnz_csr);
+  CK(cudaMemcpyAsync(dvals, vals, sizeof(double) * h->nnz_csr, cudaMemcpyHostToDevice, s));
+  numeric(h, dvals);
+  CK(cudaFree(dvals));
+  h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)dvals), h->allocs.end());
+  // one direct V-cycle so every kernel instantiation is configured before graph capture
+  CK(cudaMemsetAsync(h->cb, 0, sizeof(double) * h->n, s));
+  if (prm.precision == 1) vcycle_apply<float>(h, h->cb, h->cz, false);
+  else vcycle_apply<double>(h, h->cb, h->cz, false);
+  CK(cudaStreamSynchronize(s));
+}
+
+template <typename F>
+r3mg_status guarded(r3mg_hierarchy* h, F&& f) {
+  try {
+    f();
+    return R3MG_OK;
+  } catch (Fail& e) {
+    if (h) h->err = e.msg;
+    g_last_error = e.msg;
+    return e.st;
+  } catch (std::bad_alloc&) {
+    if (h) h->err = "host allocation failed";
+    g_last_error = "host allocation failed";
+    return R3MG_E_OOM;
+  }
+}
+
+struct StreamJoin {  // run the hierarchy's work after the caller's stream, and vice versa
+  r3mg_hierarchy* h;
+  cudaStream_t user;
+  StreamJoin(r3mg_hierarchy* hh, void* st) : h(hh), user((cudaStream_t)st) {
+    CK(cudaEventRecord(h->ev_in, user));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+  }
+  ~StreamJoin() {
+    if (cudaEventRecord(h->ev_out, h->stream) == cudaSuccess) cudaStreamWaitEvent(user, h->ev_out, 0);
+  }
+};
+
+// PCG (FP64 V-cycle) or flexible CG (FP32 V-cycle) on tree-ordered b (cb) and x (cx).
+template <typename T>
+r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double* relres) {
+  cudaStream_t s = h->stream;
+  Level& F = h->lv[0];
+  const int64_t n = h->n;
+  const bool fcg = (h->prm.precision == 1);
+  const int gv = grid_for(n);
+  const int nb0 = (int)F.nbox;
+  auto true_residual = [&](double& rr, double* bb) {
+    launch_level<double>(F, h->cx, EpApply<double>{h->cq}, nullptr, s);
+    k_residual<<<gv, 256, 0, s>>>(h->cb, h->cq, h->cr, n, h->part_a, bb ? h->part_b : nullptr);
+    CK(cudaGetLastError());
+    rr = reduce_read(h, h->part_a, gv, S_RR);
+    if (bb) *bb = reduce_read(h, h->part_b, gv, S_BB);
+  };
+  auto precondition_restart = [&]() {
+    // z = M r; p = z; (PCG) rz = r.z ; (FCG) pr = p.r
+    k_vc_init<T><<<gv, 256, 0, s>>>(h->cr, n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), (T)F.c0);
+    CK(cudaGetLastError());
+    T* d = run_vcycle<T>(h);
+    k_vc_final_dot<T><<<gv, 256, 0, s>>>((const T*)F.x, d, h->cz, h->cr, n, h->part_a);
+    CK(cudaGetLastError());
+    reduce_dev(h, h->part_a, gv, fcg ? S_PR : S_RZ, FIN_NONE);
+    CK(cudaMemcpyAsync(h->cp, h->cz, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  };
+  double rr = 0.0, bb = 0.0;
+  true_residual(rr, &bb);
+  const double bnorm = std::sqrt(bb);
+  *iters = 0;
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(h->cx, 0, sizeof(double) * n, s));
+    *relres = 0.0;
+    return R3MG_OK;
+  }
+  double rel = std::sqrt(rr) / bnorm;
+  *relres = rel;
+  if (rel <= rtol) return R3MG_OK;
+  precondition_restart();
+  for (int it = 1; it <= maxit; ++it) {
+    launch_level<double>(F, h->cp, EpApplyDot<double>{h->cq, h->cp}, h->part_a, s);
+    reduce_dev(h, h->part_a, nb0, S_PQ, fcg ? FIN_ALPHA_FCG : FIN_ALPHA_PCG);
+    k_cg_update<T><<<gv, 256, 0, s>>>(h->cx, h->cr, h->cp, h->cq, h->scal, n, h->part_a, (T*)F.r, (T*)F.x,
+                                      (T*)F.d[0], Dinv<T>(F), (T)F.c0);
+    CK(cudaGetLastError());
+    k_reduce<<<1, 1024, 0, s>>>(h->part_a, gv, h->scal, S_RR, FIN_NONE, h->status);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&h->host_scal[S_RR], &h->scal[S_RR], sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&h->host_scal[15], h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rr = h->host_scal[S_RR];
+    int st = 0;
+    std::memcpy(&st, &h->host_scal[15], sizeof(int));
+    if (st) {
+      CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+      throw Fail{R3MG_E_BREAKDOWN, "CG breakdown: p^T A p <= 0 or non-finite scalar"};
+    }
+    *iters = it;
+    rel = std::sqrt(rr) / bnorm;
+    *relres = rel;
+    if (!std::isfinite(rel)) throw Fail{R3MG_E_BREAKDOWN, "CG breakdown: non-finite residual"};
+    if (rel <= rtol) {
+      double rt = 0.0;
+      true_residual(rt, nullptr);
+      *relres = std::sqrt(rt) / bnorm;
+      if (*relres <= rtol) return R3MG_OK;
+      precondition_restart();   // recursive residual drifted: restart from the true residual
+      continue;
+    }
+    T* d = run_vcycle<T>(h);
+    k_vc_final_dot<T><<<gv, 256, 0, s>>>((const T*)F.x, d, h->cz, fcg ? h->cq : h->cr, n, h->part_a);
+    CK(cudaGetLastError());
+    reduce_dev(h, h->part_a, gv, fcg ? S_ZQ : S_RZNEW, fcg ? FIN_BETA_FCG : FIN_BETA_PCG);
+    k_p_update<<<gv, 256, 0, s>>>(h->cp, h->cz, h->cr, h->scal, n, fcg ? 1 : 0, fcg ? h->part_a : nullptr);
+    CK(cudaGetLastError());
+    if (fcg) reduce_dev(h, h->part_a, gv, S_PR, FIN_NONE);
+  }
+  return R3MG_E_NOCONV;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+void r3mg_default_params(r3mg_params* p) {
+  if (!p) return;
+  p->leaf_size = 64; p->pprime = 1; p->levels = 3; p->cheb_degree = 3; p->sweeps = 2; p->lanczos_steps = 10;
+  p->eig_safety = 1.1; p->eig_ratio = 30.0; p->precision = 0; p->group_lanes = 0; p->seed = 0x5EED;
+}
+
+r3mg_status r3mg_partition(int64_t n, int dim, const double* coords_host, int leaf_size, int levels, int64_t* perm_out,
+                           int64_t* leaf_offsets_out, int* depth_out) {
+  if (!coords_host || !perm_out) { g_last_error = "partition: null pointer"; return R3MG_E_ARG; }
+  HostPartition P;
+  Error err;
+  try {
+    if (!partition_points(n, dim, coords_host, leaf_size, levels, P, err)) { g_last_error = err.msg; return err.status; }
+  } catch (std::bad_alloc&) { g_last_error = "host allocation failed"; return R3MG_E_OOM; }
+  std::memcpy(perm_out, P.perm.data(), sizeof(int64_t) * n);
+  if (leaf_offsets_out) std::memcpy(leaf_offsets_out, P.leaf_off.data(), sizeof(int64_t) * P.leaf_off.size());
+  if (depth_out) *depth_out = P.depth;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_host,
+                       const int32_t* colidx_host, const double* vals_host, const r3mg_params* params, void* stream,
+                       r3mg_hierarchy** out) {
+  if (!out) { g_last_error = "setup: null output"; return R3MG_E_ARG; }
+  *out = nullptr;
+  if (!coords_host || !rowptr_host || !colidx_host || !vals_host || n < 1 || (dim != 2 && dim != 3)) {
+    g_last_error = "setup: null pointer, n < 1 or dim not in {2,3}";
+    return R3MG_E_ARG;
+  }
+  r3mg_hierarchy* h = new (std::nothrow) r3mg_hierarchy();
+  if (!h) return R3MG_E_OOM;
+  if (params) h->prm = *params; else r3mg_default_params(&h->prm);
+  const r3mg_params& p = h->prm;
+  int b = 1;
+  for (int a = 0; a < dim; ++a) b *= (p.pprime + 1);
+  if (p.pprime < 0 || p.pprime > 8 || b > 64 || p.leaf_size < b || p.levels < 2 || p.cheb_degree < 1 || p.sweeps < 1 ||
+      p.lanczos_steps < 1 || !(p.eig_safety > 0) || !(p.eig_ratio > 1) || (p.precision != 0 && p.precision != 1) ||
+      (p.group_lanes != 0 && p.group_lanes != 4 && p.group_lanes != 8 && p.group_lanes != 16 && p.group_lanes != 32)) {
+    g_last_error = "setup: invalid parameters (need 0 <= p' <= 8, (p'+1)^d <= 64, leaf >= (p'+1)^d, levels >= 2, "
+                   "degree >= 1, sweeps >= 1, lanes in {0,4,8,16,32}, precision in {0,1})";
+    delete h;
+    return R3MG_E_ARG;
+  }
+  h->n = n; h->dim = dim;
+  r3mg_status st = guarded(h, [&] {
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CK(cudaMallocHost(&h->host_scal, sizeof(double) * 16));
+    h->status = dalloc<int>(h, 1);
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    StreamJoin j(h, stream);
+    build(h, coords_host, rowptr_host, colidx_host, vals_host);
+    CK(cudaStreamSynchronize(h->stream));
+  });
+  if (st != R3MG_OK) {
+    g_last_error = h->err;
+    r3mg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_update_values(r3mg_hierarchy* h, const double* vals_dev, void* stream) {
+  if (!h || !vals_dev) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    numeric(h, vals_dev);
+  });
+}
+
+r3mg_status r3mg_vcycle(r3mg_hierarchy* h, const double* r_dev, double* z_dev, void* stream) {
+  if (!h || !r_dev || !z_dev) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    const int gv = grid_for(h->n);
+    k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(r_dev, h->perm, h->cb, h->n);
+    CK(cudaGetLastError());
+    if (h->prm.precision == 1) vcycle_apply<float>(h, h->cb, h->cz);
+    else vcycle_apply<double>(h, h->cb, h->cz);
+    k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cz, h->perm, z_dev, h->n);
+    CK(cudaGetLastError());
+  });
+}
+
+r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_out,
+                     double* relres_out, void* stream) {
+  if (!h || !b_dev || !x_dev || maxit < 0 || !(rtol >= 0.0)) return R3MG_E_ARG;
+  int it = 0;
+  double rel = 0.0;
+  r3mg_status res = R3MG_OK;
+  r3mg_status st = guarded(h, [&] {
+    StreamJoin j(h, stream);
+    const int gv = grid_for(h->n);
+    k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(b_dev, h->perm, h->cb, h->n);
+    k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(x_dev, h->perm, h->cx, h->n);
+    CK(cudaGetLastError());
+    res = (h->prm.precision == 1) ? krylov<float>(h, rtol, maxit, &it, &rel) : krylov<double>(h, rtol, maxit, &it, &rel);
+    k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cx, h->perm, x_dev, h->n);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+  });
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = rel;
+  if (st != R3MG_OK) return st;
+  if (res == R3MG_E_NOCONV) h->err = "PCG: maximum iterations reached";
+  return res;
+}
+
+r3mg_status r3mg_pcg_host(r3mg_hierarchy* h, const double* b_host, double* x_host, double rtol, int maxit,
+                          int* iters_out, double* relres_out, void* stream) {
+  if (!h || !b_host || !x_host) return R3MG_E_ARG;
+  r3mg_status st = guarded(h, [&] {
+    if (!h->hb_dev) { h->hb_dev = dalloc<double>(h, h->n); h->hx_dev = dalloc<double>(h, h->n); }
+    cudaStream_t us = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(h->hb_dev, b_host, sizeof(double) * h->n, cudaMemcpyHostToDevice, us));
+    CK(cudaMemcpyAsync(h->hx_dev, x_host, sizeof(double) * h->n, cudaMemcpyHostToDevice, us));
+  });
+  if (st != R3MG_OK) return st;
+  r3mg_status res = r3mg_pcg(h, h->hb_dev, h->hx_dev, rtol, maxit, iters_out, relres_out, stream);
+  r3mg_status st2 = guarded(h, [&] {
+    CK(cudaMemcpyAsync(x_host, h->hx_dev, sizeof(double) * h->n, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+  return res == R3MG_OK ? st2 : res;
+}
+
+r3mg_status r3mg_level_apply(r3mg_hierarchy* h, int level, const double* x_dev, double* y_dev, void* stream) {
+  if (!h || level < 0 || level >= h->L || !x_dev || !y_dev) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    Level& A = h->lv[level];
+    if (level == 0) {
+      const int gv = grid_for(h->n);
+      k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(x_dev, h->perm, h->cb, h->n);
+      launch_level<double>(A, h->cb, EpApply<double>{h->cz}, nullptr, h->stream);
+      k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cz, h->perm, y_dev, h->n);
+    } else {
+      launch_level<double>(A, x_dev, EpApply<double>{y_dev}, nullptr, h->stream);
+    }
+    CK(cudaGetLastError());
+  });
+}
+
+r3mg_status r3mg_info(const r3mg_hierarchy* h, int* levels_out, int* depth_out, int64_t* n_out, int64_t* nnz_out,
+                      int64_t* nbox_out, double* lam_out) {
+  if (!h) return R3MG_E_ARG;
+  if (levels_out) *levels_out = h->L;
+  if (depth_out) *depth_out = h->part.depth;
+  for (int l = 0; l < h->L; ++l) {
+    if (n_out) n_out[l] = h->lv[l].n;
+    if (nnz_out) nnz_out[l] = h->lv[l].nnz;
+    if (nbox_out) nbox_out[l] = h->lv[l].nbox;
+    if (lam_out) lam_out[l] = h->lv[l].lam_hi;
+  }
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_get_agglomerates(const r3mg_hierarchy* h, int level, int64_t* box_of_point_host) {
+  if (!h || level < 1 || level >= h->L || !box_of_point_host) return R3MG_E_ARG;
+  const std::vector<int64_t>& off = h->part.box_off[level];
+  for (int64_t B = 0; B + 1 < (int64_t)off.size(); ++B)
+    for (int64_t k = off[B]; k < off[B + 1]; ++k) box_of_point_host[h->part.perm[k]] = B;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_get_level_pattern(const r3mg_hierarchy* h, int level, int64_t* nbr_ptr_host, int64_t* nbr_host) {
+  if (!h || level < 1 || level >= h->L || !nbr_ptr_host) return R3MG_E_ARG;
+  const HostPattern& pt = h->lv[level].pat;
+  std::memcpy(nbr_ptr_host, pt.ptr.data(), sizeof(int64_t) * pt.ptr.size());
+  if (nbr_host) std::memcpy(nbr_host, pt.nbr.data(), sizeof(int64_t) * pt.nbr.size());
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_get_level_blocks(r3mg_hierarchy* h, int level, double* vals_host) {
+  if (!h || level < 1 || level >= h->L || !vals_host) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    Level& C = h->lv[level];
+    double* tmp = dalloc<double>(h, C.npairs * h->b * h->b);
+    k_blocks_export<<<grid_for(C.npairs * h->b * h->b), 256, 0, h->stream>>>(C.pair_box, C.nbr_ptr, C.row_ptr, C.v64,
+                                                                              C.npairs, h->b, tmp);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(vals_host, tmp, sizeof(double) * C.npairs * h->b * h->b, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaFree(tmp));
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)tmp), h->allocs.end());
+  });
+}
+
+r3mg_status r3mg_get_prolongation(r3mg_hierarchy* h, int level, double* p_host) {
+  if (!h || level < 0 || level + 1 >= h->L || !p_host) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    const int b = h->b;
+    if (level == 0) {
+      std::vector<double> t(h->n * b);
+      CK(cudaMemcpyAsync(t.data(), h->P64[0], sizeof(double) * t.size(), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int64_t k = 0; k < h->n; ++k) std::memcpy(p_host + h->part.perm[k] * b, t.data() + k * b, sizeof(double) * b);
+    } else {
+      CK(cudaMemcpyAsync(p_host, h->P64[level], sizeof(double) * h->lv[level].nbox * b * b, cudaMemcpyDeviceToHost,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+  });
+}
+
+const char* r3mg_last_error(const r3mg_hierarchy* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+void r3mg_destroy(r3mg_hierarchy* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->host_scal) cudaFreeHost(h->host_scal);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

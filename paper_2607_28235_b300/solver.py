@@ -1,0 +1,168 @@
+"""Python binding of libr3mg: argument marshalling only.
+
+Every step of the solver runs inside libr3mg (CUDA kernels for sm_103a and
+host C++ for the R-tree); PyTorch tensors only provide device memory and
+the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import R3MGError, _Params, lib
+
+
+def _p(a) -> ctypes.c_void_p:
+    if isinstance(a, torch.Tensor):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(rc: int, h=None):
+    if rc != 0:
+        raise R3MGError(rc, lib().r3mg_last_error(h).decode())
+
+
+def default_params() -> dict:
+    p = _Params()
+    lib().r3mg_default_params(ctypes.byref(p))
+    return {f: getattr(p, f) for f, _ in _Params._fields_}
+
+
+def partition(coords: np.ndarray, leaf_size: int, levels: int):
+    """Host-only R-tree bisection: (perm, leaf_offsets, depth); perm[k] = caller index at tree position k."""
+    x = np.ascontiguousarray(coords, dtype=np.float64)
+    n, d = x.shape
+    perm = np.empty(n, np.int64)
+    depth = ctypes.c_int(0)
+    # leaf offsets need 2^D + 1 entries; D <= ceil(log2(n)) + 1
+    off = np.empty((1 << (max(int(np.ceil(np.log2(max(n, 1)))), 0) + 1)) + 1, np.int64)
+    rc = lib().r3mg_partition(n, d, _p(x), int(leaf_size), int(levels), _p(perm), _p(off), ctypes.byref(depth))
+    _check(rc)
+    return perm, off[: (1 << depth.value) + 1].copy(), depth.value
+
+
+class Hierarchy:
+    """R-tree multilevel hierarchy on the current CUDA device."""
+
+    def __init__(self, coords, rowptr, colidx, vals, **params):
+        p = _Params()
+        lib().r3mg_default_params(ctypes.byref(p))
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = {f: getattr(p, f) for f, _ in _Params._fields_}
+        x = np.ascontiguousarray(coords, dtype=np.float64)
+        self.n, self.dim = x.shape
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(colidx, dtype=np.int32)
+        va = np.ascontiguousarray(vals, dtype=np.float64)
+        self.nnz = int(rp[-1])
+        self.b = (p.pprime + 1) ** self.dim
+        h = ctypes.c_void_p()
+        rc = lib().r3mg_setup(self.n, self.dim, _p(x), _p(rp), _p(ci), _p(va), ctypes.byref(p), _stream(),
+                              ctypes.byref(h))
+        _check(rc)
+        self._h = h
+        info = self.info()
+        self.levels = info["levels"]
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().r3mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ solves
+    def vcycle(self, r: torch.Tensor) -> torch.Tensor:
+        r = r.contiguous()
+        assert r.is_cuda and r.dtype == torch.float64 and r.numel() == self.n
+        z = torch.empty_like(r)
+        _check(lib().r3mg_vcycle(self._h, _p(r), _p(z), _stream()), self._h)
+        return z
+
+    def pcg(self, b: torch.Tensor, x0: torch.Tensor | None = None, rtol: float = 1e-8, maxit: int = 500,
+            raise_on_noconv: bool = True):
+        b = b.contiguous()
+        assert b.is_cuda and b.dtype == torch.float64 and b.numel() == self.n
+        x = torch.zeros_like(b) if x0 is None else x0.clone().contiguous()
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0)
+        rc = lib().r3mg_pcg(self._h, _p(b), _p(x), float(rtol), int(maxit), ctypes.byref(it), ctypes.byref(rel),
+                            _stream())
+        if rc != 0 and not (rc == 7 and not raise_on_noconv):
+            _check(rc, self._h)
+        return x, it.value, rel.value
+
+    def pcg_host(self, b: np.ndarray, x0: np.ndarray | None = None, rtol: float = 1e-8, maxit: int = 500):
+        """Host buffers in and out; the copies happen inside the library call."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0)
+        rc = lib().r3mg_pcg_host(self._h, _p(b), _p(x), float(rtol), int(maxit), ctypes.byref(it),
+                                 ctypes.byref(rel), _stream())
+        _check(rc, self._h)
+        return x, it.value, rel.value
+
+    def update_values(self, vals: torch.Tensor):
+        vals = vals.contiguous()
+        assert vals.is_cuda and vals.dtype == torch.float64 and vals.numel() == self.nnz
+        _check(lib().r3mg_update_values(self._h, _p(vals), _stream()), self._h)
+
+    def level_apply(self, level: int, x: torch.Tensor) -> torch.Tensor:
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        _check(lib().r3mg_level_apply(self._h, int(level), _p(x), _p(y), _stream()), self._h)
+        return y
+
+    # ------------------------------------------------------------------ introspection
+    def info(self) -> dict:
+        L = ctypes.c_int(0)
+        D = ctypes.c_int(0)
+        _check(lib().r3mg_info(self._h, ctypes.byref(L), ctypes.byref(D), None, None, None, None), self._h)
+        n = np.zeros(L.value, np.int64); nnz = np.zeros(L.value, np.int64); nb = np.zeros(L.value, np.int64)
+        lam = np.zeros(L.value, np.float64)
+        _check(lib().r3mg_info(self._h, None, None, _p(n), _p(nnz), _p(nb), _p(lam)), self._h)
+        return {"levels": L.value, "depth": D.value, "n": n, "nnz": nnz, "nbox": nb, "lam_hi": lam}
+
+    def agglomerates(self, level: int) -> np.ndarray:
+        out = np.empty(self.n, np.int64)
+        _check(lib().r3mg_get_agglomerates(self._h, int(level), _p(out)), self._h)
+        return out
+
+    def level_pattern(self, level: int):
+        nbox = int(self.info()["nbox"][level])
+        ptr = np.empty(nbox + 1, np.int64)
+        _check(lib().r3mg_get_level_pattern(self._h, int(level), _p(ptr), None), self._h)
+        nbr = np.empty(int(ptr[-1]), np.int64)
+        _check(lib().r3mg_get_level_pattern(self._h, int(level), _p(ptr), _p(nbr)), self._h)
+        return ptr, nbr
+
+    def level_blocks(self, level: int) -> np.ndarray:
+        ptr, _ = self.level_pattern(level)
+        out = np.empty((int(ptr[-1]), self.b, self.b), np.float64)
+        _check(lib().r3mg_get_level_blocks(self._h, int(level), _p(out)), self._h)
+        return out
+
+    def prolongation(self, level: int) -> np.ndarray:
+        if level == 0:
+            out = np.empty((self.n, self.b), np.float64)
+        else:
+            nbox = int(self.info()["nbox"][level])
+            out = np.empty((nbox, self.b, self.b), np.float64)
+        _check(lib().r3mg_get_prolongation(self._h, int(level), _p(out)), self._h)
+        return out

@@ -1,0 +1,147 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances (FP64 path): structure bit-exact; P values 1e-14 absolute (products of
+O(1) Lagrange factors); Galerkin blocks and level products 1e-12 relative to the
+largest entry (sums of O(nnz_row * b) FP64 terms in a different order); one
+V-cycle 1e-12 relative (2-norm); PCG iterations +-1 and the solution within
+1e-10 relative of the oracle's.  FP32 V-cycle: the flexible CG still reaches
+the FP64 tolerance; its solution is compared with the oracle's at rtol * 1e3.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle.hierarchy import Params
+from tests.gpu_cases import CASES, make
+
+pytestmark = pytest.mark.gpu
+
+
+def _hier(P, params, precision=0):
+    import paper_2607_28235_b300 as R
+    return R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, precision=precision, **params)
+
+
+def _oracle(P, params):
+    return O.build_hierarchy(P.coords, P.scipy(), Params(params["leaf_size"], params["pprime"], params["levels"],
+                                                          cheb_degree=params["cheb_degree"]))
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def pair(request):
+    P, params = make(request.param)
+    return P, params, _hier(P, params), _oracle(P, params)
+
+
+def test_agglomerates_and_patterns_bit_exact(pair):
+    P, params, H, Ho = pair
+    for lev in range(1, params["levels"]):
+        assert np.array_equal(H.agglomerates(lev), Ho.part.box_of_point[lev])
+        ptr, nbr = H.level_pattern(lev)
+        ref = Ho.patterns[lev]
+        assert np.array_equal(np.diff(ptr), [len(v) for v in ref])
+        assert np.array_equal(nbr, np.concatenate(ref))
+
+
+def test_prolongation_values(pair):
+    P, params, H, Ho = pair
+    b = H.b
+    P0 = H.prolongation(0)
+    ref = Ho.P[0].toarray()
+    box = Ho.part.box_of_point[1]
+    got = np.zeros_like(ref)
+    for q in range(b):
+        got[np.arange(P.n), box * b + q] = P0[:, q]
+    assert np.max(np.abs(got - ref)) <= 1e-14
+    for lev in range(1, params["levels"] - 1):
+        Pt = H.prolongation(lev)
+        R = Ho.P[lev].toarray()
+        fan = 1 << P.dim
+        for c in range(Pt.shape[0]):
+            Bp = c // fan
+            assert np.max(np.abs(Pt[c] - R[c * b:(c + 1) * b, Bp * b:(Bp + 1) * b])) <= 1e-14
+
+
+def test_galerkin_blocks(pair):
+    P, params, H, Ho = pair
+    b = H.b
+    for lev in range(1, params["levels"]):
+        blocks = H.level_blocks(lev)
+        ptr, nbr = H.level_pattern(lev)
+        ref = Ho.A[lev].toarray()
+        got = np.zeros_like(ref)
+        for B in range(len(ptr) - 1):
+            for e in range(ptr[B], ptr[B + 1]):
+                got[B * b:(B + 1) * b, nbr[e] * b:(nbr[e] + 1) * b] = blocks[e]
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(got - ref)) <= 1e-12 * scale, (lev, np.max(np.abs(got - ref)) / scale)
+
+
+def test_level_apply_and_lambda(pair):
+    P, params, H, Ho = pair
+    info = H.info()
+    rng = np.random.default_rng(1)
+    for lev in range(params["levels"]):
+        A = Ho.A[lev]
+        x = rng.standard_normal(A.shape[0])
+        y = H.level_apply(lev, torch.tensor(x, device="cuda")).cpu().numpy()
+        ref = A @ x
+        assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
+        if lev < params["levels"] - 1:
+            assert abs(info["lam_hi"][lev] - Ho.lam[lev][1]) <= 1e-11 * Ho.lam[lev][1]
+
+
+def test_vcycle_fp64_parity(pair):
+    P, params, H, Ho = pair
+    rng = np.random.default_rng(2)
+    for trial in range(2):
+        r = rng.standard_normal(P.n) if trial else P.b.copy()
+        z = H.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+        ref = O.vcycle(Ho, r)
+        err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+        assert err <= 1e-12, err
+        # twice in a row gives the same bits (graph replay is deterministic)
+        z2 = H.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+        assert np.array_equal(z, z2)
+
+
+def test_pcg_fp64_parity(pair):
+    P, params, H, Ho = pair
+    rtol = 1e-10
+    x, it, rel = H.pcg(torch.tensor(P.b, device="cuda"), rtol=rtol)
+    ref = O.pcg(P.scipy(), P.b, lambda r: O.vcycle(Ho, r), rtol=rtol)
+    assert abs(it - ref.iterations) <= 1, (it, ref.iterations)
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x) * max(1.0, 1e10 * rtol)
+    assert np.linalg.norm(P.b - P.scipy() @ x) <= rtol * np.linalg.norm(P.b)
+
+
+def test_pcg_mixed_precision(pair):
+    P, params, H, Ho = pair
+    Hm = _hier(P, params, precision=1)
+    rtol = 1e-10
+    x, it, rel = Hm.pcg(torch.tensor(P.b, device="cuda"), rtol=rtol)
+    ref = O.pcg(P.scipy(), P.b, lambda r: O.vcycle(Ho, r), rtol=rtol)
+    x = x.cpu().numpy()
+    assert np.linalg.norm(P.b - P.scipy() @ x) <= rtol * np.linalg.norm(P.b)
+    assert np.linalg.norm(x - ref.x) <= 1e3 * rtol * np.linalg.norm(ref.x)
+    assert it <= ref.iterations + 3
+    Hm.close()
+
+
+def test_pcg_host_buffers(pair):
+    P, params, H, Ho = pair
+    x, it, rel = H.pcg_host(P.b, rtol=1e-9)
+    assert np.linalg.norm(P.b - P.scipy() @ x) <= 1e-9 * np.linalg.norm(P.b)
+
+
+def test_initial_guess_and_zero_rhs(pair):
+    P, params, H, Ho = pair
+    xs = np.linalg.solve(P.scipy().toarray(), P.b) if P.n < 3000 else None
+    x0 = torch.tensor(P.b * 0.0, device="cuda")
+    x, it, rel = H.pcg(torch.zeros(P.n, dtype=torch.float64, device="cuda"), x0=x0)
+    assert it == 0 and float(x.abs().max()) == 0.0
+    if xs is not None:
+        x, it, rel = H.pcg(torch.tensor(P.b, device="cuda"), x0=torch.tensor(xs, device="cuda"), rtol=1e-8)
+        assert it == 0

@@ -1,0 +1,76 @@
+"""C-ABI library checks that need no GPU: symbols, host R-tree bit-exactness, error codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2607_28235_b300 as R
+from paper_2607_28235_b300 import _lib
+from oracle.rtree import rtree_partition
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    R.build()
+    return _lib.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "r3mg.h")).read()
+    names = set(re.findall(r"\b(r3mg_[a-z_]+)\s*\(", hdr))
+    assert len(names) >= 15
+    raw = ctypes.CDLL(_lib.SO_PATH)
+    for nm in sorted(names):
+        assert hasattr(raw, nm), nm
+
+
+def test_default_params(lib):
+    p = R.default_params()
+    assert p["cheb_degree"] == 3 and p["sweeps"] == 2 and p["lanczos_steps"] == 10
+    assert p["eig_safety"] == 1.1 and p["eig_ratio"] == 30.0
+
+
+@pytest.mark.parametrize("n,d,leaf,L,seed", [(1000, 2, 17, 3, 0), (4097, 3, 64, 3, 1), (777, 3, 5, 4, 2),
+                                             (64, 2, 64, 2, 3), (5000, 3, 40, 3, 4), (3, 2, 2, 2, 5)])
+def test_partition_bit_exact_vs_oracle(lib, n, d, leaf, L, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, (n, d))
+    x[::5] = np.round(x[::5], 1)        # coordinate ties exercise the secondary keys
+    x[::11] = x[2]                      # full duplicates exercise the index tie-break
+    perm, off, D = R.partition(x, leaf, L)
+    part = rtree_partition(x, leaf, L)
+    assert D == part.depth
+    assert np.array_equal(perm, part.perm)
+    assert np.array_equal(off, part.box_offsets[1] if L >= 2 else off)
+
+
+def test_partition_fe_points(lib):
+    import workloads as W
+    P = W.poisson(3, 6, 3, perturb=0.2, seed=3)
+    perm, off, D = R.partition(P.coords, 50, 3)
+    part = rtree_partition(P.coords, 50, 3)
+    assert np.array_equal(perm, part.perm) and np.array_equal(off, part.box_offsets[1])
+
+
+def test_partition_hand_example(lib):
+    pts = np.array([[0, 0], [4, 1], [1, 3], [2, 2], [3, .5], [.5, 1.5], [3.5, 3.5], [2.5, 1], [1.5, .2], [2, 3]], float)
+    perm, off, D = R.partition(pts, 3, 2)
+    assert perm.tolist() == [0, 8, 5, 3, 2, 4, 7, 1, 9, 6] and off.tolist() == [0, 3, 5, 8, 10] and D == 2
+
+
+def test_partition_errors(lib):
+    x = np.random.default_rng(0).uniform(0, 1, (100, 3))
+    with pytest.raises(R.R3MGError) as e:
+        R.partition(x, 64, 3)
+    assert e.value.name == "E_DEPTH"
+    with pytest.raises(R.R3MGError) as e:
+        R.partition(x, 1, 2)
+    assert e.value.name == "E_ARG"
+    x[3, 1] = np.nan
+    with pytest.raises(R.R3MGError) as e:
+        R.partition(x, 8, 2)
+    assert e.value.name == "E_ARG"
