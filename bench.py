@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark: PCG solve to 1e-8 relative residual, preconditioned by one R-tree V-cycle.
+
+Workload (one GPU): 3D Poisson on the unit cube, Q3 Lagrange elements on a 32^3 hex
+mesh with interior vertices perturbed by up to 0.2 h per component (seeded uniform),
+manufactured right-hand side; 857,375 free DoFs, 101.8M nonzeros.  Hierarchy: R-tree
+leaf 128 points, p' = 2, 4 levels, Chebyshev-Jacobi degree 3, 2 + 2 sweeps.
+A step is one complete PCG solve (hierarchy already set up, inputs resident in HBM).
+The headline form is the FP32 V-cycle inside FP64 flexible CG; the plain FP64 solve is
+timed beside it.  The matrix (0.6-1.2 GB per level) is far larger than L2, so no flush
+is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (the single solve does not shard); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+# the oracle timing uses one host thread: BLAS threads off (OpenMP of the library's host setup untouched)
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+
+def _one_thread():
+    """Limit BLAS pools to one thread when threadpoolctl is available (env vars cover the rest)."""
+    try:
+        from threadpoolctl import threadpool_limits
+        return threadpool_limits(1)
+    except ImportError:
+        import contextlib
+        return contextlib.nullcontext()
+
+WORKLOAD = dict(name="poisson3d_q3_32cube_perturbed", dim=3, N=32, p=3, perturb=0.2, seed=1, leaf_size=128,
+                pprime=2, levels=4, cheb_degree=3, sweeps=2, rtol=1e-8)
+# smaller instance for ncu captures (inputs still larger than L2, a few GB on the device)
+SMALL = dict(WORKLOAD, name="poisson3d_q3_24cube_perturbed", N=24)
+# bounded CPU sample of the same workload family for the oracle timing (8x fewer DoFs)
+SAMPLE = dict(WORKLOAD, name="poisson3d_q3_16cube_perturbed", N=16)
+METRIC = "PCG solve ms to 1e-8 rel-res"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _problem(w):
+    import workloads as W
+    return W.poisson(w["dim"], w["N"], w["p"], perturb=w["perturb"], seed=w["seed"])
+
+
+def _hparams(w, precision):
+    return dict(leaf_size=w["leaf_size"], pprime=w["pprime"], levels=w["levels"], cheb_degree=w["cheb_degree"],
+                sweeps=w["sweeps"], precision=precision)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path).read().splitlines()[1:]:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1].split()[0]), float(parts[2].split()[0]), parts))
+            except ValueError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, _, parts in rows:
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def _traffic(kernel_name):
+    """dram bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", f"{kernel_name}.md")
+    if not os.path.exists(prof):
+        return None
+    src = open(os.path.join(ROOT, "paper_2607_28235_b300", "csrc", "kernels_level.cuh"), "rb").read()
+    digest = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in open(prof):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(reps=2):
+    """The oracle as it stands on the host cores (1 thread), bounded sample, scaled to the workload."""
+    import oracle as O
+    from oracle.hierarchy import Params
+    import workloads as W
+    Ps = _problem(SAMPLE)
+    nfull = W.sizes(WORKLOAD["dim"], WORKLOAD["N"], WORKLOAD["p"])[1]
+    with _one_thread():
+        A = Ps.scipy()
+        H = O.build_hierarchy(Ps.coords, A, Params(SAMPLE["leaf_size"], SAMPLE["pprime"], SAMPLE["levels"],
+                                                   cheb_degree=SAMPLE["cheb_degree"], sweeps=SAMPLE["sweeps"]))
+        times, its = [], []
+        for _ in range(reps):
+            t = time.perf_counter()
+            r = O.pcg(A, Ps.b, lambda v: O.vcycle(H, v), rtol=SAMPLE["rtol"])
+            times.append((time.perf_counter() - t) * 1e3)
+            its.append(r.iterations)
+    ms = min(times)
+    scale = nfull / Ps.nnz
+    return {"value": ms * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle PCG solve (setup excluded), 1 thread, on the same workload family at 16^3 cells "
+                       f"({Ps.n} DoFs, {Ps.nnz} nnz, {its[0]} iterations), best of {reps}: {ms:.1f} ms, "
+                       f"scaled by the fine-level nnz ratio {scale:.2f} to the 32^3 workload"),
+            "sample_ms": ms, "sample_iterations": its[0]}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    import oracle as O
+    from oracle.hierarchy import Params
+    import workloads as W
+    Ps = _problem(SAMPLE)
+    nfull = W.sizes(WORKLOAD["dim"], WORKLOAD["N"], WORKLOAD["p"])[1]
+    scale = nfull / Ps.nnz
+    with _one_thread():
+        A = Ps.scipy()
+        H = O.build_hierarchy(Ps.coords, A, Params(SAMPLE["leaf_size"], SAMPLE["pprime"], SAMPLE["levels"],
+                                                   cheb_degree=SAMPLE["cheb_degree"], sweeps=SAMPLE["sweeps"]))
+        for _ in range(args.warmup):
+            O.pcg(A, Ps.b, lambda v: O.vcycle(H, v), rtol=SAMPLE["rtol"])
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            r = O.pcg(A, Ps.b, lambda v: O.vcycle(H, v), rtol=SAMPLE["rtol"])
+        ms = (time.perf_counter() - t) * 1e3 / max(args.steps, 1)
+    val = ms * scale
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "sample": SAMPLE["name"], "iterations": r.iterations},
+            "cpu_baseline": {"value": val, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": (f"oracle PCG solve per step on the 16^3 instance ({Ps.n} DoFs, {ms:.1f} ms), "
+                                        f"scaled by the fine nnz ratio {scale:.2f}")},
+            "e2e": {"value": val, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2607_28235_b300 as R
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = SMALL if args.workload == "small" else WORKLOAD
+    P = _problem(w)
+    t0 = time.perf_counter()
+    Hm = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, **_hparams(w, 1))
+    setup_mixed_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Hd = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, **_hparams(w, 0))
+    setup_fp64_s = time.perf_counter() - t0
+    info = Hm.info()
+    b = torch.tensor(P.b, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(H, steps, warmup, profile=False):
+        for _ in range(warmup):
+            H.pcg(b, rtol=w["rtol"])
+        if profile:
+            H.profile(True)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = []
+        for _ in range(steps):
+            x, it, rel = H.pcg(b, rtol=w["rtol"])
+            its.append(it)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        prof = H.profile_read() if profile else None
+        if profile:
+            H.profile(False)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, its, x, rel, prof
+
+    clocks = Clocks(local)
+    with clocks:
+        torch.cuda.profiler.start()      # ncu --profile-from-start off captures this region only
+        ms_mixed, its_m, x_m, rel_m, prof = timed(Hm, args.steps, args.warmup, profile=True)
+        torch.cuda.profiler.stop()
+    ms_fp64, its_d, x_d, rel_d, prof_d = timed(Hd, max(1, args.steps // 2), max(3, args.warmup // 2), profile=True)
+    # end to end through the C ABI with host buffers (copies inside the call)
+    bh = np.ascontiguousarray(P.b)
+    for _ in range(2):
+        Hm.pcg_host(bh, rtol=w["rtol"])
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        xh, ith, relh = Hm.pcg_host(bh, rtol=w["rtol"])
+    e2e_ms = (time.perf_counter() - t) * 1e3 / args.steps
+    # independent check of the answers (scipy on the host)
+    A = P.scipy()
+    bn = np.linalg.norm(P.b)
+    chk_m = float(np.linalg.norm(P.b - A @ x_m.cpu().numpy()) / bn)
+    chk_d = float(np.linalg.norm(P.b - A @ x_d.cpu().numpy()) / bn)
+    diff_md = float(np.linalg.norm(x_m.cpu().numpy() - x_d.cpu().numpy()) / np.linalg.norm(x_d.cpu().numpy()))
+    if rank != 0:
+        return
+    peak, peak_kind = _peaks()
+    kinds = {k: v for k, v in prof.items() if isinstance(v, dict) and v["launches"] > 0}
+    top = max(kinds, key=lambda k: kinds[k]["ms"])
+    tk = kinds[top]
+    avg_ms = tk["ms"] / tk["launches"]
+    achieved = tk["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    kernel_name = f"{top}_{'f64' if top.startswith('cg') else 'f32'}"
+    share = {k: round(v["ms"] / (ms_mixed * args.steps), 4) for k, v in kinds.items()}
+    kinds_d = {k: v for k, v in prof_d.items() if isinstance(v, dict) and v["launches"] > 0}
+    top_d = max(kinds_d, key=lambda k: kinds_d[k]["ms"])
+    td = kinds_d[top_d]
+    avg_d = td["ms"] / td["launches"]
+    line = {
+        "metric": METRIC, "value": ms_mixed, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": w["name"], "dofs_free": P.n, "nnz": P.nnz, "leaf_size": w["leaf_size"],
+                   "pprime": w["pprime"], "levels": w["levels"], "cheb_degree": w["cheb_degree"],
+                   "sweeps": w["sweeps"], "rtol": w["rtol"], "precision": "FP32 V-cycle in FP64 flexible CG",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (level matrices 0.6-1.4 GB)", "level_n": info["n"].tolist(),
+                   "level_nnz": info["nnz"].tolist()},
+        "iterations": its_m[-1], "relres_check": chk_m,
+        "fp64": {"ms": ms_fp64, "iterations": its_d[-1], "relres_check": chk_d,
+                 "top_kernel": top_d, "top_kernel_avg_ms": avg_d,
+                 "top_kernel_achieved_gbs": td["bytes_per_launch"] / (avg_d * 1e-3) / 1e9},
+        "mixed_vs_fp64_speedup": ms_fp64 / ms_mixed, "mixed_vs_fp64_solution_reldiff": diff_md,
+        "setup_s": {"mixed": setup_mixed_s, "fp64": setup_fp64_s},
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes_per_launch": tk["bytes_per_launch"], "avg_launch_ms": avg_ms,
+                     "traffic": _traffic(kernel_name)},
+        "kernel_time_share": share,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * 8 * P.n, "d2h_bytes_per_step": 8 * P.n},
+        "gpu_launches": int(prof["kernel_launches"]),
+        "clocks": clocks.summary(),
+    }
+    print("gpu part: " + json.dumps(line), file=sys.stderr, flush=True)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="full", choices=["full", "small"],
+                    help="small: the 24^3 instance used for ncu captures (not a bench line)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,23 @@ r3mg_status r3mg_get_level_blocks(r3mg_hierarchy* h, int level, double* vals_hos
  * level l >= 1: p_host (nbox_l x b x b), block c = P~[(c,q'), (parent(c), q)]. Synchronises. */
 r3mg_status r3mg_get_prolongation(r3mg_hierarchy* h, int level, double* p_host);
 
+/*
+ * Instrumentation.  r3mg_profile_enable(h, 1) records a pair of CUDA events on the
+ * library's internal stream (the stream the kernels run on) around every level-operator
+ * launch of subsequent r3mg_pcg calls: kind 0 = the CG product A p (FP64 fine level),
+ * kind 1 + l = the fused Chebyshev-Jacobi steps on level l (the V-cycle graph is
+ * recaptured with event-record nodes).  Enabling or disabling resets the totals and the
+ * kernel launch counter.  Synchronises the stream.
+ */
+r3mg_status r3mg_profile_enable(r3mg_hierarchy* h, int on);
+
+/* Totals for one kind since r3mg_profile_enable: summed event time (ms), number of
+ * launches timed, the kind's algorithmic bytes per launch (stored nonzeros x (value +
+ * index bytes) + 8 bytes per row pointer + each vector read or written once), and the
+ * number of kernels launched by solve-path calls.  Any output may be NULL.  Synchronises. */
+r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int64_t* count, double* bytes_per_launch,
+                              int64_t* kernel_launches);
+
 /* Message of the last failure on h (or of the last failed r3mg_setup /
  * r3mg_partition in this thread when h is NULL).  Never NULL. */
 const char* r3mg_last_error(const r3mg_hierarchy* h);

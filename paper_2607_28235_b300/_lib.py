@@ -86,6 +86,9 @@ def lib():
         "r3mg_get_level_pattern": (ip, [vp, i32, vp, vp]),
         "r3mg_get_level_blocks": (ip, [vp, i32, vp]),
         "r3mg_get_prolongation": (ip, [vp, i32, vp]),
+        "r3mg_profile_enable": (ip, [vp, i32]),
+        "r3mg_profile_read": (ip, [vp, i32, P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_double),
+                                   P(ctypes.c_int64)]),
         "r3mg_last_error": (ctypes.c_char_p, [vp]),
         "r3mg_destroy": (None, [vp]),
     }

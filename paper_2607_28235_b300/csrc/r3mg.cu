@@ -70,8 +70,23 @@ struct r3mg_hierarchy {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_state = 0;  // 0 untried, 1 ready, -1 unavailable
+  int graph_prof = 0;   // profiling state the graph was captured with
   std::vector<void*> allocs;
   std::string err = "no error";
+  // instrumentation: event pairs around level-operator launches, kernel launch counter
+  int prof_on = 0;
+  struct ProfSlot { int kind; cudaEvent_t e0, e1; };
+  std::vector<ProfSlot> slots;        // fixed slots used by the V-cycle body (same in every replay)
+  size_t slot_next = 0;
+  std::vector<int> pending;           // slots recorded since the last harvest
+  std::vector<int> graph_slots;       // slots recorded by one replay of the V-cycle graph
+  ProfSlot cg_slot{0, nullptr, nullptr};  // the CG product (launched outside the graph)
+  bool cg_pending = false;
+  std::vector<double> prof_ms;        // per kind: total milliseconds
+  std::vector<int64_t> prof_n;        // per kind: launches
+  std::vector<double> prof_bytes;     // per kind: algorithmic bytes per launch
+  int64_t launches = 0;               // kernels launched by solve-path calls
+  int64_t graph_kernels = 0;          // kernels in one replay of the V-cycle graph
 };
 
 namespace {
@@ -150,6 +165,49 @@ void launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_
   }
 }
 
+// kinds: 0 = CG product (FP64 fine level), 1 + l = smoother steps on level l
+int prof_begin(r3mg_hierarchy* h, int kind, bool capturing) {
+  if (!h->prof_on) return -1;
+  if (h->slot_next == h->slots.size()) {
+    r3mg_hierarchy::ProfSlot s{kind, nullptr, nullptr};
+    CK(cudaEventCreate(&s.e0));
+    CK(cudaEventCreate(&s.e1));
+    h->slots.push_back(s);
+  }
+  const int id = (int)h->slot_next++;
+  h->slots[id].kind = kind;
+  CK(cudaEventRecordWithFlags(h->slots[id].e0, h->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+  return id;
+}
+
+void prof_end(r3mg_hierarchy* h, int id, bool capturing) {
+  if (id < 0) return;
+  CK(cudaEventRecordWithFlags(h->slots[id].e1, h->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+  if (capturing) h->graph_slots.push_back(id); else h->pending.push_back(id);
+}
+
+// after a host synchronisation: fold the elapsed times of every recorded pair into the totals
+void prof_add(r3mg_hierarchy* h, int k, float ms) {
+  if ((int)h->prof_ms.size() <= k) { h->prof_ms.resize(k + 1, 0.0); h->prof_n.resize(k + 1, 0); }
+  h->prof_ms[k] += ms;
+  h->prof_n[k] += 1;
+}
+
+void prof_harvest(r3mg_hierarchy* h) {
+  if (h->cg_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->cg_slot.e0, h->cg_slot.e1) == cudaSuccess) prof_add(h, 0, ms);
+    h->cg_pending = false;
+  }
+  for (int id : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->slots[id].e0, h->slots[id].e1) == cudaSuccess) {
+      prof_add(h, h->slots[id].kind, ms);
+    }
+  }
+  h->pending.clear();
+}
+
 void read_status(r3mg_hierarchy* h, int& st) {
   CK(cudaMemcpyAsync(&h->host_scal[15], h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -221,17 +279,22 @@ const T* Dinv(const Level& L) {
 // d[0] = D^{-1} b / theta.  Returns the d buffer of level 0 holding the last update:
 // the result is z = x_0 + d.
 template <typename T>
-T* vcycle_body(r3mg_hierarchy* h) {
+T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
   cudaStream_t s = h->stream;
   const int L = h->L;
   std::vector<int> cur(L, 0);
+  int64_t nk = 0;
+  h->slot_next = 0;
   for (int l = 0; l < L - 1; ++l) {
     Level& A = h->lv[l];
     T* x = (T*)A.x; T* r = (T*)A.r;
     for (auto& ac : A.pre) {
       T* d = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      const int ps = prof_begin(h, 1 + l, capturing);
       launch_level<T>(A, d, EpCheb<T>{x, r, d, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, s);
+      prof_end(h, ps, capturing);
       cur[l] ^= 1;
+      ++nk;
     }
     Level& C = h->lv[l + 1];
     const bool coarsest = (l + 1 == L - 1);
@@ -241,11 +304,13 @@ T* vcycle_body(r3mg_hierarchy* h) {
     else
       k_restrict_coarse<T><<<grid_for(C.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), r, C.nbox, h->b, h->fan, nx);
     CK(cudaGetLastError());
+    ++nk;
   }
   {
     Level& C = h->lv[L - 1];
     k_dense_gemv<T><<<grid_for(h->nc * 32), 256, 0, s>>>(Ainv<T>(h), h->ncp, (const T*)C.r, h->nc, (T*)C.x);
     CK(cudaGetLastError());
+    ++nk;
   }
   for (int l = L - 2; l >= 0; --l) {
     Level& A = h->lv[l];
@@ -259,35 +324,47 @@ T* vcycle_body(r3mg_hierarchy* h) {
     else
       k_prolong_coarse<T><<<grid_for(A.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), x1, d1, A.nbox, h->b, h->fan, d);
     CK(cudaGetLastError());
+    ++nk;
     T* x = (T*)A.x; T* r = (T*)A.r;
     for (auto& ac : A.post) {
       T* dd = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      const int ps = prof_begin(h, 1 + l, capturing);
       launch_level<T>(A, dd, EpCheb<T>{x, r, dd, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, s);
+      prof_end(h, ps, capturing);
       cur[l] ^= 1;
+      ++nk;
     }
   }
+  if (capturing) h->graph_kernels = nk; else h->launches += nk;
   return (T*)h->lv[0].d[cur[0]];
 }
 
 template <typename T>
 T* run_vcycle(r3mg_hierarchy* h) {
-  // capture once into a CUDA graph; the buffers never move, so the graph is reusable
+  // capture once into a CUDA graph; the buffers never move, so the graph is reusable.
+  // Switching profiling on or off recaptures (event-record nodes are part of the graph).
+  if (h->graph_state == 1 && h->graph_prof != h->prof_on) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_state = 0;
+  }
   if (h->graph_state == 0) {
     cudaGraph_t g = nullptr;
-    T* out = nullptr;
+    h->graph_slots.clear();
     bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      try { out = vcycle_body<T>(h); } catch (Fail&) { ok = false; }
+      try { vcycle_body<T>(h, true); } catch (Fail&) { ok = false; }
       if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess) ok = false;
     }
-    if (ok && cudaGraphInstantiate(&h->graph, g, 0) == cudaSuccess) h->graph_state = 1;
-    else { h->graph_state = -1; cudaGetLastError(); }
+    if (ok && cudaGraphInstantiate(&h->graph, g, 0) == cudaSuccess) { h->graph_state = 1; h->graph_prof = h->prof_on; }
+    else { h->graph_state = -1; h->graph_slots.clear(); cudaGetLastError(); }
     if (g) cudaGraphDestroy(g);
-    (void)out;
   }
   if (h->graph_state == 1) {
     CK(cudaGraphLaunch(h->graph, h->stream));
-    // the body is deterministic: recompute which buffer holds the result without launching
+    h->launches += h->graph_kernels;
+    for (int id : h->graph_slots) h->pending.push_back(id);
+    // the body is deterministic: the result sits in d[(pre + post) % 2] of level 0
     const int steps0 = (int)(h->lv[0].pre.size() + h->lv[0].post.size());
     return (T*)h->lv[0].d[steps0 & 1];
   }
@@ -302,6 +379,7 @@ void vcycle_apply(r3mg_hierarchy* h, const double* r_tree, double* z_tree, bool 
   T* d = use_graph ? run_vcycle<T>(h) : vcycle_body<T>(h);
   k_vc_final_dot<T><<<grid_for(h->n), 256, 0, h->stream>>>((const T*)F.x, d, z_tree, nullptr, h->n, nullptr);
   CK(cudaGetLastError());
+  h->launches += 2;
 }
 
 // ---------------------------------------------------------------- setup
@@ -696,7 +774,13 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
   if (rel <= rtol) return R3MG_OK;
   precondition_restart();
   for (int it = 1; it <= maxit; ++it) {
+    if (h->prof_on) {
+      if (!h->cg_slot.e0) { CK(cudaEventCreate(&h->cg_slot.e0)); CK(cudaEventCreate(&h->cg_slot.e1)); }
+      CK(cudaEventRecord(h->cg_slot.e0, s));
+    }
     launch_level<double>(F, h->cp, EpApplyDot<double>{h->cq, h->cp}, h->part_a, s);
+    if (h->prof_on) { CK(cudaEventRecord(h->cg_slot.e1, s)); h->cg_pending = true; }
+    h->launches += 3;   // product, reduction, update
     reduce_dev(h, h->part_a, nb0, S_PQ, fcg ? FIN_ALPHA_FCG : FIN_ALPHA_PCG);
     k_cg_update<T><<<gv, 256, 0, s>>>(h->cx, h->cr, h->cp, h->cq, h->scal, n, h->part_a, (T*)F.r, (T*)F.x,
                                       (T*)F.d[0], Dinv<T>(F), (T)F.c0);
@@ -707,6 +791,8 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
     CK(cudaMemcpyAsync(&h->host_scal[15], h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     rr = h->host_scal[S_RR];
+    h->launches += 1;
+    prof_harvest(h);
     int st = 0;
     std::memcpy(&st, &h->host_scal[15], sizeof(int));
     if (st) {
@@ -732,6 +818,7 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
     k_p_update<<<gv, 256, 0, s>>>(h->cp, h->cz, h->cr, h->scal, n, fcg ? 1 : 0, fcg ? h->part_a : nullptr);
     CK(cudaGetLastError());
     if (fcg) reduce_dev(h, h->part_a, gv, S_PR, FIN_NONE);
+    h->launches += fcg ? 4 : 3;
   }
   return R3MG_E_NOCONV;
 }
@@ -842,7 +929,9 @@ r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, doub
     res = (h->prm.precision == 1) ? krylov<float>(h, rtol, maxit, &it, &rel) : krylov<double>(h, rtol, maxit, &it, &rel);
     k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cx, h->perm, x_dev, h->n);
     CK(cudaGetLastError());
+    h->launches += 3;
     CK(cudaStreamSynchronize(h->stream));
+    prof_harvest(h);
   });
   if (iters_out) *iters_out = it;
   if (relres_out) *relres_out = rel;
@@ -948,12 +1037,53 @@ r3mg_status r3mg_get_prolongation(r3mg_hierarchy* h, int level, double* p_host) 
   });
 }
 
+r3mg_status r3mg_profile_enable(r3mg_hierarchy* h, int on) {
+  if (!h) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    CK(cudaStreamSynchronize(h->stream));
+    prof_harvest(h);
+    h->prof_on = on ? 1 : 0;
+    h->prof_ms.clear();
+    h->prof_n.clear();
+    h->launches = 0;
+  });
+}
+
+r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int64_t* count, double* bytes_per_launch,
+                              int64_t* kernel_launches) {
+  if (!h || kind < 0 || kind > h->L) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    CK(cudaStreamSynchronize(h->stream));
+    prof_harvest(h);
+    if (total_ms) *total_ms = kind < (int)h->prof_ms.size() ? h->prof_ms[kind] : 0.0;
+    if (count) *count = kind < (int)h->prof_n.size() ? h->prof_n[kind] : 0;
+    if (kernel_launches) *kernel_launches = h->launches;
+    if (bytes_per_launch) {
+      // algorithmic bytes: stored nonzeros (padding excluded) x (value + index bytes), one
+      // 8-byte row pointer per row, and every vector read or written once
+      const bool f32 = (h->prm.precision == 1);
+      if (kind == 0) {
+        const Level& F = h->lv[0];
+        *bytes_per_launch = (double)F.nnz * (8 + 2) + 8.0 * (F.n + 1) + 2.0 * 8.0 * F.n;
+      } else {
+        const Level& A = h->lv[kind - 1];
+        const double es = f32 ? 4.0 : 8.0;
+        const double ib = (A.b == 0) ? 2.0 : 0.0;
+        *bytes_per_launch = (double)A.nnz * (es + ib) + 8.0 * (A.n + 1) + 7.0 * es * A.n +
+                            (A.b == 0 ? 0.0 : 8.0 * (double)A.npairs);
+      }
+    }
+  });
+}
+
 const char* r3mg_last_error(const r3mg_hierarchy* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
 
 void r3mg_destroy(r3mg_hierarchy* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (auto& sl : h->slots) { cudaEventDestroy(sl.e0); cudaEventDestroy(sl.e1); }
+  if (h->cg_slot.e0) { cudaEventDestroy(h->cg_slot.e0); cudaEventDestroy(h->cg_slot.e1); }
   for (void* p : h->allocs) cudaFree(p);
   if (h->host_scal) cudaFreeHost(h->host_scal);
   if (h->ev_in) cudaEventDestroy(h->ev_in);

@@ -129,6 +129,23 @@ class Hierarchy:
         _check(lib().r3mg_level_apply(self._h, int(level), _p(x), _p(y), _stream()), self._h)
         return y
 
+    # ------------------------------------------------------------------ instrumentation
+    def profile(self, on: bool = True):
+        _check(lib().r3mg_profile_enable(self._h, 1 if on else 0), self._h)
+
+    def profile_read(self) -> dict:
+        """Per kind: (total ms, launches, algorithmic bytes per launch); plus kernel launches."""
+        out = {}
+        nl = ctypes.c_int64(0)
+        for kind in range(self.levels + 1):
+            ms = ctypes.c_double(0); n = ctypes.c_int64(0); by = ctypes.c_double(0)
+            _check(lib().r3mg_profile_read(self._h, kind, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by),
+                                           ctypes.byref(nl)), self._h)
+            name = "cg_product_f64" if kind == 0 else f"cheb_step_level{kind - 1}"
+            out[name] = {"ms": ms.value, "launches": n.value, "bytes_per_launch": by.value}
+        out["kernel_launches"] = nl.value
+        return out
+
     # ------------------------------------------------------------------ introspection
     def info(self) -> dict:
         L = ctypes.c_int(0)
