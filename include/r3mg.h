@@ -63,10 +63,14 @@ typedef struct {
   int precision;        /* 0: FP64 V-cycle inside FP64 PCG; 1: FP32 V-cycle inside FP64 flexible CG */
   int group_lanes;      /* lanes per matrix row in the level kernels (4, 8, 16, 32); 0 = automatic */
   uint64_t seed;        /* splitmix64 seed of the Lanczos start vectors (level l uses seed + l) */
+  int kernel_form;      /* level operator kernel: 0 = autotuned at setup (each level times the
+                           register- and TMA-streamed kernels over lanes-per-row and CTA sizes
+                           and keeps the fastest), 1 = register-streamed, 2 = TMA-streamed
+                           where a box fits the shared memory */
 } r3mg_params;
 
 /* Fill `p` with the defaults: leaf 64, p' 1, 3 levels, degree 3, 2 sweeps,
- * 10 Lanczos steps, 1.1, 30, FP64, automatic lanes, seed 0x5EED. */
+ * 10 Lanczos steps, 1.1, 30, FP64, automatic lanes, seed 0x5EED, automatic kernel form. */
 void r3mg_default_params(r3mg_params* p);
 
 /*
@@ -187,6 +191,12 @@ r3mg_status r3mg_profile_enable(r3mg_hierarchy* h, int on);
  * number of kernels launched by solve-path calls.  Any output may be NULL.  Synchronises. */
 r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int64_t* count, double* bytes_per_launch,
                               int64_t* kernel_launches);
+
+/* Level-operator kernel chosen for level l and precision (fp32 = 0: FP64, 1: FP32):
+ * form 0 = register-streamed, 1 = TMA-streamed; lanes per matrix row; threads per CTA;
+ * the autotuner's measured time of one launch (0 when not tuned).  Any output may be NULL. */
+r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
+                               float* tuned_ms);
 
 /* Message of the last failure on h (or of the last failed r3mg_setup /
  * r3mg_partition in this thread when h is NULL).  Never NULL. */

@@ -57,7 +57,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("pprime", ctypes.c_int), ("levels", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("sweeps", ctypes.c_int), ("lanczos_steps", ctypes.c_int),
                 ("eig_safety", ctypes.c_double), ("eig_ratio", ctypes.c_double), ("precision", ctypes.c_int),
-                ("group_lanes", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("group_lanes", ctypes.c_int), ("seed", ctypes.c_uint64), ("kernel_form", ctypes.c_int)]
 
 
 _lib = None
@@ -89,6 +89,8 @@ def lib():
         "r3mg_profile_enable": (ip, [vp, i32]),
         "r3mg_profile_read": (ip, [vp, i32, P(ctypes.c_double), P(ctypes.c_int64), P(ctypes.c_double),
                                    P(ctypes.c_int64)]),
+        "r3mg_kernel_config": (ip, [vp, i32, i32, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                                    P(ctypes.c_float)]),
         "r3mg_last_error": (ctypes.c_char_p, [vp]),
         "r3mg_destroy": (None, [vp]),
     }

@@ -55,6 +55,15 @@ __device__ __forceinline__ void load_idx4(const uint16_t* p, int (&i)[4]) {
   i[0] = a.x & 0xffff; i[1] = a.x >> 16; i[2] = a.y & 0xffff; i[3] = a.y >> 16;
 }
 
+// asynchronous 4- or 8-byte global -> shared copy (cp.async.ca), completed by cp_async_wait_all
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(sizeof(T)));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int G, typename T>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
@@ -79,18 +88,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Each gets (row, y = (A x)_row) from the group leader; `acc` is a per-thread partial sum
 // folded into one value per CTA written to `part[blockIdx.x]` when the epilogue wants it.
 
+// Each epilogue loads the row's own vector entries in pre() -- issued before the row's matrix
+// stream so their latency overlaps it -- and finishes the row in post().
 template <typename T>
 struct EpApply {            // y_out = A x
   T* y;
   static constexpr bool kDot = false;
-  __device__ void operator()(int64_t r, T y_r, double&) const { y[r] = y_r; }
+  struct St {};
+  __device__ St pre(int64_t) const { return {}; }
+  __device__ void post(int64_t r, T y_r, const St&, double&) const { y[r] = y_r; }
 };
 
 template <typename T>
 struct EpApplyDot {         // y_out = A x, partial += w . (A x)  (CG: p^T A p)
   T* y; const T* w;
   static constexpr bool kDot = true;
-  __device__ void operator()(int64_t r, T y_r, double& acc) const { y[r] = y_r; acc += (double)w[r] * (double)y_r; }
+  struct St {};
+  __device__ St pre(int64_t) const { return {}; }
+  __device__ void post(int64_t r, T y_r, const St&, double& acc) const { y[r] = y_r; acc += (double)w[r] * (double)y_r; }
 };
 
 // One Chebyshev-Jacobi step (Saad, Algorithm 12.1, D^{-1}-preconditioned), with the input
@@ -99,7 +114,9 @@ template <typename T>
 struct EpCheb {
   T* x; T* r; const T* d; T* dnext; const T* dinv; T a, c;
   static constexpr bool kDot = false;
-  __device__ void operator()(int64_t i, T y_r, double&) const {
+  struct St {};
+  __device__ St pre(int64_t) const { return {}; }
+  __device__ void post(int64_t i, T y_r, const St&, double&) const {
     const T di = d[i];
     x[i] += di;
     const T rn = r[i] - y_r;
@@ -108,14 +125,11 @@ struct EpCheb {
   }
 };
 
-template <typename T, int G, bool FINE, class Ep>
+template <typename T, int G, bool FINE, class Ep, int U>
 __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __restrict__ xin, Ep ep,
                                                     double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* win = reinterpret_cast<T*>(smem_raw);
-  int32_t* s_woff = reinterpret_cast<int32_t*>(smem_raw + sizeof(T) * L.win_max);
-  int64_t* s_src = reinterpret_cast<int64_t*>(smem_raw + sizeof(T) * L.win_max +
-                                              sizeof(int32_t) * ((L.max_slots + 1 + 1) & ~1));
   __shared__ double red[8];
   constexpr int NG = 256 / G;
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
@@ -125,34 +139,30 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
     const int nn = (int)(L.nbr_ptr[B + 1] - e0);
     int W;
     int64_t r0, r1;
+    // window staging: one warp per neighbour slot, asynchronous global->shared copies
+    // (cp.async) so every element of the window is in flight at once
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
     if constexpr (FINE) {
-      for (int s = threadIdx.x; s < nn; s += blockDim.x) {
-        s_woff[s] = L.win_off[e0 + s];
-        s_src[s] = L.slot_src[e0 + s];
-      }
       W = L.win_size[B];
-      if (threadIdx.x == 0) s_woff[nn] = W;
       r0 = L.box_row[B];
       r1 = L.box_row[B + 1];
-      __syncthreads();
-      for (int k = threadIdx.x; k < W; k += blockDim.x) {
-        int lo = 0, hi = nn;  // slot s with s_woff[s] <= k < s_woff[s+1]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_woff[mid] <= k) lo = mid; else hi = mid;
-        }
-        win[k] = xin[s_src[lo] + (k - s_woff[lo])];
+      for (int s = warp; s < nn; s += 8) {
+        const int wo = L.win_off[e0 + s];
+        const int64_t src = L.slot_src[e0 + s];
+        const int len = (s + 1 < nn ? L.win_off[e0 + s + 1] : W) - wo;
+        for (int t = wl; t < len; t += 32) cp_async_elem(win + wo + t, xin + src + t);
       }
     } else {
       const int b = L.b;
       W = nn * b;
       r0 = B * b;
       r1 = r0 + b;
-      for (int k = threadIdx.x; k < W; k += blockDim.x) {
-        const int s = k / b;
-        win[k] = xin[L.nbr[e0 + s] * b + (k - s * b)];
+      for (int s = warp; s < nn; s += 8) {
+        const int64_t src = L.nbr[e0 + s] * b;
+        for (int t = wl; t < b; t += 32) cp_async_elem(win + s * b + t, xin + src + t);
       }
     }
+    cp_async_wait_all();
     const int Wp = (W + 3) & ~3;
     for (int k = W + threadIdx.x; k < Wp; k += blockDim.x) win[k] = T(0);
     __syncthreads();
@@ -163,35 +173,49 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
       const int64_t row = base + g;
       const bool ok = row < r1;
       int64_t k0 = 0, k1 = 0;
-      if (ok) { k0 = L.row_ptr[row]; k1 = L.row_ptr[row + 1]; }
+      typename Ep::St st{};
+      if (ok) {
+        k0 = L.row_ptr[row];
+        k1 = L.row_ptr[row + 1];
+        if (lane == 0) st = ep.pre(row);
+      }
       T s = T(0);
-      for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G) {
-        T v[4];
-        Vec4<T>::load(L.vals + k, v);
-        if constexpr (FINE) {
-          int ii[4];
-          load_idx4(L.idx + k, ii);
-          s += v[0] * win[ii[0]] + v[1] * win[ii[1]] + v[2] * win[ii[2]] + v[3] * win[ii[3]];
-        } else {
-          const int t = (int)(k - k0);
-          s += v[0] * win[t] + v[1] * win[t + 1] + v[2] * win[t + 2] + v[3] * win[t + 3];
+      // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
+      for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G * U) {
+        T v[U][4];
+        int ii[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t kk = k + (int64_t)u * 4 * G;
+          if (kk < k1) {
+            Vec4<T>::load(L.vals + kk, v[u]);
+            if constexpr (FINE) load_idx4(L.idx + kk, ii[u]);
+            else { const int t = (int)(kk - k0); ii[u][0] = t; ii[u][1] = t + 1; ii[u][2] = t + 2; ii[u][3] = t + 3; }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { v[u][j] = T(0); ii[u][j] = 0; }
+          }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          s += v[u][0] * win[ii[u][0]] + v[u][1] * win[ii[u][1]] + v[u][2] * win[ii[u][2]] + v[u][3] * win[ii[u][3]];
       }
       s = group_sum<G>(s);
-      if (ok && lane == 0) ep(row, s, acc);
+      if (ok && lane == 0) ep.post(row, s, st, acc);
     }
     __syncthreads();
   }
   if constexpr (Ep::kDot) {
-    const double t = block_sum(acc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    if (part != nullptr) {   // a product without a dot passes no partial buffer
+      const double t = block_sum(acc, red);
+      if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
   }
 }
 
 template <typename T>
 inline size_t level_smem_bytes(const LevelView<T>& L) {
-  return sizeof(T) * (size_t)L.win_max + sizeof(int32_t) * (size_t)((L.max_slots + 1 + 1) & ~1) +
-         sizeof(int64_t) * (size_t)(L.max_slots + 1);
+  return sizeof(T) * (size_t)L.win_max;
 }
 
 }  // namespace r3mg

@@ -12,6 +12,7 @@
 #include "kernels_dense.cuh"
 #include "kernels_krylov.cuh"
 #include "kernels_level.cuh"
+#include "kernels_level_tma.cuh"
 #include "kernels_setup.cuh"
 #include "kernels_vcycle.cuh"
 
@@ -41,6 +42,15 @@ struct Level {
   void *x = nullptr, *r = nullptr, *d[2] = {nullptr, nullptr};
   int G = 8;
   HostPattern pat;
+  // TMA-streamed kernel: work items per precision ([0] FP64, [1] FP32)
+  struct Items { unsigned char* desc = nullptr; int64_t* desc_off = nullptr; int64_t nitems = 0; int SE = 0; int rmax = 0; int dmax = 0; size_t smem = 0; int grid = 0; };
+  Items tma[2];
+  // kernel configuration per precision ([0] FP64, [1] FP32): form 0 = register-streamed,
+  // 1 = TMA-streamed; G lanes per row; nt threads per CTA (TMA form)
+  struct KConf { int form = 0; int G = 8; int nt = 256; float ms = 0.f; };
+  KConf conf[2];
+  int use_tma = 1;   // TMA work items could be built for this level
+  std::vector<int64_t> h_box_row;   // host copy of box row offsets (fine) for item building
 };
 
 }  // namespace
@@ -86,6 +96,9 @@ struct r3mg_hierarchy {
   std::vector<int64_t> prof_n;        // per kind: launches
   std::vector<double> prof_bytes;     // per kind: algorithmic bytes per launch
   int64_t launches = 0;               // kernels launched by solve-path calls
+  int* tma_err = nullptr;             // bounded-wait expiry flag of the TMA kernels
+  int nsm = 148;
+  int tma_ctas = 1;                   // TMA kernel CTAs per SM
   int64_t graph_kernels = 0;          // kernels in one replay of the V-cycle graph
 };
 
@@ -137,10 +150,14 @@ LevelView<T> view(const Level& L) {
   return v;
 }
 
+// loads in flight per lane: 4 x 16-byte steps (FP32) or 2 x 32-byte steps (FP64)
+template <typename T, bool FINE>
+constexpr int unroll_for() { return sizeof(T) == 4 ? 4 : 2; }
+
 template <typename T, int G, bool FINE, class Ep>
 void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s) {
   const size_t sm = level_smem_bytes(v);
-  auto kern = level_kernel<T, G, FINE, Ep>;
+  auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>()>;
   // opt in to more than 48 KB of dynamic shared memory per instantiation (the setup's warm-up
   // V-cycle does this before any graph capture)
   static size_t configured = 48 * 1024;
@@ -157,7 +174,7 @@ template <typename T, class Ep>
 void launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t s) {
   const LevelView<T> v = view<T>(L);
   const bool fine = (L.b == 0);
-  switch (L.G) {
+  switch (L.conf[sizeof(T) == 4 ? 1 : 0].G) {
     case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s) : launch_level_g<T, 4, false>(v, xin, ep, part, s); break;
     case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s) : launch_level_g<T, 8, false>(v, xin, ep, part, s); break;
     case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s) : launch_level_g<T, 16, false>(v, xin, ep, part, s); break;
@@ -206,6 +223,131 @@ void prof_harvest(r3mg_hierarchy* h) {
     }
   }
   h->pending.clear();
+}
+
+template <typename T, int G, bool FINE, class Ep>
+void launch_tma_g(const Level& A, const Level::Items& it, const T* xin, Ep ep, double* part, cudaStream_t s, int* err) {
+  TmaView<T> v;
+  v.L = view<T>(A);
+  v.desc = it.desc; v.desc_off = it.desc_off; v.nitems = it.nitems; v.stage_entries = it.SE; v.max_item_rows = it.rmax;
+  v.desc_max = it.dmax; v.err = err;
+  auto kern = level_kernel_tma<T, G, FINE, Ep>;
+  static size_t configured = 48 * 1024;
+  if (it.smem > configured) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)it.smem));
+    configured = it.smem;
+  }
+  kern<<<it.grid, A.conf[sizeof(T) == 4 ? 1 : 0].nt, it.smem, s>>>(v, xin, ep, part);
+  CK(cudaGetLastError());
+}
+
+template <typename T, class Ep>
+void launch_tma(const Level& A, const T* xin, Ep ep, double* part, cudaStream_t s, int* err) {
+  const Level::Items& it = A.tma[sizeof(T) == 4 ? 1 : 0];
+  const bool fine = (A.b == 0);
+  switch (A.conf[sizeof(T) == 4 ? 1 : 0].G) {
+    case 4: fine ? launch_tma_g<T, 4, true>(A, it, xin, ep, part, s, err) : launch_tma_g<T, 4, false>(A, it, xin, ep, part, s, err); break;
+    case 8: fine ? launch_tma_g<T, 8, true>(A, it, xin, ep, part, s, err) : launch_tma_g<T, 8, false>(A, it, xin, ep, part, s, err); break;
+    case 16: fine ? launch_tma_g<T, 16, true>(A, it, xin, ep, part, s, err) : launch_tma_g<T, 16, false>(A, it, xin, ep, part, s, err); break;
+    default: fine ? launch_tma_g<T, 32, true>(A, it, xin, ep, part, s, err) : launch_tma_g<T, 32, false>(A, it, xin, ep, part, s, err); break;
+  }
+}
+
+// Product y = A x (+ partial w . y) on either kernel form; partial count = grid of the kernel.
+template <typename T>
+bool tma_on(const Level& A) {
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  return A.conf[pi].form == 1 && A.tma[pi].nitems > 0;
+}
+
+template <typename T>
+int level_apply_dot(r3mg_hierarchy* h, const Level& A, const T* x, T* y, const T* w, double* part) {
+  if (tma_on<T>(A)) {
+    launch_tma<T>(A, x, TEpApplyDot<T>{y, w}, part, h->stream, h->tma_err);
+    return A.tma[sizeof(T) == 4 ? 1 : 0].grid;
+  }
+  if (w) launch_level<T>(A, x, EpApplyDot<T>{y, w}, part, h->stream);
+  else launch_level<T>(A, x, EpApply<T>{y}, part, h->stream);
+  return (int)A.nbox;
+}
+
+template <typename T>
+void level_cheb(r3mg_hierarchy* h, const Level& A, T* x, T* r, T* d, T* dn, const T* dinv, T a, T c) {
+  if (tma_on<T>(A)) launch_tma<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream, h->tma_err);
+  else launch_level<T>(A, d, EpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream);
+}
+
+// Work items of the TMA kernel: each box, split into runs of rows whose entries fit one
+// stage buffer; the stage size fills the shared memory of tma_ctas CTAs per SM.  Every item
+// gets a descriptor (entry range, window segments, local row offsets) the kernel bulk-copies.
+void build_items(r3mg_hierarchy* h, Level& A, int prec_idx, const std::vector<int64_t>& row_ptr,
+                 const std::vector<int32_t>& win_off_h, const std::vector<int64_t>& slot_src_h) {
+  const bool fine = (A.b == 0);
+  const size_t es = prec_idx == 1 ? 4 : 8;
+  auto box_rows = [&](int64_t B, int64_t& r0, int64_t& r1) {
+    r0 = fine ? A.h_box_row[B] : B * A.b;
+    r1 = fine ? A.h_box_row[B + 1] : (B + 1) * A.b;
+  };
+  int rmax = 0, nnmax = 0;
+  for (int64_t B = 0; B < A.nbox; ++B) {
+    int64_t r0, r1;
+    box_rows(B, r0, r1);
+    rmax = std::max<int>(rmax, (int)(r1 - r0));
+    nnmax = std::max<int>(nnmax, (int)(A.pat.ptr[B + 1] - A.pat.ptr[B]));
+  }
+  const int dmax = (int)((sizeof(ItemDesc) + sizeof(SegDesc) * nnmax + 4 * (rmax + 1) + 15) & ~(size_t)15);
+  const size_t budget = kMaxSmem / h->tma_ctas - 1024;
+  const size_t fixed = 128 + 3 * ((size_t)dmax + 128) + 2 * ((size_t)A.win_max * es + 128) +
+                       2 * ((size_t)kAux * rmax * es + 128) + (fine ? 2 * (32 + 128) : 0) + 256;
+  if (fixed + 2 * 1024 * (es + 2) > budget) { A.use_tma = 0; return; }
+  int SE = (int)((budget - fixed) / (2 * (es + (fine ? 2 : 0))));
+  SE = std::min(SE, 1 << 20) & ~7;
+  std::vector<unsigned char> blob;
+  std::vector<int64_t> off{0};
+  for (int64_t B = 0; B < A.nbox; ++B) {
+    int64_t r0, r1;
+    box_rows(B, r0, r1);
+    const int64_t q0 = A.pat.ptr[B], nn = A.pat.ptr[B + 1] - q0;
+    int64_t rs = r0;
+    while (rs < r1) {
+      int64_t re = rs;
+      while (re < r1 && row_ptr[re + 1] - row_ptr[rs] <= SE) ++re;
+      if (re == rs) { A.use_tma = 0; return; }   // one row longer than a stage: register kernel
+      ItemDesc hd{row_ptr[rs], row_ptr[re], rs, (int32_t)(re - rs), (int32_t)nn, 0, 0};
+      std::vector<SegDesc> seg(nn);
+      int64_t W = 0;
+      for (int64_t s = 0; s < nn; ++s) {
+        if (fine) {
+          const int64_t c = A.pat.nbr[q0 + s];
+          seg[s] = SegDesc{slot_src_h[q0 + s], win_off_h[q0 + s], (int32_t)(A.h_box_row[c + 1] - A.h_box_row[c])};
+        } else {
+          seg[s] = SegDesc{A.pat.nbr[q0 + s] * A.b, (int32_t)(s * A.b), A.b};
+        }
+        W = std::max<int64_t>(W, seg[s].wo + seg[s].len);
+      }
+      hd.W = (int32_t)W;
+      const size_t o = blob.size();
+      const size_t sz = (sizeof(ItemDesc) + sizeof(SegDesc) * nn + 4 * (re - rs + 1) + 15) & ~(size_t)15;
+      blob.resize(o + sz, 0);
+      std::memcpy(blob.data() + o, &hd, sizeof hd);
+      std::memcpy(blob.data() + o + sizeof hd, seg.data(), sizeof(SegDesc) * nn);
+      int32_t* ro = reinterpret_cast<int32_t*>(blob.data() + o + sizeof hd + sizeof(SegDesc) * nn);
+      for (int64_t rr = rs; rr <= re; ++rr) ro[rr - rs] = (int32_t)(row_ptr[rr] - row_ptr[rs]);
+      off.push_back((int64_t)blob.size());
+      rs = re;
+    }
+  }
+  Level::Items& it = A.tma[prec_idx];
+  it.nitems = (int64_t)off.size() - 1;
+  it.desc = upload(h, blob);
+  it.desc_off = upload(h, off);
+  it.SE = SE;
+  it.rmax = rmax;
+  it.dmax = dmax;
+  it.smem = fine ? (es == 4 ? TmaLayout<float, true>(SE, A.win_max, rmax, dmax).total : TmaLayout<double, true>(SE, A.win_max, rmax, dmax).total)
+                 : (es == 4 ? TmaLayout<float, false>(SE, A.win_max, rmax, dmax).total : TmaLayout<double, false>(SE, A.win_max, rmax, dmax).total);
+  if (it.smem > kMaxSmem / h->tma_ctas) { A.use_tma = 0; return; }
+  it.grid = (int)std::max<int64_t>(1, std::min<int64_t>(it.nitems, (int64_t)h->nsm * h->tma_ctas));
 }
 
 void read_status(r3mg_hierarchy* h, int& st) {
@@ -291,7 +433,7 @@ T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
     for (auto& ac : A.pre) {
       T* d = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
       const int ps = prof_begin(h, 1 + l, capturing);
-      launch_level<T>(A, d, EpCheb<T>{x, r, d, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, s);
+      level_cheb<T>(h, A, x, r, d, dn, Dinv<T>(A), (T)ac.first, (T)ac.second);
       prof_end(h, ps, capturing);
       cur[l] ^= 1;
       ++nk;
@@ -329,7 +471,7 @@ T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
     for (auto& ac : A.post) {
       T* dd = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
       const int ps = prof_begin(h, 1 + l, capturing);
-      launch_level<T>(A, dd, EpCheb<T>{x, r, dd, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, s);
+      level_cheb<T>(h, A, x, r, dd, dn, Dinv<T>(A), (T)ac.first, (T)ac.second);
       prof_end(h, ps, capturing);
       cur[l] ^= 1;
       ++nk;
@@ -397,8 +539,8 @@ void lanczos(r3mg_hierarchy* h, int l) {
   std::vector<double> al, be;
   const int steps = (int)std::min<int64_t>(h->prm.lanczos_steps, n);
   for (int j = 0; j < steps; ++j) {
-    launch_level<double>(A, p, EpApplyDot<double>{q, p}, h->part_a, s);
-    const double pq = reduce_read(h, h->part_a, (int)A.nbox, S_TMP);
+    const int npq = level_apply_dot<double>(h, A, p, q, p, h->part_a);
+    const double pq = reduce_read(h, h->part_a, npq, S_TMP);
     const double alpha = rz / pq;
     k_axpy<<<gv, 256, 0, s>>>(-alpha, q, r, n);
     k_jacobi_dot<<<gv, 256, 0, s>>>(A.dinv64, r, z, n, h->part_a);
@@ -462,6 +604,56 @@ void dense_coarsest(r3mg_hierarchy* h) {
   CK(cudaFree(D)); CK(cudaFree(Li));
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)D), h->allocs.end());
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)Li), h->allocs.end());
+}
+
+// Autotuner: times one fused level step (or the FP64 product for the fine level of the mixed
+// solver) for every candidate kernel shape and keeps the fastest.  Candidates: the
+// register-streamed kernel with 4..32 lanes per row, and the TMA-streamed kernel with 8..32
+// lanes per row and 256, 512 or 1024 threads per CTA.
+template <typename T>
+void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  cudaStream_t s = h->stream;
+  T *x, *r, *d, *dn;
+  if (product) { x = (T*)h->cb; r = (T*)h->cz; d = (T*)h->cp; dn = nullptr; }
+  else { x = (T*)A.x; r = (T*)A.r; d = (T*)A.d[0]; dn = (T*)A.d[1]; }
+  const int64_t nb = A.n * (int64_t)sizeof(T);
+  CK(cudaMemsetAsync(x, 0, nb, s)); CK(cudaMemsetAsync(r, 0, nb, s)); CK(cudaMemsetAsync(d, 0, nb, s));
+  if (dn) CK(cudaMemsetAsync(dn, 0, nb, s));
+  const bool fine = (A.b == 0);
+  std::vector<Level::KConf> cand;
+  for (int G : {4, 8, 16, 32}) {
+    if (fine && G == 32) continue;
+    if (!fine && G < 16) continue;
+    cand.push_back({0, G, 256, 0.f});
+    if (A.tma[pi].nitems > 0)
+      for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f});
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
+  Level::KConf best = A.conf[pi];
+  float best_ms = 1e30f;
+  for (auto& c : cand) {
+    A.conf[pi] = c;
+    auto once = [&] {
+      if (product) level_apply_dot<T>(h, A, x, r, d, h->part_a);
+      else level_cheb<T>(h, A, x, r, d, dn, Dinv<T>(A), T(0), T(0));
+    };
+    once();
+    CK(cudaEventRecord(e0, s));
+    for (int k = 0; k < 3; ++k) once();
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= 3.f;
+    if (ms < best_ms) { best_ms = ms; best = c; best.ms = ms; }
+  }
+  CK(cudaEventDestroy(e0)); CK(cudaEventDestroy(e1));
+  A.conf[pi] = best;
+  int terr = 0;
+  CK(cudaMemcpy(&terr, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (terr) throw Fail{R3MG_E_TIMEOUT, "autotuner: a bounded wait of the TMA-streamed kernel expired"};
 }
 
 // Numeric setup from CSR values on the device (setup and r3mg_update_values).
@@ -571,13 +763,22 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
     F.max_slots = ms;
     F.win_max = (lay.win_max + 3) & ~3;
     F.row_ptr = upload(h, lay.row_ptr);
+    lay.idx.resize(lay.idx.size() + 16, 0);   // bulk copies of index runs round up to 16 bytes
     F.idx = upload(h, lay.idx);
     F.stored = lay.row_ptr[h->n];
     F.nnz = lay.nnz;
     F.v64 = dalloc<double>(h, F.stored);
     F.dinv64 = dalloc<double>(h, F.n);
     F.pat = pats[1];
-    F.G = prm.group_lanes ? prm.group_lanes : auto_lanes((double)F.nnz / (double)F.n);
+    for (auto& c : F.conf) {
+      c.G = prm.group_lanes ? prm.group_lanes : auto_lanes((double)F.nnz / (double)F.n);
+      c.form = (prm.kernel_form == 2) ? 1 : 0;
+      c.nt = 512;
+    }
+    F.h_box_row = P.box_off[1];
+    F.use_tma = (prm.kernel_form != 1);
+    if (F.use_tma) build_items(h, F, 0, lay.row_ptr, lay.win_off, ss);
+    if (F.use_tma && prm.precision == 1) build_items(h, F, 1, lay.row_ptr, lay.win_off, ss);
     h->src = upload(h, lay.src);
     h->diag_src = upload(h, lay.diag_src);
     h->perm = upload(h, P.perm);
@@ -617,7 +818,14 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
     C.v64 = dalloc<double>(h, C.stored);
     CK(cudaMemsetAsync(C.v64, 0, sizeof(double) * C.stored, s));
     C.dinv64 = dalloc<double>(h, C.n);
-    C.G = prm.group_lanes ? prm.group_lanes : auto_lanes((double)C.nnz / (double)C.n);
+    for (auto& c : C.conf) {
+      c.G = prm.group_lanes ? prm.group_lanes : auto_lanes((double)C.nnz / (double)C.n);
+      c.form = (prm.kernel_form == 2) ? 1 : 0;
+      c.nt = 512;
+    }
+    C.use_tma = (prm.kernel_form != 1);
+    if (C.use_tma) build_items(h, C, 0, rp, {}, {});
+    if (C.use_tma && prm.precision == 1 && l + 1 < L) build_items(h, C, 1, rp, {}, {});
   }
   // ---- transfers (geometry only: computed once)
   GLLTable g{};
@@ -699,6 +907,13 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
   numeric(h, dvals);
   CK(cudaFree(dvals));
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)dvals), h->allocs.end());
+  if (prm.kernel_form == 0) {
+    for (int l = 0; l + 1 < L; ++l) {
+      if (prm.precision == 1) autotune_level<float>(h, h->lv[l], false);
+      else autotune_level<double>(h, h->lv[l], false);
+    }
+    if (prm.precision == 1) autotune_level<double>(h, h->lv[0], true);   // the FP64 CG product
+  }
   // one direct V-cycle so every kernel instantiation is configured before graph capture
   CK(cudaMemsetAsync(h->cb, 0, sizeof(double) * h->n, s));
   if (prm.precision == 1) vcycle_apply<float>(h, h->cb, h->cz, false);
@@ -742,9 +957,8 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
   const int64_t n = h->n;
   const bool fcg = (h->prm.precision == 1);
   const int gv = grid_for(n);
-  const int nb0 = (int)F.nbox;
   auto true_residual = [&](double& rr, double* bb) {
-    launch_level<double>(F, h->cx, EpApply<double>{h->cq}, nullptr, s);
+    level_apply_dot<double>(h, F, h->cx, h->cq, nullptr, nullptr);
     k_residual<<<gv, 256, 0, s>>>(h->cb, h->cq, h->cr, n, h->part_a, bb ? h->part_b : nullptr);
     CK(cudaGetLastError());
     rr = reduce_read(h, h->part_a, gv, S_RR);
@@ -778,7 +992,7 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
       if (!h->cg_slot.e0) { CK(cudaEventCreate(&h->cg_slot.e0)); CK(cudaEventCreate(&h->cg_slot.e1)); }
       CK(cudaEventRecord(h->cg_slot.e0, s));
     }
-    launch_level<double>(F, h->cp, EpApplyDot<double>{h->cq, h->cp}, h->part_a, s);
+    const int nb0 = level_apply_dot<double>(h, F, h->cp, h->cq, h->cp, h->part_a);
     if (h->prof_on) { CK(cudaEventRecord(h->cg_slot.e1, s)); h->cg_pending = true; }
     h->launches += 3;   // product, reduction, update
     reduce_dev(h, h->part_a, nb0, S_PQ, fcg ? FIN_ALPHA_FCG : FIN_ALPHA_PCG);
@@ -832,6 +1046,7 @@ void r3mg_default_params(r3mg_params* p) {
   if (!p) return;
   p->leaf_size = 64; p->pprime = 1; p->levels = 3; p->cheb_degree = 3; p->sweeps = 2; p->lanczos_steps = 10;
   p->eig_safety = 1.1; p->eig_ratio = 30.0; p->precision = 0; p->group_lanes = 0; p->seed = 0x5EED;
+  p->kernel_form = 0;
 }
 
 r3mg_status r3mg_partition(int64_t n, int dim, const double* coords_host, int leaf_size, int levels, int64_t* perm_out,
@@ -865,7 +1080,8 @@ r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int6
   for (int a = 0; a < dim; ++a) b *= (p.pprime + 1);
   if (p.pprime < 0 || p.pprime > 8 || b > 64 || p.leaf_size < b || p.levels < 2 || p.cheb_degree < 1 || p.sweeps < 1 ||
       p.lanczos_steps < 1 || !(p.eig_safety > 0) || !(p.eig_ratio > 1) || (p.precision != 0 && p.precision != 1) ||
-      (p.group_lanes != 0 && p.group_lanes != 4 && p.group_lanes != 8 && p.group_lanes != 16 && p.group_lanes != 32)) {
+      (p.group_lanes != 0 && p.group_lanes != 4 && p.group_lanes != 8 && p.group_lanes != 16 && p.group_lanes != 32) ||
+      p.kernel_form < 0 || p.kernel_form > 2) {
     g_last_error = "setup: invalid parameters (need 0 <= p' <= 8, (p'+1)^d <= 64, leaf >= (p'+1)^d, levels >= 2, "
                    "degree >= 1, sweeps >= 1, lanes in {0,4,8,16,32}, precision in {0,1})";
     delete h;
@@ -878,7 +1094,12 @@ r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int6
     CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     CK(cudaMallocHost(&h->host_scal, sizeof(double) * 16));
     h->status = dalloc<int>(h, 1);
+    h->tma_err = dalloc<int>(h, 1);
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
     StreamJoin j(h, stream);
     build(h, coords_host, rowptr_host, colidx_host, vals_host);
     CK(cudaStreamSynchronize(h->stream));
@@ -932,6 +1153,12 @@ r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, doub
     h->launches += 3;
     CK(cudaStreamSynchronize(h->stream));
     prof_harvest(h);
+    int terr = 0;
+    CK(cudaMemcpy(&terr, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (terr) {
+      CK(cudaMemset(h->tma_err, 0, sizeof(int)));
+      throw Fail{R3MG_E_TIMEOUT, "a bounded wait of the TMA-streamed level kernel expired"};
+    }
   });
   if (iters_out) *iters_out = it;
   if (relres_out) *relres_out = rel;
@@ -966,10 +1193,10 @@ r3mg_status r3mg_level_apply(r3mg_hierarchy* h, int level, const double* x_dev, 
     if (level == 0) {
       const int gv = grid_for(h->n);
       k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(x_dev, h->perm, h->cb, h->n);
-      launch_level<double>(A, h->cb, EpApply<double>{h->cz}, nullptr, h->stream);
+      level_apply_dot<double>(h, A, h->cb, h->cz, nullptr, nullptr);
       k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cz, h->perm, y_dev, h->n);
     } else {
-      launch_level<double>(A, x_dev, EpApply<double>{y_dev}, nullptr, h->stream);
+      level_apply_dot<double>(h, A, x_dev, y_dev, nullptr, nullptr);
     }
     CK(cudaGetLastError());
   });
@@ -1074,6 +1301,18 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
       }
     }
   });
+}
+
+r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
+                               float* tuned_ms) {
+  if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
+  const Level::KConf& c = h->lv[level].conf[fp32 ? 1 : 0];
+  const bool tma = c.form == 1 && h->lv[level].tma[fp32 ? 1 : 0].nitems > 0;
+  if (form) *form = tma ? 1 : 0;
+  if (lanes) *lanes = c.G;
+  if (threads) *threads = tma ? c.nt : 256;
+  if (tuned_ms) *tuned_ms = c.ms;
+  return R3MG_OK;
 }
 
 const char* r3mg_last_error(const r3mg_hierarchy* h) { return h ? h->err.c_str() : g_last_error.c_str(); }

@@ -156,6 +156,20 @@ class Hierarchy:
         _check(lib().r3mg_info(self._h, None, None, _p(n), _p(nnz), _p(nb), _p(lam)), self._h)
         return {"levels": L.value, "depth": D.value, "n": n, "nnz": nnz, "nbox": nb, "lam_hi": lam}
 
+    def kernel_config(self) -> list:
+        """Per level: the level-operator kernel chosen for FP64 and FP32 (form, lanes, threads, tuned ms)."""
+        out = []
+        for lev in range(self.levels):
+            row = {}
+            for fp32, key in ((0, "f64"), (1, "f32")):
+                f = ctypes.c_int(0); g = ctypes.c_int(0); t = ctypes.c_int(0); ms = ctypes.c_float(0)
+                _check(lib().r3mg_kernel_config(self._h, lev, fp32, ctypes.byref(f), ctypes.byref(g), ctypes.byref(t),
+                                                ctypes.byref(ms)), self._h)
+                row[key] = {"form": "tma" if f.value else "register", "lanes": g.value, "threads": t.value,
+                            "tuned_ms": round(ms.value, 5)}
+            out.append(row)
+        return out
+
     def agglomerates(self, level: int) -> np.ndarray:
         out = np.empty(self.n, np.int64)
         _check(lib().r3mg_get_agglomerates(self._h, int(level), _p(out)), self._h)

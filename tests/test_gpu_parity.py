@@ -145,3 +145,15 @@ def test_initial_guess_and_zero_rhs(pair):
     if xs is not None:
         x, it, rel = H.pcg(torch.tensor(P.b, device="cuda"), x0=torch.tensor(xs, device="cuda"), rtol=1e-8)
         assert it == 0
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_kernel_forms_match_oracle(pair, form):
+    """Both level-operator kernels (register-streamed, TMA-streamed) give the oracle's V-cycle."""
+    P, params, H, Ho = pair
+    Hf = _hier(P, dict(params, kernel_form=form))
+    r = np.random.default_rng(7).standard_normal(P.n)
+    z = Hf.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    ref = O.vcycle(Ho, r)
+    assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+    Hf.close()
