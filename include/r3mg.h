@@ -193,7 +193,9 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
                               int64_t* kernel_launches);
 
 /* Level-operator kernel chosen for level l and precision (fp32 = 0: FP64, 1: FP32):
- * form 0 = register-streamed, 1 = TMA-streamed; lanes per matrix row; threads per CTA;
+ * form 0 = register-streamed, 1 = TMA-streamed, 2 = register-streamed persistent with a
+ * double-buffered window, 3 = register-streamed with a bulk L2 prefetch of each box's matrix
+ * slice; lanes per matrix row; threads per CTA;
  * the autotuner's measured time of one launch (0 when not tuned).  Any output may be NULL. */
 r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
                                float* tuned_ms);

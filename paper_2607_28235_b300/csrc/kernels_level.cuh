@@ -28,8 +28,9 @@ struct LevelView {
   const uint16_t* idx = nullptr;      // fine: window index per entry
   const T* vals = nullptr;
   const T* dinv = nullptr;
-  int max_slots = 0;                  // largest neighbour count (shared-memory slot cache)
+  int max_slots = 0;                  // largest neighbour count
   int win_max = 0;                    // largest window (padded to 4)
+  int max_box_rows = 0;               // rows of the largest box (own-row staging)
 };
 
 template <typename T>
@@ -63,6 +64,18 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// L2 prefetch of a contiguous range by the copy engine (no registers, no shared memory);
+// start and size are rounded to the 16-byte granularity the instruction requires
+__device__ __forceinline__ void bulk_prefetch_l2(const void* base, int64_t begin_byte, int64_t end_byte) {
+  const int64_t a = begin_byte & ~(int64_t)15;
+  const int64_t z = (end_byte + 15) & ~(int64_t)15;
+  if (z > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"((const char*)base + a), "r"((uint32_t)(z - a))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 template <int G, typename T>
 __device__ __forceinline__ T group_sum(T v) {
@@ -88,64 +101,70 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Each gets (row, y = (A x)_row) from the group leader; `acc` is a per-thread partial sum
 // folded into one value per CTA written to `part[blockIdx.x]` when the epilogue wants it.
 
-// Each epilogue loads the row's own vector entries in pre() -- issued before the row's matrix
-// stream so their latency overlaps it -- and finishes the row in post().
-template <typename T>
-struct EpApply {            // y_out = A x
-  T* y;
-  static constexpr bool kDot = false;
-  struct St {};
-  __device__ St pre(int64_t) const { return {}; }
-  __device__ void post(int64_t r, T y_r, const St&, double&) const { y[r] = y_r; }
-};
+// Epilogues.  Each names up to kAuxMax own-row vectors (src(j), staged when stage(j)); the
+// kernels copy them into shared memory with the window, and post() finishes a row from the
+// staged values: aux[j][lr] is vector j at local row lr of the box (or item).
+constexpr int kAuxMax = 4;
 
 template <typename T>
-struct EpApplyDot {         // y_out = A x, partial += w . (A x)  (CG: p^T A p)
+struct TEpApplyDot {     // y = A x, and partial += w . y when w is given
   T* y; const T* w;
   static constexpr bool kDot = true;
-  struct St {};
-  __device__ St pre(int64_t) const { return {}; }
-  __device__ void post(int64_t r, T y_r, const St&, double& acc) const { y[r] = y_r; acc += (double)w[r] * (double)y_r; }
+  static constexpr int kStage = 1;
+  __device__ const T* src(int) const { return w; }
+  __device__ bool stage(int) const { return w != nullptr; }
+  __device__ void post(int64_t r, int lr, T y_r, T* const* aux, double& acc) const {
+    y[r] = y_r;
+    if (w) acc += (double)aux[0][lr] * (double)y_r;
+  }
 };
 
 // One Chebyshev-Jacobi step (Saad, Algorithm 12.1, D^{-1}-preconditioned), with the input
 // window being the current update d:  x += d;  r -= A d;  d' = a d + c D^{-1} r.
 template <typename T>
-struct EpCheb {
+struct TEpCheb {
   T* x; T* r; const T* d; T* dnext; const T* dinv; T a, c;
   static constexpr bool kDot = false;
-  struct St {};
-  __device__ St pre(int64_t) const { return {}; }
-  __device__ void post(int64_t i, T y_r, const St&, double&) const {
-    const T di = d[i];
-    x[i] += di;
-    const T rn = r[i] - y_r;
+  static constexpr int kStage = 4;
+  __device__ const T* src(int j) const { return j == 0 ? x : j == 1 ? r : j == 2 ? d : dinv; }
+  __device__ bool stage(int) const { return true; }
+  __device__ void post(int64_t i, int lr, T y_r, T* const* aux, double&) const {
+    const T di = aux[2][lr];
+    x[i] = aux[0][lr] + di;
+    const T rn = aux[1][lr] - y_r;
     r[i] = rn;
-    dnext[i] = a * di + c * dinv[i] * rn;
+    dnext[i] = a * di + c * aux[3][lr] * rn;
   }
 };
 
-template <typename T, int G, bool FINE, class Ep, int U>
+template <typename T, int G, bool FINE, class Ep, int U, bool PIPE, bool PF>
 __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __restrict__ xin, Ep ep,
                                                     double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* win = reinterpret_cast<T*>(smem_raw);
   __shared__ double red[8];
   constexpr int NG = 256 / G;
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
+  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
   double acc = 0.0;
-  for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
+  // window staging: one warp per neighbour slot, asynchronous global->shared copies
+  // (cp.async) so every element of the window is in flight at once
+  // the box's matrix slice is contiguous: one thread asks the copy engine to pull it into L2
+  auto prefetch = [&](int64_t B) {
+    if (threadIdx.x == 0) {
+      int64_t r0, r1;
+      if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
+      else { r0 = B * L.b; r1 = r0 + L.b; }
+      const int64_t k0 = L.row_ptr[r0], k1 = L.row_ptr[r1];
+      bulk_prefetch_l2(L.vals, k0 * (int64_t)sizeof(T), k1 * (int64_t)sizeof(T));
+      if constexpr (FINE) bulk_prefetch_l2(L.idx, k0 * 2, k1 * 2);
+    }
+  };
+  auto stage = [&](int64_t B, T* win) {
     const int64_t e0 = L.nbr_ptr[B];
     const int nn = (int)(L.nbr_ptr[B + 1] - e0);
     int W;
-    int64_t r0, r1;
-    // window staging: one warp per neighbour slot, asynchronous global->shared copies
-    // (cp.async) so every element of the window is in flight at once
-    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
     if constexpr (FINE) {
       W = L.win_size[B];
-      r0 = L.box_row[B];
-      r1 = L.box_row[B + 1];
       for (int s = warp; s < nn; s += 8) {
         const int wo = L.win_off[e0 + s];
         const int64_t src = L.slot_src[e0 + s];
@@ -155,17 +174,31 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
     } else {
       const int b = L.b;
       W = nn * b;
-      r0 = B * b;
-      r1 = r0 + b;
       for (int s = warp; s < nn; s += 8) {
         const int64_t src = L.nbr[e0 + s] * b;
         for (int t = wl; t < b; t += 32) cp_async_elem(win + s * b + t, xin + src + t);
       }
     }
-    cp_async_wait_all();
     const int Wp = (W + 3) & ~3;
     for (int k = W + threadIdx.x; k < Wp; k += blockDim.x) win[k] = T(0);
-    __syncthreads();
+    // the epilogue's own-row vectors, so no row waits on a dependent global load
+    int64_t r0, r1;
+    if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
+    else { r0 = B * L.b; r1 = r0 + L.b; }
+    T* aux = win + L.win_max;
+    const int nr = (int)(r1 - r0);
+    for (int j = 0; j < Ep::kStage; ++j) {
+      if (!ep.stage(j)) continue;
+      const T* sp = ep.src(j);
+      for (int t = threadIdx.x; t < nr; t += blockDim.x) cp_async_elem(aux + j * L.max_box_rows + t, sp + r0 + t);
+    }
+  };
+  auto compute = [&](int64_t B, const T* win) {
+    int64_t r0, r1;
+    if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
+    else { r0 = B * L.b; r1 = r0 + L.b; }
+    T* auxp[kAuxMax];
+    for (int j = 0; j < kAuxMax; ++j) auxp[j] = const_cast<T*>(win) + L.win_max + j * L.max_box_rows;
     // warp-uniform trip count: every lane of a warp runs the same iterations so the
     // group shuffles always see the full warp; rows past the box end are masked.
     const int g_first = (threadIdx.x >> 5) * (32 / G);
@@ -173,11 +206,9 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
       const int64_t row = base + g;
       const bool ok = row < r1;
       int64_t k0 = 0, k1 = 0;
-      typename Ep::St st{};
       if (ok) {
         k0 = L.row_ptr[row];
         k1 = L.row_ptr[row + 1];
-        if (lane == 0) st = ep.pre(row);
       }
       T s = T(0);
       // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
@@ -201,9 +232,34 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
           s += v[u][0] * win[ii[u][0]] + v[u][1] * win[ii[u][1]] + v[u][2] * win[ii[u][2]] + v[u][3] * win[ii[u][3]];
       }
       s = group_sum<G>(s);
-      if (ok && lane == 0) ep.post(row, s, st, acc);
+      if (ok && lane == 0) ep.post(row, (int)(row - r0), s, auxp, acc);
     }
-    __syncthreads();
+  };
+  T* win0 = reinterpret_cast<T*>(smem_raw);
+  if constexpr (!PIPE) {
+    for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
+      if (PF) prefetch(B);
+      stage(B, win0);
+      cp_async_wait_all();
+      __syncthreads();
+      compute(B, win0);
+      __syncthreads();
+    }
+  } else {
+    // persistent CTAs: the next box's window is staged while the current box computes
+    T* win1 = win0 + L.win_max + kAuxMax * L.max_box_rows;
+    int64_t B = blockIdx.x;
+    if (B < L.nbox) { if (PF) prefetch(B); stage(B, win0); }
+    cp_async_commit_group();
+    for (int k = 0; B < L.nbox; B += gridDim.x, ++k) {
+      const int64_t nxt = B + gridDim.x;
+      if (nxt < L.nbox) { if (PF) prefetch(nxt); stage(nxt, (k & 1) ? win0 : win1); }
+      cp_async_commit_group();
+      cp_async_wait_group1();
+      __syncthreads();
+      compute(B, (k & 1) ? win1 : win0);
+      __syncthreads();
+    }
   }
   if constexpr (Ep::kDot) {
     if (part != nullptr) {   // a product without a dot passes no partial buffer
@@ -214,8 +270,8 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
 }
 
 template <typename T>
-inline size_t level_smem_bytes(const LevelView<T>& L) {
-  return sizeof(T) * (size_t)L.win_max;
+inline size_t level_smem_bytes(const LevelView<T>& L) {   // one window + staged own-row vectors
+  return sizeof(T) * ((size_t)L.win_max + (size_t)kAuxMax * L.max_box_rows);
 }
 
 }  // namespace r3mg

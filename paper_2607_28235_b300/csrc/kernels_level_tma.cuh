@@ -18,7 +18,7 @@
 
 namespace r3mg {
 
-constexpr int kAux = 4;                       // own-row vectors an epilogue may stage
+constexpr int kAux = kAuxMax;                 // own-row vectors an epilogue may stage
 constexpr long long kWaitCycles = 2000000000LL;  // bounded mbarrier wait (~1 s at 2 GHz)
 
 // Per-item descriptor, built on the host and bulk-copied to shared memory two items ahead:
@@ -92,37 +92,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// ---------------------------------------------------------------- epilogues (staged form)
-// aux[j] points at the item's staged copy of own-row vector j (index: row - first row).
-template <typename T>
-struct TEpApplyDot {     // y = A x, and partial += w . y when w is given
-  T* y; const T* w;
-  static constexpr bool kDot = true;
-  static constexpr int kStage = 1;
-  __device__ const T* src(int) const { return w; }
-  __device__ bool stage(int) const { return w != nullptr; }
-  __device__ void post(int64_t r, int lr, T y_r, T* const* aux, double& acc) const {
-    y[r] = y_r;
-    if (w) acc += (double)aux[0][lr] * (double)y_r;
-  }
-};
-
-template <typename T>
-struct TEpCheb {         // x += d;  r -= A d;  d' = a d + c D^{-1} r
-  T* x; T* r; const T* d; T* dnext; const T* dinv; T a, c;
-  static constexpr bool kDot = false;
-  static constexpr int kStage = 4;
-  __device__ const T* src(int j) const { return j == 0 ? x : j == 1 ? r : j == 2 ? d : dinv; }
-  __device__ bool stage(int) const { return true; }
-  __device__ void post(int64_t i, int lr, T y_r, T* const* aux, double&) const {
-    const T di = aux[2][lr];
-    x[i] = aux[0][lr] + di;
-    const T rn = aux[1][lr] - y_r;
-    r[i] = rn;
-    dnext[i] = a * di + c * aux[3][lr] * rn;
-  }
-};
 
 template <typename T, bool FINE>
 struct TmaLayout {  // shared-memory carve-up (byte offsets), shared by host and device

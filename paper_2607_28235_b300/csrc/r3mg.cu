@@ -30,7 +30,7 @@ struct Level {
           *pair_box = nullptr;
   int32_t *win_off = nullptr, *win_size = nullptr;
   uint16_t* idx = nullptr;
-  int max_slots = 0, win_max = 0;
+  int max_slots = 0, win_max = 0, max_box_rows = 0;
   int64_t stored = 0, nnz = 0, npairs = 0;
   double* v64 = nullptr;
   float* v32 = nullptr;
@@ -47,7 +47,10 @@ struct Level {
   Items tma[2];
   // kernel configuration per precision ([0] FP64, [1] FP32): form 0 = register-streamed,
   // 1 = TMA-streamed; G lanes per row; nt threads per CTA (TMA form)
+  // form 0 = register, 1 = TMA-streamed, 2 = register persistent (double-buffered window),
+  // 3 = register with an L2 bulk prefetch of each box's matrix slice
   struct KConf { int form = 0; int G = 8; int nt = 256; float ms = 0.f; };
+  int nsm = 148;
   KConf conf[2];
   int use_tma = 1;   // TMA work items could be built for this level
   std::vector<int64_t> h_box_row;   // host copy of box row offsets (fine) for item building
@@ -146,7 +149,7 @@ LevelView<T> view(const Level& L) {
   v.win_size = L.win_size; v.row_ptr = L.row_ptr; v.idx = L.idx;
   if constexpr (sizeof(T) == 8) { v.vals = (const T*)L.v64; v.dinv = (const T*)L.dinv64; }
   else { v.vals = (const T*)L.v32; v.dinv = (const T*)L.dinv32; }
-  v.max_slots = L.max_slots; v.win_max = L.win_max;
+  v.max_slots = L.max_slots; v.win_max = L.win_max; v.max_box_rows = L.max_box_rows;
   return v;
 }
 
@@ -155,9 +158,37 @@ template <typename T, bool FINE>
 constexpr int unroll_for() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <typename T, int G, bool FINE, class Ep>
-void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s) {
+void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
+                    int pf) {
+  if (pf) {
+    const size_t sm = level_smem_bytes(v);
+    auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>(), false, true>;
+    static size_t configured = 48 * 1024;
+    if (sm > configured) {
+      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      configured = sm;
+    }
+    kern<<<(int)std::max<int64_t>(1, v.nbox), 256, sm, s>>>(v, xin, ep, part);
+    CK(cudaGetLastError());
+    return;
+  }
+  if (pipe) {
+    // persistent form: two windows per CTA, grid sized to the CTAs that fit the SMs
+    const size_t sm = 2 * level_smem_bytes(v);
+    auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>(), true, false>;
+    static size_t configured = 48 * 1024;
+    if (sm > configured) {
+      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      configured = sm;
+    }
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (kMaxSmem + 1024) / (sm + 1024)));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(v.nbox, (int64_t)nsm * per_sm));
+    kern<<<grid, 256, sm, s>>>(v, xin, ep, part);
+    CK(cudaGetLastError());
+    return;
+  }
   const size_t sm = level_smem_bytes(v);
-  auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>()>;
+  auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>(), false, false>;
   // opt in to more than 48 KB of dynamic shared memory per instantiation (the setup's warm-up
   // V-cycle does this before any graph capture)
   static size_t configured = 48 * 1024;
@@ -171,15 +202,21 @@ void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cu
 }
 
 template <typename T, class Ep>
-void launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t s) {
+int launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t s) {
   const LevelView<T> v = view<T>(L);
   const bool fine = (L.b == 0);
-  switch (L.conf[sizeof(T) == 4 ? 1 : 0].G) {
-    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s) : launch_level_g<T, 4, false>(v, xin, ep, part, s); break;
-    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s) : launch_level_g<T, 8, false>(v, xin, ep, part, s); break;
-    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s) : launch_level_g<T, 16, false>(v, xin, ep, part, s); break;
-    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s) : launch_level_g<T, 32, false>(v, xin, ep, part, s); break;
+  const Level::KConf& c = L.conf[sizeof(T) == 4 ? 1 : 0];
+  const int pipe = (c.form == 2), pf = (c.form == 3), nsm = L.nsm;
+  switch (c.G) {
+    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
+    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
+    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
+    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 32, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
   }
+  if (!pipe) return (int)std::max<int64_t>(1, v.nbox);
+  const size_t sm = 2 * level_smem_bytes(v);
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (kMaxSmem + 1024) / (sm + 1024)));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(v.nbox, (int64_t)nsm * per_sm));
 }
 
 // kinds: 0 = CG product (FP64 fine level), 1 + l = smoother steps on level l
@@ -257,7 +294,7 @@ void launch_tma(const Level& A, const T* xin, Ep ep, double* part, cudaStream_t 
 template <typename T>
 bool tma_on(const Level& A) {
   const int pi = sizeof(T) == 4 ? 1 : 0;
-  return A.conf[pi].form == 1 && A.tma[pi].nitems > 0;
+  return A.conf[pi].form == 1 && A.tma[pi].nitems > 0;   // form 0 / 2: register kernel
 }
 
 template <typename T>
@@ -266,15 +303,13 @@ int level_apply_dot(r3mg_hierarchy* h, const Level& A, const T* x, T* y, const T
     launch_tma<T>(A, x, TEpApplyDot<T>{y, w}, part, h->stream, h->tma_err);
     return A.tma[sizeof(T) == 4 ? 1 : 0].grid;
   }
-  if (w) launch_level<T>(A, x, EpApplyDot<T>{y, w}, part, h->stream);
-  else launch_level<T>(A, x, EpApply<T>{y}, part, h->stream);
-  return (int)A.nbox;
+  return launch_level<T>(A, x, TEpApplyDot<T>{y, w}, part, h->stream);
 }
 
 template <typename T>
 void level_cheb(r3mg_hierarchy* h, const Level& A, T* x, T* r, T* d, T* dn, const T* dinv, T a, T c) {
   if (tma_on<T>(A)) launch_tma<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream, h->tma_err);
-  else launch_level<T>(A, d, EpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream);
+  else launch_level<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream);
 }
 
 // Work items of the TMA kernel: each box, split into runs of rows whose entries fit one
@@ -626,6 +661,8 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
     if (fine && G == 32) continue;
     if (!fine && G < 16) continue;
     cand.push_back({0, G, 256, 0.f});
+    if (2 * level_smem_bytes(view<T>(A)) <= kMaxSmem) cand.push_back({2, G, 256, 0.f});
+    cand.push_back({3, G, 256, 0.f});
     if (A.tma[pi].nitems > 0)
       for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f});
   }
@@ -762,6 +799,8 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
     F.npairs = (int64_t)pb.size();
     F.max_slots = ms;
     F.win_max = (lay.win_max + 3) & ~3;
+    for (int64_t B = 0; B < F.nbox; ++B)
+      F.max_box_rows = std::max<int>(F.max_box_rows, (int)(P.box_off[1][B + 1] - P.box_off[1][B]));
     F.row_ptr = upload(h, lay.row_ptr);
     lay.idx.resize(lay.idx.size() + 16, 0);   // bulk copies of index runs round up to 16 bytes
     F.idx = upload(h, lay.idx);
@@ -813,6 +852,7 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
     C.npairs = (int64_t)pb.size();
     C.max_slots = ms;
     C.win_max = (ms * b + 3) & ~3;
+    C.max_box_rows = b;
     C.stored = rp[C.n];
     C.nnz = (int64_t)pt.nbr.size() * b * b;
     C.v64 = dalloc<double>(h, C.stored);
@@ -827,6 +867,7 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
     if (C.use_tma) build_items(h, C, 0, rp, {}, {});
     if (C.use_tma && prm.precision == 1 && l + 1 < L) build_items(h, C, 1, rp, {}, {});
   }
+  for (auto& A : h->lv) A.nsm = h->nsm;
   // ---- transfers (geometry only: computed once)
   GLLTable g{};
   g.pp = prm.pprime;
@@ -1308,7 +1349,7 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
   const Level::KConf& c = h->lv[level].conf[fp32 ? 1 : 0];
   const bool tma = c.form == 1 && h->lv[level].tma[fp32 ? 1 : 0].nitems > 0;
-  if (form) *form = tma ? 1 : 0;
+  if (form) *form = tma ? 1 : (c.form == 2 || c.form == 3 ? c.form : 0);
   if (lanes) *lanes = c.G;
   if (threads) *threads = tma ? c.nt : 256;
   if (tuned_ms) *tuned_ms = c.ms;

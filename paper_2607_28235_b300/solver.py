@@ -165,7 +165,8 @@ class Hierarchy:
                 f = ctypes.c_int(0); g = ctypes.c_int(0); t = ctypes.c_int(0); ms = ctypes.c_float(0)
                 _check(lib().r3mg_kernel_config(self._h, lev, fp32, ctypes.byref(f), ctypes.byref(g), ctypes.byref(t),
                                                 ctypes.byref(ms)), self._h)
-                row[key] = {"form": "tma" if f.value else "register", "lanes": g.value, "threads": t.value,
+                row[key] = {"form": ["register", "tma", "register_persistent", "register_l2_prefetch"][f.value], "lanes": g.value,
+                            "threads": t.value,
                             "tuned_ms": round(ms.value, 5)}
             out.append(row)
         return out
