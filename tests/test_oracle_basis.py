@@ -49,3 +49,12 @@ def test_box_basis_reproduces_qpprime(d, pp):
     for alpha in np.ndindex(*([nb1] * d)):
         f = lambda y: np.prod(y ** np.array(alpha), axis=1)
         assert np.allclose(phi @ f(nodes), f(x), atol=1e-12)
+
+
+def test_splitmix64_published_outputs():
+    """splitmix64 (Steele, Lea, Flood 2014) from state 0 yields 0xE220A8397B1DCDAF, then
+    0x6E789E6AA1B965F4; the oracle maps each to 2 * (top 53 bits / 2^53) - 1."""
+    from oracle.rng import splitmix64_uniform
+    u = splitmix64_uniform(0, 2)
+    for v, z in zip(u, (0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4)):
+        assert v == 2.0 * ((z >> 11) / 2.0 ** 53) - 1.0
