@@ -200,6 +200,26 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
 r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
                                float* tuned_ms);
 
+/*
+ * y = A x on the fine level (the product of r3mg_level_apply with level 0), without any
+ * device allocation.  For callers that cannot call cudaMalloc when they apply the operator:
+ * code recording its own CUDA graph by stream capture (an allocation cannot be captured and
+ * would break the capture), and latency-critical or memory-budgeted loops that forbid the
+ * allocator after start-up.  The paper has no counterpart; this is a library service.
+ *   x_dev, y_dev: device, n doubles, caller numbering (as r3mg_level_apply); no aliasing.
+ * Scratch: a static 16 MiB device array inside the library (two vectors of 2^20 doubles),
+ * loaded with the library on every GPU that uses it and kept until the process exits.
+ * Limits: n <= 2^20 (1,048,576 DoFs), else R3MG_E_LIMIT and nothing is launched.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make this first call before any stream
+ * capture.  Nothing in the scratch needs clearing: every call overwrites the n entries it
+ * reads.  All calls share the one array, which keeps the last call's contents, so calls
+ * whose work overlaps on the GPU (other streams, other threads, other hierarchies on the
+ * same device) race and must be serialised by the caller.  Asynchronous on `stream`.
+ * Errors: R3MG_E_ARG, R3MG_E_LIMIT, R3MG_E_CUDA.
+ */
+r3mg_status r3mg_level0_apply_noalloc(r3mg_hierarchy* h, const double* x_dev, double* y_dev, void* stream);
+
 /* Message of the last failure on h (or of the last failed r3mg_setup /
  * r3mg_partition in this thread when h is NULL).  Never NULL. */
 const char* r3mg_last_error(const r3mg_hierarchy* h);

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1370,6 +1371,46 @@ void r3mg_destroy(r3mg_hierarchy* h) {
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+// ---------------------------------------------------------------- allocation-free product
+// Scratch of r3mg_level0_apply_noalloc: the caller-numbered input and output permuted into
+// tree order.  It lives in the library image, so every GPU that loads the library holds it
+// (16 MiB) until the process exits; no call ever allocates it.
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 20;
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxN];
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_addr[256] = {};   // device address of the scratch, per device ordinal
+
+r3mg_status r3mg_level0_apply_noalloc(r3mg_hierarchy* h, const double* x_dev, double* y_dev, void* stream) {
+  if (!h || !x_dev || !y_dev) return R3MG_E_ARG;
+  if (h->n > kNoAllocMaxN) {
+    h->err = "level0_apply_noalloc: n = " + std::to_string(h->n) + " exceeds the static scratch limit of " +
+             std::to_string(kNoAllocMaxN) + " DoFs";
+    return R3MG_E_LIMIT;
+  }
+  return guarded(h, [&] {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) throw Fail{R3MG_E_ARG, "level0_apply_noalloc: device ordinal out of range"};
+    double* scratch = nullptr;
+    {
+      // first call on a device: look up the device address of the static array (host code
+      // may not use the symbol itself as a device pointer)
+      std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+      if (!g_noalloc_addr[dev]) CK(cudaGetSymbolAddress((void**)&g_noalloc_addr[dev], g_noalloc_scratch));
+      scratch = g_noalloc_addr[dev];
+    }
+    double* xt = scratch;                  // x in tree order
+    double* yt = scratch + kNoAllocMaxN;   // y in tree order
+    StreamJoin j(h, stream);
+    const int gv = grid_for(h->n);
+    k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(x_dev, h->perm, xt, h->n);
+    CK(cudaGetLastError());
+    level_apply_dot<double>(h, h->lv[0], xt, yt, nullptr, nullptr);
+    k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(yt, h->perm, y_dev, h->n);
+    CK(cudaGetLastError());
+  });
 }
 
 }  // extern "C"
