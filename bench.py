@@ -222,6 +222,13 @@ def run_ours(args):
     t0 = time.perf_counter()
     Hd = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, **_hparams(w, 0))
     setup_fp64_s = time.perf_counter() - t0
+    if args.kernel_config:
+        cfg = json.load(open(args.kernel_config))
+        Hm.set_kernel_config(cfg["mixed"])
+        Hd.set_kernel_config(cfg["fp64"])
+    if args.save_config:
+        os.makedirs(os.path.dirname(os.path.abspath(args.save_config)), exist_ok=True)
+        json.dump({"mixed": Hm.kernel_config(), "fp64": Hd.kernel_config()}, open(args.save_config, "w"))
     info = Hm.info()
     b = torch.tensor(P.b, device=dev)
     stream = torch.cuda.current_stream()
@@ -330,6 +337,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--save-config", default=None, help="write the autotuned kernel configuration (JSON)")
+    ap.add_argument("--kernel-config", default=None, help="replay a saved kernel configuration (JSON)")
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small: the 24^3 instance used for ncu captures (not a bench line)")
     args = ap.parse_args()

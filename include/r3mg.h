@@ -220,6 +220,12 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
  */
 r3mg_status r3mg_level0_apply_noalloc(r3mg_hierarchy* h, const double* x_dev, double* y_dev, void* stream);
 
+/* Pin the level-operator kernel of level l and precision (fp32 = 1 needs an FP32 V-cycle):
+ * form 0..3 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads in {256, 512,
+ * 1024} (used by the TMA form).  Replays a configuration chosen earlier (reproducible timing
+ * and profiling).  Errors: R3MG_E_ARG for an unsupported combination.  Synchronises. */
+r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads);
+
 /* Message of the last failure on h (or of the last failed r3mg_setup /
  * r3mg_partition in this thread when h is NULL).  Never NULL. */
 const char* r3mg_last_error(const r3mg_hierarchy* h);

@@ -31,6 +31,7 @@ struct LevelView {
   int max_slots = 0;                  // largest neighbour count
   int win_max = 0;                    // largest window (padded to 4)
   int max_box_rows = 0;               // rows of the largest box (own-row staging)
+  const int32_t* row_order = nullptr; // fine: per box, local rows longest first (balances the groups)
 };
 
 template <typename T>
@@ -203,8 +204,9 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
     // group shuffles always see the full warp; rows past the box end are masked.
     const int g_first = (threadIdx.x >> 5) * (32 / G);
     for (int64_t base = r0; base + g_first < r1; base += NG) {
-      const int64_t row = base + g;
-      const bool ok = row < r1;
+      const bool ok = base + g < r1;
+      // rows are taken longest first (host-built order) so the groups finish together
+      const int64_t row = (FINE && L.row_order && ok) ? r0 + L.row_order[base + g] : base + g;
       int64_t k0 = 0, k1 = 0;
       if (ok) {
         k0 = L.row_ptr[row];

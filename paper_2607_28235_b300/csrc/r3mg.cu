@@ -32,6 +32,7 @@ struct Level {
   int32_t *win_off = nullptr, *win_size = nullptr;
   uint16_t* idx = nullptr;
   int max_slots = 0, win_max = 0, max_box_rows = 0;
+  int32_t* row_order = nullptr;   // fine level: per box, local row indices by decreasing length
   int64_t stored = 0, nnz = 0, npairs = 0;
   double* v64 = nullptr;
   float* v32 = nullptr;
@@ -151,6 +152,7 @@ LevelView<T> view(const Level& L) {
   if constexpr (sizeof(T) == 8) { v.vals = (const T*)L.v64; v.dinv = (const T*)L.dinv64; }
   else { v.vals = (const T*)L.v32; v.dinv = (const T*)L.dinv32; }
   v.max_slots = L.max_slots; v.win_max = L.win_max; v.max_box_rows = L.max_box_rows;
+  v.row_order = L.row_order;
   return v;
 }
 
@@ -800,8 +802,16 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
     F.npairs = (int64_t)pb.size();
     F.max_slots = ms;
     F.win_max = (lay.win_max + 3) & ~3;
-    for (int64_t B = 0; B < F.nbox; ++B)
-      F.max_box_rows = std::max<int>(F.max_box_rows, (int)(P.box_off[1][B + 1] - P.box_off[1][B]));
+    std::vector<int32_t> ord(h->n);
+    for (int64_t B = 0; B < F.nbox; ++B) {
+      const int64_t r0 = P.box_off[1][B], r1 = P.box_off[1][B + 1];
+      F.max_box_rows = std::max<int>(F.max_box_rows, (int)(r1 - r0));
+      for (int64_t k = r0; k < r1; ++k) ord[k] = (int32_t)(k - r0);
+      std::stable_sort(ord.begin() + r0, ord.begin() + r1, [&](int32_t a, int32_t c) {
+        return lay.row_ptr[r0 + a + 1] - lay.row_ptr[r0 + a] > lay.row_ptr[r0 + c + 1] - lay.row_ptr[r0 + c];
+      });
+    }
+    F.row_order = upload(h, ord);
     F.row_ptr = upload(h, lay.row_ptr);
     lay.idx.resize(lay.idx.size() + 16, 0);   // bulk copies of index runs round up to 16 bytes
     F.idx = upload(h, lay.idx);
@@ -1342,6 +1352,25 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
                             (A.b == 0 ? 0.0 : 8.0 * (double)A.npairs);
       }
     }
+  });
+}
+
+r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads) {
+  if (!h || level < 0 || level >= h->L || form < 0 || form > 3 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
+      (threads != 256 && threads != 512 && threads != 1024)) {
+    if (h) h->err = "set_kernel_config: invalid level, form (0..3), lanes (4,8,16,32) or threads (256,512,1024)";
+    return R3MG_E_ARG;
+  }
+  Level& A = h->lv[level];
+  const int pi = fp32 ? 1 : 0;
+  if (fp32 && h->prm.precision != 1) { h->err = "set_kernel_config: the hierarchy has no FP32 V-cycle"; return R3MG_E_ARG; }
+  if (form == 1 && A.tma[pi].nitems == 0) { h->err = "set_kernel_config: no TMA work items on this level"; return R3MG_E_ARG; }
+  if (form == 2 && 2 * level_smem_bytes(view<double>(A)) > kMaxSmem) { h->err = "set_kernel_config: windows too large"; return R3MG_E_ARG; }
+  return guarded(h, [&] {
+    CK(cudaStreamSynchronize(h->stream));
+    A.conf[pi] = Level::KConf{form, lanes, threads, 0.f};
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    h->graph_state = 0;   // recaptured at the next V-cycle
   });
 }
 

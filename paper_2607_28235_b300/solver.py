@@ -171,6 +171,17 @@ class Hierarchy:
             out.append(row)
         return out
 
+    def set_kernel_config(self, config: list):
+        """Replay a configuration returned by kernel_config() (same hierarchy shape)."""
+        forms = {"register": 0, "tma": 1, "register_persistent": 2, "register_l2_prefetch": 3}
+        for lev, row in enumerate(config):
+            for fp32, key in ((0, "f64"), (1, "f32")):
+                if key not in row or (fp32 and self.params["precision"] != 1):
+                    continue
+                c = row[key]
+                _check(lib().r3mg_set_kernel_config(self._h, lev, fp32, forms[c["form"]], int(c["lanes"]),
+                                                    int(c["threads"]) if c["form"] == "tma" else 256), self._h)
+
     def agglomerates(self, level: int) -> np.ndarray:
         out = np.empty(self.n, np.int64)
         _check(lib().r3mg_get_agglomerates(self._h, int(level), _p(out)), self._h)

@@ -157,3 +157,23 @@ def test_kernel_forms_match_oracle(pair, form):
     ref = O.vcycle(Ho, r)
     assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
     Hf.close()
+
+
+@pytest.mark.parametrize("form", ["register", "tma", "register_persistent", "register_l2_prefetch"])
+def test_set_kernel_config_each_form(pair, form):
+    """Every kernel form, pinned through r3mg_set_kernel_config, gives the oracle's V-cycle and PCG."""
+    P, params, H, Ho = pair
+    Hf = _hier(P, params, precision=1)
+    cfg = Hf.kernel_config()
+    for lev, row in enumerate(cfg[:-1]):
+        for key in ("f64", "f32"):
+            row[key] = {"form": form, "lanes": row[key]["lanes"], "threads": 512}
+    try:
+        Hf.set_kernel_config(cfg[:-1])
+    except Exception as e:       # a form a level cannot host (windows too large for two buffers)
+        pytest.skip(str(e))
+    got = Hf.kernel_config()
+    assert all(got[l]["f32"]["form"] == form for l in range(len(cfg) - 1))
+    x, it, rel = Hf.pcg(torch.tensor(P.b, device="cuda"), rtol=1e-10)
+    assert np.linalg.norm(P.b - P.scipy() @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(P.b)
+    Hf.close()
