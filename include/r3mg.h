@@ -220,6 +220,19 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
  */
 r3mg_status r3mg_level0_apply_noalloc(r3mg_hierarchy* h, const double* x_dev, double* y_dev, void* stream);
 
+/*
+ * Sampled outer product on the stored pattern of A:  out[k] = alpha * lam[i] * u[j] for every
+ * stored entry k = (i, j) of the CSR given to r3mg_setup, in that CSR's order.  With
+ * alpha = -1, lam the adjoint solution (A lam = dL/du; A is symmetric so the same hierarchy
+ * solves it) and u the solution, this is dL/dA on the pattern (the gradient of a loss of
+ * u = A^{-1} b with respect to the stored values).  The paper has no adjoint; this serves
+ * differentiation through the solve.
+ *   lam_dev, u_dev: device, n doubles (caller numbering); out_dev: device, nnz doubles.
+ * Asynchronous.  Errors: R3MG_E_ARG, R3MG_E_CUDA.
+ */
+r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const double* u_dev, double alpha,
+                               double* out_dev, void* stream);
+
 /* Pin the level-operator kernel of level l and precision (fp32 = 1 needs an FP32 V-cycle):
  * form 0..3 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads in {256, 512,
  * 1024} (used by the TMA form).  Replays a configuration chosen earlier (reproducible timing

@@ -93,6 +93,7 @@ def lib():
                                     P(ctypes.c_float)]),
         "r3mg_level0_apply_noalloc": (ip, [vp, vp, vp, vp]),
         "r3mg_set_kernel_config": (ip, [vp, i32, i32, i32, i32, i32]),
+        "r3mg_sampled_outer": (ip, [vp, vp, vp, dbl, vp, vp]),
         "r3mg_last_error": (ctypes.c_char_p, [vp]),
         "r3mg_destroy": (None, [vp]),
     }

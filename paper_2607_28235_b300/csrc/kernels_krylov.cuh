@@ -160,4 +160,19 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
     y[k] += a * x[k];
 }
 
+// Sampled outer product on the stored pattern of A (the adjoint's matrix gradient):
+// out[k] = alpha * lam[i] * u[col[k]] for every entry k of row i, in the caller's CSR order.
+// One warp per row; the row's values are read once, u is gathered from L2.
+__global__ void k_sampled_outer(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ lam, const double* __restrict__ u, double alpha,
+                                double* __restrict__ out, int64_t n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w; i < n; i += nw) {
+    const double li = alpha * lam[i];
+    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) out[k] = li * u[col[k]];
+  }
+}
+
 }  // namespace r3mg

@@ -68,6 +68,8 @@ struct r3mg_hierarchy {
   std::vector<Level> lv;
   int64_t nnz_csr = 0;
   int64_t *src = nullptr, *diag_src = nullptr, *perm = nullptr;
+  int64_t* csr_rowptr = nullptr;   // the caller's CSR structure (adjoint sampled outer product)
+  int32_t* csr_col = nullptr;
   int32_t* box_of_tree = nullptr;
   double* coords_tree = nullptr;
   std::vector<double*> P64;
@@ -953,6 +955,9 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
       throw Fail{R3MG_E_LIMIT, "level " + std::to_string(l) + " window needs " + std::to_string(need) +
                                    " bytes of shared memory (> 227 KB): use a smaller leaf_size"};
   }
+  // ---- the caller's CSR structure, for the sampled outer product of the adjoint
+  h->csr_rowptr = upload(h, std::vector<int64_t>(rowptr, rowptr + h->n + 1));
+  h->csr_col = upload(h, std::vector<int32_t>(colidx, colidx + h->nnz_csr));
   // ---- numeric setup from the caller's values
   double* dvals = dalloc<double>(h, h->nnz_csr);
   CK(cudaMemcpyAsync(dvals, vals, sizeof(double) * h->nnz_csr, cudaMemcpyHostToDevice, s));
@@ -1352,6 +1357,17 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
                             (A.b == 0 ? 0.0 : 8.0 * (double)A.npairs);
       }
     }
+  });
+}
+
+r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const double* u_dev, double alpha,
+                               double* out_dev, void* stream) {
+  if (!h || !lam_dev || !u_dev || !out_dev) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    k_sampled_outer<<<grid_for(h->n * 32), 256, 0, h->stream>>>(h->csr_rowptr, h->csr_col, lam_dev, u_dev, alpha,
+                                                                  out_dev, h->n);
+    CK(cudaGetLastError());
   });
 }
 

@@ -129,6 +129,13 @@ class Hierarchy:
         _check(lib().r3mg_level_apply(self._h, int(level), _p(x), _p(y), _stream()), self._h)
         return y
 
+    def sampled_outer(self, lam: torch.Tensor, u: torch.Tensor, alpha: float = -1.0) -> torch.Tensor:
+        """out[k] = alpha * lam[i] * u[j] on every stored entry (i, j), in the setup CSR order."""
+        lam = lam.contiguous(); u = u.contiguous()
+        out = torch.empty(self.nnz, dtype=torch.float64, device=lam.device)
+        _check(lib().r3mg_sampled_outer(self._h, _p(lam), _p(u), float(alpha), _p(out), _stream()), self._h)
+        return out
+
     # ------------------------------------------------------------------ instrumentation
     def profile(self, on: bool = True):
         _check(lib().r3mg_profile_enable(self._h, 1 if on else 0), self._h)
