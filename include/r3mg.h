@@ -234,8 +234,8 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
                                double* out_dev, void* stream);
 
 /* Pin the level-operator kernel of level l and precision (fp32 = 1 needs an FP32 V-cycle):
- * form 0..3 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads in {256, 512,
- * 1024} (used by the TMA form).  Replays a configuration chosen earlier (reproducible timing
+ * form 0..3 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads per CTA in
+ * {128, 256} for the register forms and {256, 512, 1024} for the TMA form.  Replays a configuration chosen earlier (reproducible timing
  * and profiling).  Errors: R3MG_E_ARG for an unsupported combination.  Synchronises. */
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads);
 

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
                                                     double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8];
-  constexpr int NG = 256 / G;
+  const int NG = blockDim.x / G, NW = blockDim.x >> 5;   // 128 or 256 threads
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
   const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
   double acc = 0.0;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
     int W;
     if constexpr (FINE) {
       W = L.win_size[B];
-      for (int s = warp; s < nn; s += 8) {
+      for (int s = warp; s < nn; s += NW) {
         const int wo = L.win_off[e0 + s];
         const int64_t src = L.slot_src[e0 + s];
         const int len = (s + 1 < nn ? L.win_off[e0 + s + 1] : W) - wo;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
     } else {
       const int b = L.b;
       W = nn * b;
-      for (int s = warp; s < nn; s += 8) {
+      for (int s = warp; s < nn; s += NW) {
         const int64_t src = L.nbr[e0 + s] * b;
         for (int t = wl; t < b; t += 32) cp_async_elem(win + s * b + t, xin + src + t);
       }

@@ -164,7 +164,7 @@ constexpr int unroll_for() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <typename T, int G, bool FINE, class Ep>
 void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
-                    int pf) {
+                    int pf, int nt) {
   if (pf) {
     const size_t sm = level_smem_bytes(v);
     auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>(), false, true>;
@@ -173,7 +173,7 @@ void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cu
       CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       configured = sm;
     }
-    kern<<<(int)std::max<int64_t>(1, v.nbox), 256, sm, s>>>(v, xin, ep, part);
+    kern<<<(int)std::max<int64_t>(1, v.nbox), nt, sm, s>>>(v, xin, ep, part);
     CK(cudaGetLastError());
     return;
   }
@@ -186,9 +186,9 @@ void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cu
       CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
       configured = sm;
     }
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (kMaxSmem + 1024) / (sm + 1024)));
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / nt, (kMaxSmem + 1024) / (sm + 1024)));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(v.nbox, (int64_t)nsm * per_sm));
-    kern<<<grid, 256, sm, s>>>(v, xin, ep, part);
+    kern<<<grid, nt, sm, s>>>(v, xin, ep, part);
     CK(cudaGetLastError());
     return;
   }
@@ -202,7 +202,7 @@ void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cu
     configured = sm;
   }
   const int grid = (int)std::max<int64_t>(1, v.nbox);
-  kern<<<grid, 256, sm, s>>>(v, xin, ep, part);
+  kern<<<grid, nt, sm, s>>>(v, xin, ep, part);
   CK(cudaGetLastError());
 }
 
@@ -211,16 +211,16 @@ int launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t
   const LevelView<T> v = view<T>(L);
   const bool fine = (L.b == 0);
   const Level::KConf& c = L.conf[sizeof(T) == 4 ? 1 : 0];
-  const int pipe = (c.form == 2), pf = (c.form == 3), nsm = L.nsm;
+  const int pipe = (c.form == 2), pf = (c.form == 3), nsm = L.nsm, nt = (c.nt == 128) ? 128 : 256;
   switch (c.G) {
-    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
-    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
-    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
-    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s, pipe, nsm, pf) : launch_level_g<T, 32, false>(v, xin, ep, part, s, pipe, nsm, pf); break;
+    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
+    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
+    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
+    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 32, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
   }
   if (!pipe) return (int)std::max<int64_t>(1, v.nbox);
   const size_t sm = 2 * level_smem_bytes(v);
-  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (kMaxSmem + 1024) / (sm + 1024)));
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / nt, (kMaxSmem + 1024) / (sm + 1024)));
   return (int)std::max<int64_t>(1, std::min<int64_t>(v.nbox, (int64_t)nsm * per_sm));
 }
 
@@ -665,9 +665,12 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
   for (int G : {4, 8, 16, 32}) {
     if (fine && G == 32) continue;
     if (!fine && G < 16) continue;
-    cand.push_back({0, G, 256, 0.f});
-    if (2 * level_smem_bytes(view<T>(A)) <= kMaxSmem) cand.push_back({2, G, 256, 0.f});
-    cand.push_back({3, G, 256, 0.f});
+    for (int nt : {128, 256}) {
+      if (nt / G < 2) continue;
+      cand.push_back({0, G, nt, 0.f});
+      if (2 * level_smem_bytes(view<T>(A)) <= kMaxSmem) cand.push_back({2, G, nt, 0.f});
+      cand.push_back({3, G, nt, 0.f});
+    }
     if (A.tma[pi].nitems > 0)
       for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f});
   }
@@ -1373,8 +1376,8 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
 
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads) {
   if (!h || level < 0 || level >= h->L || form < 0 || form > 3 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
-      (threads != 256 && threads != 512 && threads != 1024)) {
-    if (h) h->err = "set_kernel_config: invalid level, form (0..3), lanes (4,8,16,32) or threads (256,512,1024)";
+      (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || (form == 1 && threads == 128)) {
+    if (h) h->err = "set_kernel_config: invalid level, form (0..3), lanes (4,8,16,32) or threads (128 register forms only, 256, 512, 1024)";
     return R3MG_E_ARG;
   }
   Level& A = h->lv[level];
@@ -1397,7 +1400,7 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
   const bool tma = c.form == 1 && h->lv[level].tma[fp32 ? 1 : 0].nitems > 0;
   if (form) *form = tma ? 1 : (c.form == 2 || c.form == 3 ? c.form : 0);
   if (lanes) *lanes = c.G;
-  if (threads) *threads = tma ? c.nt : 256;
+  if (threads) *threads = tma ? c.nt : (c.nt == 128 ? 128 : 256);
   if (tuned_ms) *tuned_ms = c.ms;
   return R3MG_OK;
 }

@@ -187,7 +187,7 @@ class Hierarchy:
                     continue
                 c = row[key]
                 _check(lib().r3mg_set_kernel_config(self._h, lev, fp32, forms[c["form"]], int(c["lanes"]),
-                                                    int(c["threads"]) if c["form"] == "tma" else 256), self._h)
+                                                    int(c["threads"])), self._h)
 
     def agglomerates(self, level: int) -> np.ndarray:
         out = np.empty(self.n, np.int64)
