@@ -110,6 +110,37 @@ r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int6
                        void* stream, r3mg_hierarchy** out);
 
 /*
+ * Batched setup: nprob independent problems (uneven sizes allowed), each with its own R-tree
+ * partition, transfers, Galerkin levels, smoother intervals and coarsest factor, stored as one
+ * block-diagonal hierarchy so that every V-cycle step of all problems is one kernel launch.
+ * The paper solves one problem at a time; batching is a serving extension of the same method.
+ *   n[k], coords_host[k], rowptr_host[k], colidx_host[k], vals_host[k]: problem k, as in
+ *   r3mg_setup (host memory; each problem in its own 0-based numbering).
+ * Vectors of batched calls are the problems' vectors concatenated in order (problem 0 first).
+ * All problems share params (dim, p', leaf size, levels ...).  The TMA kernel form is not used.
+ * Errors: as r3mg_setup; the message names the failing problem.
+ */
+r3mg_status r3mg_batch_setup(int nprob, int dim, const int64_t* n, const double* const* coords_host,
+                             const int64_t* const* rowptr_host, const int32_t* const* colidx_host,
+                             const double* const* vals_host, const r3mg_params* params, void* stream,
+                             r3mg_hierarchy** out);
+
+/*
+ * Solve every problem of a batched hierarchy: PCG with the FP64 V-cycle, flexible CG with the FP32
+ * V-cycle, per-problem scalars and stop tests (||r_k|| <= rtol ||b_k||).  After a host-launched
+ * start, the iteration loop of all problems runs as ONE CUDA graph launch whose conditional
+ * WHILE node repeats a batched iteration until every problem has stopped.
+ *   b_dev, x_dev: device, concatenated (sum of n) doubles; x in = x0, out = solution.
+ *   iters_out, relres_out (host, nprob): per-problem iterations and true relative residuals.
+ * Errors: R3MG_E_NOCONV (some problem reached maxit), R3MG_E_BREAKDOWN, R3MG_E_CUDA.
+ */
+r3mg_status r3mg_batch_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit,
+                           int* iters_out, double* relres_out, void* stream);
+
+/* Number of problems and their row offsets on level l (row_off_host: nprob + 1 entries). */
+r3mg_status r3mg_batch_offsets(const r3mg_hierarchy* h, int level, int* nprob_out, int64_t* row_off_host);
+
+/*
  * Replace the matrix values (same pattern as at setup, CSR order, device
  * memory, nnz doubles) and redo every numeric setup step: P is unchanged,
  * the Galerkin levels, smoother intervals and coarsest factor are rebuilt.
@@ -134,7 +165,8 @@ r3mg_status r3mg_vcycle(r3mg_hierarchy* h, const double* r_dev, double* z_dev, v
  *   b_dev (device, n), x_dev (device, n): in = initial guess, out = solution.
  *   iters_out: completed updates of x; relres_out: final ||r||/||b||.
  * Errors: R3MG_E_NOCONV (maxit reached; x holds the last iterate),
- *         R3MG_E_BREAKDOWN, R3MG_E_CUDA.  Synchronises the stream.
+ *         R3MG_E_BREAKDOWN, R3MG_E_CUDA, R3MG_E_ARG (batched hierarchy: use r3mg_batch_pcg).
+ *         Synchronises the stream.
  */
 r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit,
                      int* iters_out, double* relres_out, void* stream);

@@ -15,7 +15,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("Hierarchy", "partition", "default_params"):
+    if name in ("Hierarchy", "BatchHierarchy", "partition", "default_params"):
         from . import solver
         return getattr(solver, name)
     if name in ("R3MGSolve", "solve"):
@@ -24,4 +24,4 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["build", "Hierarchy", "partition", "default_params", "R3MGSolve", "solve", "R3MGError", "SO_PATH"]
+__all__ = ["build", "Hierarchy", "BatchHierarchy", "partition", "default_params", "R3MGSolve", "solve", "R3MGError", "SO_PATH"]

@@ -94,6 +94,9 @@ def lib():
         "r3mg_level0_apply_noalloc": (ip, [vp, vp, vp, vp]),
         "r3mg_set_kernel_config": (ip, [vp, i32, i32, i32, i32, i32]),
         "r3mg_sampled_outer": (ip, [vp, vp, vp, dbl, vp, vp]),
+        "r3mg_batch_setup": (ip, [i32, i32, vp, vp, vp, vp, vp, P(_Params), vp, P(vp)]),
+        "r3mg_batch_pcg": (ip, [vp, vp, vp, dbl, i32, vp, vp, vp]),
+        "r3mg_batch_offsets": (ip, [vp, i32, P(ctypes.c_int), vp]),
         "r3mg_last_error": (ctypes.c_char_p, [vp]),
         "r3mg_destroy": (None, [vp]),
     }

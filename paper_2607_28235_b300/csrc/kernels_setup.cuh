@@ -285,18 +285,20 @@ __global__ void __launch_bounds__(256) k_rap_coarse(
   }
 }
 
-// Dense copy of a block level (coarsest): D[(B,q'), (nbr_s, q)] = block value.
+// Dense copy of the boxes [B0, B0 + nbox) of a block level (coarsest of one problem):
+// D[(B,q'), (nbr_s, q)] = block value, rows and columns relative to box B0.
 __global__ void k_blocks_to_dense(const int64_t* __restrict__ nbr_ptr, const int64_t* __restrict__ nbr,
                                   const int64_t* __restrict__ row_ptr, const double* __restrict__ vals, int64_t nbox,
-                                  int b, double* D, int64_t ld) {
+                                  int b, double* D, int64_t ld, int64_t B0) {
   const int64_t nc = nbox * b;
-  for (int64_t r = blockIdx.x; r < nc; r += gridDim.x) {
+  for (int64_t rl = blockIdx.x; rl < nc; rl += gridDim.x) {
+    const int64_t r = B0 * b + rl;
     const int64_t B = r / b;
     const int64_t e0 = nbr_ptr[B], nn = nbr_ptr[B + 1] - e0;
     for (int64_t t = threadIdx.x; t < nn * b; t += blockDim.x) {
       const int64_t s = t / b;
       const int q = (int)(t - s * b);
-      D[r * ld + nbr[e0 + s] * b + q] = vals[row_ptr[r] + t];
+      D[rl * ld + (nbr[e0 + s] - B0) * b + q] = vals[row_ptr[r] + t];
     }
   }
 }

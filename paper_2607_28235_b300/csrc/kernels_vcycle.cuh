@@ -19,10 +19,10 @@ struct NextInit {
 };
 
 // Fine -> level 1: b1[B*b + q] = sum_{i in B} P0[i][q] r[i].  One CTA per box.
-template <typename T>
+template <typename T, class NX>
 __global__ void __launch_bounds__(256) k_restrict_fine(const T* __restrict__ P0, const T* __restrict__ r,
                                                        const int64_t* __restrict__ box_row, int64_t nbox, int b,
-                                                       NextInit<T> nx) {
+                                                       NX nx) {
   __shared__ T part[256];
   const int per = blockDim.x / b;   // row lanes per coefficient (b <= 256)
   const int q = threadIdx.x % b, j = threadIdx.x / b;
@@ -42,9 +42,9 @@ __global__ void __launch_bounds__(256) k_restrict_fine(const T* __restrict__ P0,
 }
 
 // Level l -> l+1 (l >= 1): b_{l+1}[B][q] = sum_{children c} sum_{q'} Pt[c][q'][q] r_l[c][q'].
-template <typename T>
+template <typename T, class NX>
 __global__ void k_restrict_coarse(const T* __restrict__ Pt, const T* __restrict__ r, int64_t nparent, int b, int fan,
-                                  NextInit<T> nx) {
+                                  NX nx) {
   const int64_t tot = nparent * b;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t B = t / b;

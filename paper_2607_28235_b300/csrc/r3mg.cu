@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <limits>
 #include <mutex>
 #include <cmath>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include "kernels_krylov.cuh"
 #include "kernels_level.cuh"
 #include "kernels_level_tma.cuh"
+#include "kernels_batch.cuh"
 #include "kernels_setup.cuh"
 #include "kernels_vcycle.cuh"
 
@@ -60,6 +62,8 @@ struct Level {
 
 }  // namespace
 
+struct r3mg_hierarchy;
+using Hier = r3mg_hierarchy;
 struct r3mg_hierarchy {
   r3mg_params prm{};
   int64_t n = 0;
@@ -104,6 +108,32 @@ struct r3mg_hierarchy {
   std::vector<double> prof_bytes;     // per kind: algorithmic bytes per launch
   int64_t launches = 0;               // kernels launched by solve-path calls
   int* tma_err = nullptr;             // bounded-wait expiry flag of the TMA kernels
+  // ---- batches of independent problems (nprob > 1): one block-diagonal hierarchy
+  int nprob = 1;
+  struct BLevel {
+    std::vector<int64_t> row_off;                 // nprob + 1 row offsets of the problems
+    int32_t* rprob = nullptr;                     // problem of every row
+    int64_t* label = nullptr;                     // index of every row inside its problem (Lanczos start)
+    int64_t *sb = nullptr, *se = nullptr;         // segments: rows of one problem, at most kSegRows
+    int* soff = nullptr;                          // nprob + 1 first segments
+    int nseg = 0;
+    double *preA = nullptr, *preC = nullptr, *postA = nullptr, *postC = nullptr;   // [step][nprob]
+    double* c0 = nullptr;                         // per problem: 1 / theta
+    std::vector<double> lam;                      // per problem: upper interval end
+    int npre = 0, npost = 0;
+  };
+  std::vector<BLevel> bl;
+  std::vector<int64_t> h_moff, h_mld, h_cof;     // coarsest blocks: offset, leading dim, row offsets
+  int64_t *d_moff = nullptr, *d_mld = nullptr, *d_cof = nullptr;
+  int64_t batch_ainv_size = 0;
+  BatchScal bs{};
+  double* seg_part = nullptr;
+  double* seg_out = nullptr;                      // nprob scratch for host reads
+  std::vector<double> h_seg;
+  cudaGraphExec_t bgraph = nullptr;
+  int bgraph_state = 0;
+  double bgraph_rtol = -1.0;
+  int bgraph_maxit = -1;
   int nsm = 148;
   int tma_ctas = 1;                   // TMA kernel CTAs per SM
   int64_t graph_kernels = 0;          // kernels in one replay of the V-cycle graph
@@ -461,7 +491,11 @@ const T* Dinv(const Level& L) {
 // d[0] = D^{-1} b / theta.  Returns the d buffer of level 0 holding the last update:
 // the result is z = x_0 + d.
 template <typename T>
+T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing);
+
+template <typename T>
 T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
+  if (!h->bl.empty()) return vcycle_body_batch<T>(h, capturing);
   cudaStream_t s = h->stream;
   const int L = h->L;
   std::vector<int> cur(L, 0);
@@ -482,9 +516,9 @@ T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
     const bool coarsest = (l + 1 == L - 1);
     NextInit<T> nx{(T*)C.r, coarsest ? nullptr : (T*)C.x, coarsest ? nullptr : (T*)C.d[0], Dinv<T>(C), (T)C.c0};
     if (l == 0)
-      k_restrict_fine<T><<<(int)std::min<int64_t>(C.nbox, 148 * 64), 256, 0, s>>>(Pmat<T>(h, 0), r, A.box_row, C.nbox, h->b, nx);
+      k_restrict_fine<T, NextInit<T>><<<(int)std::min<int64_t>(C.nbox, 148 * 64), 256, 0, s>>>(Pmat<T>(h, 0), r, A.box_row, C.nbox, h->b, nx);
     else
-      k_restrict_coarse<T><<<grid_for(C.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), r, C.nbox, h->b, h->fan, nx);
+      k_restrict_coarse<T, NextInit<T>><<<grid_for(C.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), r, C.nbox, h->b, h->fan, nx);
     CK(cudaGetLastError());
     ++nk;
   }
@@ -547,7 +581,8 @@ T* run_vcycle(r3mg_hierarchy* h) {
     h->launches += h->graph_kernels;
     for (int id : h->graph_slots) h->pending.push_back(id);
     // the body is deterministic: the result sits in d[(pre + post) % 2] of level 0
-    const int steps0 = (int)(h->lv[0].pre.size() + h->lv[0].post.size());
+    const int steps0 = !h->bl.empty() ? h->bl[0].npre + h->bl[0].npost
+                                    : (int)(h->lv[0].pre.size() + h->lv[0].post.size());
     return (T*)h->lv[0].d[steps0 & 1];
   }
   return vcycle_body<T>(h);
@@ -556,7 +591,11 @@ T* run_vcycle(r3mg_hierarchy* h) {
 template <typename T>
 void vcycle_apply(r3mg_hierarchy* h, const double* r_tree, double* z_tree, bool use_graph = true) {
   Level& F = h->lv[0];
-  k_vc_init<T><<<grid_for(h->n), 256, 0, h->stream>>>(r_tree, h->n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), (T)F.c0);
+  if (!h->bl.empty())
+    k_bvc_init<T><<<grid_for(h->n), 256, 0, h->stream>>>(r_tree, h->n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F),
+                                                         h->bl[0].c0, h->bl[0].rprob);
+  else
+    k_vc_init<T><<<grid_for(h->n), 256, 0, h->stream>>>(r_tree, h->n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), (T)F.c0);
   CK(cudaGetLastError());
   T* d = use_graph ? run_vcycle<T>(h) : vcycle_body<T>(h);
   k_vc_final_dot<T><<<grid_for(h->n), 256, 0, h->stream>>>((const T*)F.x, d, z_tree, nullptr, h->n, nullptr);
@@ -607,10 +646,11 @@ void lanczos(r3mg_hierarchy* h, int l) {
   make_schedule(A, h->prm.cheb_degree, h->prm.sweeps);
 }
 
-void dense_coarsest(r3mg_hierarchy* h) {
-  Level& C = h->lv[h->L - 1];
+// Dense Cholesky, triangular inverse and symmetric inverse of the boxes [B0, B0 + nbox) of the
+// coarsest block level, written to out (ncp x ncp, leading dimension ncp, identity padding).
+void dense_block(r3mg_hierarchy* h, Level& C, int64_t B0, int64_t nbox, double* out, int64_t ncp) {
   cudaStream_t s = h->stream;
-  const int64_t nc = h->nc, ncp = h->ncp;
+  const int64_t nc = nbox * h->b;
   const int nb = (int)(ncp / kTile);
   double* D = dalloc<double>(h, ncp * ncp);
   double* Li = dalloc<double>(h, ncp * ncp);
@@ -619,7 +659,7 @@ void dense_coarsest(r3mg_hierarchy* h) {
   std::vector<double> one(1, 1.0);
   for (int64_t i = nc; i < ncp; ++i) CK(cudaMemcpyAsync(D + i * ncp + i, one.data(), sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
-  k_blocks_to_dense<<<(int)std::min<int64_t>(nc, 65535), 256, 0, s>>>(C.nbr_ptr, C.nbr, C.row_ptr, C.v64, C.nbox, h->b, D, ncp);
+  k_blocks_to_dense<<<(int)std::min<int64_t>(nc, 65535), 256, 0, s>>>(C.nbr_ptr, C.nbr, C.row_ptr, C.v64, nbox, h->b, D, ncp, B0);
   CK(cudaGetLastError());
   for (int k = 0; k < nb; ++k) {
     k_potrf_diag<<<1, 256, 0, s>>>(D, ncp, k, Li, h->status);
@@ -637,13 +677,18 @@ void dense_coarsest(r3mg_hierarchy* h) {
     k_trtri_step<<<nb - t, 256, 0, s>>>(D, Li, ncp, t, nb);
     CK(cudaGetLastError());
   }
-  if (!h->Ainv64) h->Ainv64 = dalloc<double>(h, ncp * ncp);
-  k_lauum<<<nb * (nb + 1) / 2, 256, 0, s>>>(Li, h->Ainv64, ncp, nb);
+  k_lauum<<<nb * (nb + 1) / 2, 256, 0, s>>>(Li, out, ncp, nb);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   CK(cudaFree(D)); CK(cudaFree(Li));
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)D), h->allocs.end());
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)Li), h->allocs.end());
+}
+
+void dense_coarsest(r3mg_hierarchy* h) {
+  Level& C = h->lv[h->L - 1];
+  if (!h->Ainv64) h->Ainv64 = dalloc<double>(h, h->ncp * h->ncp);
+  dense_block(h, C, 0, C.nbox, h->Ainv64, h->ncp);
 }
 
 // Autotuner: times one fused level step (or the FP64 product for the fine level of the mixed
@@ -702,6 +747,11 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
 }
 
 // Numeric setup from CSR values on the device (setup and r3mg_update_values).
+void lanczos_batch(r3mg_hierarchy* h, int l);
+void dense_batch(r3mg_hierarchy* h);
+template <typename T>
+T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing);
+
 void numeric(r3mg_hierarchy* h, const double* vals_dev) {
   cudaStream_t s = h->stream;
   Level& F = h->lv[0];
@@ -737,8 +787,13 @@ void numeric(r3mg_hierarchy* h, const double* vals_dev) {
   }
   read_status(h, st);
   if (st) throw Fail{R3MG_E_NOT_SPD, "coarse level: non-positive diagonal entry"};
-  for (int l = 0; l + 1 < h->L; ++l) lanczos(h, l);
-  dense_coarsest(h);
+  if (!h->bl.empty()) {
+    for (int l = 0; l + 1 < h->L; ++l) lanczos_batch(h, l);
+    dense_batch(h);
+  } else {
+    for (int l = 0; l + 1 < h->L; ++l) lanczos(h, l);
+    dense_coarsest(h);
+  }
   if (h->prm.precision == 1) {
     for (int l = 0; l < h->L; ++l) {
       Level& A = h->lv[l];
@@ -747,28 +802,30 @@ void numeric(r3mg_hierarchy* h, const double* vals_dev) {
         k_convert<double, float><<<grid_for(A.n), 256, 0, s>>>(A.dinv64, A.dinv32, A.n);
       }
     }
-    k_convert<double, float><<<grid_for(h->ncp * h->ncp), 256, 0, s>>>(h->Ainv64, h->Ainv32, h->ncp * h->ncp);
+    const int64_t na = !h->bl.empty() ? h->batch_ainv_size : h->ncp * h->ncp;
+    k_convert<double, float><<<grid_for(na), 256, 0, s>>>(h->Ainv64, h->Ainv32, na);
     CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(s));
 }
 
-void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const int32_t* colidx, const double* vals) {
-  const r3mg_params& prm = h->prm;
-  const int dim = h->dim;
-  cudaStream_t s = h->stream;
-  h->b = 1;
-  for (int a = 0; a < dim; ++a) h->b *= (prm.pprime + 1);
-  h->fan = 1 << dim;
-  const int b = h->b;
+// Host analysis of one problem: CSR checks, R-tree partition, admissibility, block adjacency
+// of every level and the fine windowed layout.
+struct ProbHost {
+  HostPartition P;
+  std::vector<HostPattern> pats;
+  HostFineLayout lay;
+};
+
+void analyse_problem(const r3mg_params& prm, int dim, int b, int fan, int64_t n, const double* coords,
+                     const int64_t* rowptr, const int32_t* colidx, const double* vals, ProbHost& out) {
   Error err;
-  if (!validate_csr(h->n, rowptr, colidx, err)) throw Fail{err.status, err.msg};
-  for (int64_t k = 0; k < rowptr[h->n]; ++k)
+  if (!validate_csr(n, rowptr, colidx, err)) throw Fail{err.status, err.msg};
+  for (int64_t k = 0; k < rowptr[n]; ++k)
     if (!std::isfinite(vals[k])) throw Fail{R3MG_E_ARG, "CSR: non-finite value"};
-  if (!partition_points(h->n, dim, coords, prm.leaf_size, prm.levels, h->part, err)) throw Fail{err.status, err.msg};
-  HostPartition& P = h->part;
+  if (!partition_points(n, dim, coords, prm.leaf_size, prm.levels, out.P, err)) throw Fail{err.status, err.msg};
+  HostPartition& P = out.P;
   const int L = prm.levels;
-  h->L = L;
   // admissibility (Section 4, Remark on (m, M)): enough points and non-degenerate boxes
   for (int64_t B = 0; B < P.nbox(1); ++B) {
     if (P.box_off[1][B + 1] - P.box_off[1][B] < b)
@@ -780,13 +837,31 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
         for (int a = 0; a < dim; ++a)
           if (!(P.hi[l][B * dim + a] > P.lo[l][B * dim + a]))
             throw Fail{R3MG_E_UNISOLVENT, "level-" + std::to_string(l) + " box " + std::to_string(B) + " has zero extent"};
+  out.pats.assign(L, HostPattern());
+  fine_pattern(P, rowptr, colidx, out.pats[1]);
+  for (int l = 2; l < L; ++l) coarse_pattern(out.pats[l - 1], fan, P.nbox(l), out.pats[l]);
+  if (!fine_layout(P, out.pats[1], rowptr, colidx, out.lay, err)) throw Fail{err.status, err.msg};
+}
+
+void batch_levels_upload(r3mg_hierarchy* h);
+
+// Device structures and numeric setup from the (possibly concatenated) host analysis.
+//   coords: caller-numbered coordinates (h->n x dim); rowptr/colidx: the caller's CSR when the
+//   adjoint product is wanted (single problems), else null; vals: pieces of the caller's CSR
+//   values in order (one per problem).
+void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLayout& lay, const double* coords,
+                  const int64_t* rowptr, const int32_t* colidx,
+                  const std::vector<std::pair<const double*, int64_t>>& vals) {
+  const r3mg_params& prm = h->prm;
+  const int dim = h->dim;
+  cudaStream_t s = h->stream;
+  const int b = h->b;
+  HostPartition& P = h->part;
+  const int L = prm.levels;
+  h->L = L;
   h->lv.assign(L, Level());
-  std::vector<HostPattern> pats(L);
-  fine_pattern(P, rowptr, colidx, pats[1]);
-  for (int l = 2; l < L; ++l) coarse_pattern(pats[l - 1], h->fan, P.nbox(l), pats[l]);
-  HostFineLayout lay;
-  if (!fine_layout(P, pats[1], rowptr, colidx, lay, err)) throw Fail{err.status, err.msg};
-  h->nnz_csr = rowptr[h->n];
+  h->nnz_csr = 0;
+  for (auto& pc : vals) h->nnz_csr += pc.second;
   // ---- fine level
   {
     Level& F = h->lv[0];
@@ -831,7 +906,7 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
       c.nt = 512;
     }
     F.h_box_row = P.box_off[1];
-    F.use_tma = (prm.kernel_form != 1);
+    F.use_tma = (prm.kernel_form != 1) && h->bl.empty();
     if (F.use_tma) build_items(h, F, 0, lay.row_ptr, lay.win_off, ss);
     if (F.use_tma && prm.precision == 1) build_items(h, F, 1, lay.row_ptr, lay.win_off, ss);
     h->src = upload(h, lay.src);
@@ -879,7 +954,7 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
       c.form = (prm.kernel_form == 2) ? 1 : 0;
       c.nt = 512;
     }
-    C.use_tma = (prm.kernel_form != 1);
+    C.use_tma = (prm.kernel_form != 1) && h->bl.empty();
     if (C.use_tma) build_items(h, C, 0, rp, {}, {});
     if (C.use_tma && prm.precision == 1 && l + 1 < L) build_items(h, C, 1, rp, {}, {});
   }
@@ -945,7 +1020,7 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
       h->P32[l] = dalloc<float>(h, m);
       k_convert<double, float><<<grid_for(m), 256, 0, s>>>(h->P64[l], h->P32[l], m);
     }
-    h->Ainv32 = dalloc<float>(h, h->ncp * h->ncp);
+    h->Ainv32 = dalloc<float>(h, !h->bl.empty() ? h->batch_ainv_size : h->ncp * h->ncp);
     CK(cudaGetLastError());
   }
   // ---- shared-memory limits of the level kernels
@@ -959,11 +1034,20 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
                                    " bytes of shared memory (> 227 KB): use a smaller leaf_size"};
   }
   // ---- the caller's CSR structure, for the sampled outer product of the adjoint
-  h->csr_rowptr = upload(h, std::vector<int64_t>(rowptr, rowptr + h->n + 1));
-  h->csr_col = upload(h, std::vector<int32_t>(colidx, colidx + h->nnz_csr));
+  if (rowptr && colidx) {
+    h->csr_rowptr = upload(h, std::vector<int64_t>(rowptr, rowptr + h->n + 1));
+    h->csr_col = upload(h, std::vector<int32_t>(colidx, colidx + h->nnz_csr));
+  }
+  if (!h->bl.empty()) batch_levels_upload(h);
   // ---- numeric setup from the caller's values
   double* dvals = dalloc<double>(h, h->nnz_csr);
-  CK(cudaMemcpyAsync(dvals, vals, sizeof(double) * h->nnz_csr, cudaMemcpyHostToDevice, s));
+  {
+    int64_t o = 0;
+    for (auto& pc : vals) {
+      CK(cudaMemcpyAsync(dvals + o, pc.first, sizeof(double) * pc.second, cudaMemcpyHostToDevice, s));
+      o += pc.second;
+    }
+  }
   numeric(h, dvals);
   CK(cudaFree(dvals));
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)dvals), h->allocs.end());
@@ -979,6 +1063,17 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
   if (prm.precision == 1) vcycle_apply<float>(h, h->cb, h->cz, false);
   else vcycle_apply<double>(h, h->cb, h->cz, false);
   CK(cudaStreamSynchronize(s));
+}
+
+void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const int32_t* colidx, const double* vals) {
+  const r3mg_params& prm = h->prm;
+  h->b = 1;
+  for (int a = 0; a < h->dim; ++a) h->b *= (prm.pprime + 1);
+  h->fan = 1 << h->dim;
+  ProbHost ph;
+  analyse_problem(prm, h->dim, h->b, h->fan, h->n, coords, rowptr, colidx, vals, ph);
+  h->part = std::move(ph.P);
+  build_device(h, ph.pats, ph.lay, coords, rowptr, colidx, {{vals, rowptr[h->n]}});
 }
 
 template <typename F>
@@ -1097,6 +1192,458 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
   return R3MG_E_NOCONV;
 }
 
+
+
+// ================================================================ batches of problems
+constexpr int64_t kSegRows = 8192;
+
+// per-level batch arrays: problem of every row, in-problem index, segments, scalars
+void batch_levels_upload(r3mg_hierarchy* h) {
+  const int np = h->nprob;
+  int maxseg = 1;
+  for (int l = 0; l < h->L; ++l) {
+    auto& B = h->bl[l];
+    const int64_t n = B.row_off[np];
+    std::vector<int32_t> rp(n);
+    std::vector<int64_t> lab(n), sb, se;
+    std::vector<int> soff{0};
+    for (int q = 0; q < np; ++q) {
+      for (int64_t k = B.row_off[q]; k < B.row_off[q + 1]; ++k) { rp[k] = q; lab[k] = k - B.row_off[q]; }
+      for (int64_t k = B.row_off[q]; k < B.row_off[q + 1]; k += kSegRows) {
+        sb.push_back(k);
+        se.push_back(std::min(k + kSegRows, B.row_off[q + 1]));
+      }
+      soff.push_back((int)sb.size());
+    }
+    if (l == 0)   // fine level: the caller's index inside the problem (tree rows stay in their problem)
+      for (int64_t k = 0; k < n; ++k) lab[k] = h->part.perm[k] - B.row_off[rp[k]];
+    B.rprob = upload(h, rp);
+    B.label = upload(h, lab);
+    B.sb = upload(h, sb);
+    B.se = upload(h, se);
+    B.soff = upload(h, soff);
+    B.nseg = (int)sb.size();
+    maxseg = std::max(maxseg, B.nseg);
+  }
+  h->seg_part = dalloc<double>(h, maxseg);
+  h->seg_out = dalloc<double>(h, np);
+  h->h_seg.assign(np, 0.0);
+  BatchScal& S = h->bs;
+  S.pq = dalloc<double>(h, np); S.pr = dalloc<double>(h, np); S.zq = dalloc<double>(h, np);
+  S.rz = dalloc<double>(h, np); S.rzn = dalloc<double>(h, np); S.rr = dalloc<double>(h, np);
+  S.bb = dalloc<double>(h, np); S.alpha = dalloc<double>(h, np); S.beta = dalloc<double>(h, np);
+  S.active = dalloc<int>(h, np); S.its = dalloc<int>(h, np); S.any = dalloc<int>(h, 1); S.err = dalloc<int>(h, 1);
+  CK(cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
+  h->d_moff = upload(h, h->h_moff);
+  h->d_mld = upload(h, h->h_mld);
+  h->d_cof = upload(h, h->h_cof);
+}
+
+// per-problem dots on level l: out[q] = sum over problem q's rows of x y (y null: x x)
+template <typename T>
+void seg_dot(r3mg_hierarchy* h, int l, const T* x, const T* y, double* out) {
+  auto& B = h->bl[l];
+  k_seg_dot<T><<<std::min(B.nseg, 148 * 8), 256, 0, h->stream>>>(x, y, B.sb, B.se, B.nseg, h->seg_part);
+  k_seg_reduce<<<(h->nprob + 255) / 256, 256, 0, h->stream>>>(h->seg_part, B.soff, h->nprob, out);
+  CK(cudaGetLastError());
+}
+
+const std::vector<double>& seg_dot_read(r3mg_hierarchy* h, int l, const double* x, const double* y) {
+  seg_dot<double>(h, l, x, y, h->seg_out);
+  CK(cudaMemcpyAsync(h->h_seg.data(), h->seg_out, sizeof(double) * h->nprob, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return h->h_seg;
+}
+
+// Lanczos estimate of every problem's lambda_max(D^-1 A_l) at once (Section 6; same reading as
+// the single-problem estimate, each problem with its own CG scalars and start vector).
+void lanczos_batch(r3mg_hierarchy* h, int l) {
+  Level& A = h->lv[l];
+  auto& B = h->bl[l];
+  const int np = h->nprob;
+  const int64_t n = A.n;
+  cudaStream_t s = h->stream;
+  double *r = h->cr, *z = h->cz, *p = h->cp, *q = h->cq;
+  const int gv = grid_for(n);
+  k_splitmix_vec<<<gv, 256, 0, s>>>(h->prm.seed + (uint64_t)l, B.label, r, n);
+  k_jacobi<<<gv, 256, 0, s>>>(A.dinv64, r, z, n);
+  CK(cudaGetLastError());
+  std::vector<double> rz = seg_dot_read(h, l, r, z);
+  CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  std::vector<std::vector<double>> al(np), be(np);
+  std::vector<char> alive(np, 1);
+  std::vector<int> steps(np);
+  int maxsteps = 0;
+  for (int k = 0; k < np; ++k) {
+    steps[k] = (int)std::min<int64_t>(h->prm.lanczos_steps, B.row_off[k + 1] - B.row_off[k]);
+    maxsteps = std::max(maxsteps, steps[k]);
+  }
+  std::vector<double> sa(np), sbv(np);
+  for (int j = 0; j < maxsteps; ++j) {
+    level_apply_dot<double>(h, A, p, q, nullptr, nullptr);
+    const std::vector<double> pq = seg_dot_read(h, l, p, q);
+    for (int k = 0; k < np; ++k) sa[k] = (alive[k] && j < steps[k]) ? -(rz[k] / pq[k]) : 0.0;
+    CK(cudaMemcpyAsync(h->bs.alpha, sa.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    k_baxpy<<<gv, 256, 0, s>>>(h->bs.alpha, B.rprob, q, r, n);
+    k_jacobi<<<gv, 256, 0, s>>>(A.dinv64, r, z, n);
+    CK(cudaGetLastError());
+    const std::vector<double> rzn = seg_dot_read(h, l, r, z);
+    for (int k = 0; k < np; ++k) {
+      sbv[k] = 0.0;
+      if (!(alive[k] && j < steps[k])) continue;
+      al[k].push_back(-sa[k]);
+      const double beta = rzn[k] / rz[k];
+      be[k].push_back(beta);
+      if (rzn[k] == 0.0) { alive[k] = 0; continue; }
+      sbv[k] = beta;
+      rz[k] = rzn[k];
+    }
+    CK(cudaMemcpyAsync(h->bs.beta, sbv.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    k_bxpay<<<gv, 256, 0, s>>>(z, h->bs.beta, B.rprob, p, n);
+    CK(cudaGetLastError());
+  }
+  // per-problem interval and Chebyshev schedule
+  const int kdeg = h->prm.cheb_degree, nu = h->prm.sweeps;
+  std::vector<double> preA, preC, postA, postC, c0(np);
+  B.lam.assign(np, 0.0);
+  Level tmp;
+  for (int k = 0; k < np; ++k) {
+    const int m = (int)al[k].size();
+    std::vector<double> dg(m), off(m > 0 ? m - 1 : 0);
+    for (int j = 0; j < m; ++j) {
+      dg[j] = 1.0 / al[k][j] + (j > 0 ? be[k][j - 1] / al[k][j - 1] : 0.0);
+      if (j + 1 < m) off[j] = std::sqrt(be[k][j]) / al[k][j];
+    }
+    const double lmax = tridiag_max_eig(dg, off);
+    if (!(lmax > 0.0) || !std::isfinite(lmax))
+      throw Fail{R3MG_E_NOT_SPD, "Lanczos estimate non-positive on level " + std::to_string(l) + ", problem " + std::to_string(k)};
+    tmp.lam_hi = h->prm.eig_safety * lmax;
+    tmp.lam_lo = tmp.lam_hi / h->prm.eig_ratio;
+    make_schedule(tmp, kdeg, nu);
+    B.lam[k] = tmp.lam_hi;
+    c0[k] = tmp.c0;
+    if (k == 0) { preA.assign(tmp.pre.size() * np, 0); preC = preA; postA.assign(tmp.post.size() * np, 0); postC = postA; }
+    for (size_t st = 0; st < tmp.pre.size(); ++st) { preA[st * np + k] = tmp.pre[st].first; preC[st * np + k] = tmp.pre[st].second; }
+    for (size_t st = 0; st < tmp.post.size(); ++st) { postA[st * np + k] = tmp.post[st].first; postC[st * np + k] = tmp.post[st].second; }
+  }
+  // the level keeps problem 0's scalar schedule (step counts; reported interval)
+  A.lam_hi = B.lam[0];
+  A.lam_lo = A.lam_hi / h->prm.eig_ratio;
+  make_schedule(A, kdeg, nu);
+  B.npre = (int)A.pre.size();
+  B.npost = (int)A.post.size();
+  auto put = [&](double*& dst, const std::vector<double>& v) {
+    if (!dst) dst = dalloc<double>(h, (int64_t)v.size());
+    CK(cudaMemcpyAsync(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s));
+  };
+  put(B.preA, preA); put(B.preC, preC); put(B.postA, postA); put(B.postC, postC); put(B.c0, c0);
+  CK(cudaStreamSynchronize(s));
+}
+
+// every problem's coarsest block: Cholesky, inverse, stored at its own offset
+void dense_batch(r3mg_hierarchy* h) {
+  Level& C = h->lv[h->L - 1];
+  if (!h->Ainv64) h->Ainv64 = dalloc<double>(h, h->batch_ainv_size);
+  const int np = h->nprob;
+  const auto& ro = h->bl[h->L - 1].row_off;
+  for (int k = 0; k < np; ++k) {
+    const int64_t B0 = ro[k] / h->b, nb = (ro[k + 1] - ro[k]) / h->b;
+    dense_block(h, C, B0, nb, h->Ainv64 + h->h_moff[k], h->h_mld[k]);
+  }
+}
+
+// fused Chebyshev step with the per-problem coefficients of step st (register kernels)
+template <typename T>
+void level_cheb_b(r3mg_hierarchy* h, const Level& A, int l, T* x, T* r, T* d, T* dn, bool post, int st) {
+  auto& B = h->bl[l];
+  const int np = h->nprob;
+  const double* ta = (post ? B.postA : B.preA) + (int64_t)st * np;
+  const double* tc = (post ? B.postC : B.preC) + (int64_t)st * np;
+  launch_level<T>(A, d, TEpChebB<T>{x, r, d, dn, Dinv<T>(A), ta, tc, B.rprob}, nullptr, h->stream);
+}
+
+template <typename T>
+T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing) {
+  cudaStream_t s = h->stream;
+  const int L = h->L;
+  std::vector<int> cur(L, 0);
+  int64_t nk = 0;
+  for (int l = 0; l < L - 1; ++l) {
+    Level& A = h->lv[l];
+    T* x = (T*)A.x; T* r = (T*)A.r;
+    for (int st = 0; st < h->bl[l].npre; ++st) {
+      T* d = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      level_cheb_b<T>(h, A, l, x, r, d, dn, false, st);
+      cur[l] ^= 1;
+      ++nk;
+    }
+    Level& C = h->lv[l + 1];
+    const bool coarsest = (l + 1 == L - 1);
+    NextInitB<T> nx{(T*)C.r, coarsest ? nullptr : (T*)C.x, coarsest ? nullptr : (T*)C.d[0], Dinv<T>(C),
+                    h->bl[l + 1].c0, h->bl[l + 1].rprob};
+    if (l == 0)
+      k_restrict_fine<T, NextInitB<T>><<<(int)std::min<int64_t>(C.nbox, 148 * 64), 256, 0, s>>>(Pmat<T>(h, 0), r, A.box_row, C.nbox, h->b, nx);
+    else
+      k_restrict_coarse<T, NextInitB<T>><<<grid_for(C.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), r, C.nbox, h->b, h->fan, nx);
+    CK(cudaGetLastError());
+    ++nk;
+  }
+  {
+    Level& C = h->lv[L - 1];
+    k_block_gemv<T><<<grid_for(C.n * 32), 256, 0, s>>>(Ainv<T>(h), h->d_moff, h->d_mld, h->d_cof, h->bl[L - 1].rprob,
+                                                       (const T*)C.r, C.n, (T*)C.x);
+    CK(cudaGetLastError());
+    ++nk;
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    Level& A = h->lv[l];
+    Level& C = h->lv[l + 1];
+    const bool coarsest = (l + 1 == L - 1);
+    const T* x1 = (const T*)C.x;
+    const T* d1 = coarsest ? nullptr : (const T*)C.d[cur[l + 1]];
+    T* d = (T*)A.d[cur[l]];
+    if (l == 0)
+      k_prolong_fine<T><<<grid_for(h->n), 256, 0, s>>>(Pmat<T>(h, 0), h->box_of_tree, x1, d1, h->n, h->b, d);
+    else
+      k_prolong_coarse<T><<<grid_for(A.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), x1, d1, A.nbox, h->b, h->fan, d);
+    CK(cudaGetLastError());
+    ++nk;
+    T* x = (T*)A.x; T* r = (T*)A.r;
+    for (int st = 0; st < h->bl[l].npost; ++st) {
+      T* dd = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      level_cheb_b<T>(h, A, l, x, r, dd, dn, true, st);
+      cur[l] ^= 1;
+      ++nk;
+    }
+  }
+  if (!capturing) h->launches += nk;
+  return (T*)h->lv[0].d[cur[0]];
+}
+
+// Batched PCG (FP64 V-cycle) or flexible CG (FP32 V-cycle) on tree-ordered cb / cx.  After a
+// host-launched start (residuals, activity flags, first V-cycle entry), the whole iteration loop
+// runs as one CUDA graph launch: a conditional WHILE node repeats one batched iteration until
+// every problem has converged or reached maxit.
+template <typename T>
+r3mg_status krylov_batch(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double* relres) {
+  cudaStream_t s = h->stream;
+  Level& F = h->lv[0];
+  const int64_t n = h->n;
+  const int np = h->nprob;
+  const bool fcg = (h->prm.precision == 1);
+  const int gv = grid_for(n);
+  BatchScal& S = h->bs;
+  auto& B0 = h->bl[0];
+  std::vector<int> its_total(np, 0), done(np, 0);
+  std::vector<double> bbh(np), rel(np, 0.0);
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    // start: r = b - A x, per-problem norms, activity
+    level_apply_dot<double>(h, F, h->cx, h->cq, nullptr, nullptr);
+    k_residual<<<gv, 256, 0, s>>>(h->cb, h->cq, h->cr, n, h->part_a, nullptr);
+    CK(cudaGetLastError());
+    seg_dot<double>(h, 0, h->cb, nullptr, S.bb);
+    seg_dot<double>(h, 0, h->cr, nullptr, S.rr);
+    std::vector<double> rrh(np);
+    CK(cudaMemcpyAsync(bbh.data(), S.bb, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(rrh.data(), S.rr, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> act(np, 0);
+    int nact = 0;
+    for (int k = 0; k < np; ++k) {
+      rel[k] = bbh[k] > 0.0 ? std::sqrt(rrh[k] / bbh[k]) : 0.0;
+      act[k] = (bbh[k] > 0.0 && rel[k] > rtol && its_total[k] < maxit) ? 1 : 0;
+      nact += act[k];
+    }
+    if (nact == 0) break;
+    std::vector<int> zero(np, 0);
+    std::vector<double> ones(np, 1.0), infs(np, std::numeric_limits<double>::infinity());
+    CK(cudaMemcpyAsync(S.active, act.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(S.its, zero.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(S.pq, ones.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(S.rz, infs.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(S.zq, 0, sizeof(double) * np, s));
+    CK(cudaMemsetAsync(h->cp, 0, sizeof(double) * n, s));
+    CK(cudaMemsetAsync(h->cq, 0, sizeof(double) * n, s));
+    k_bvc_init<T><<<gv, 256, 0, s>>>(h->cr, n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), B0.c0, B0.rprob);
+    CK(cudaGetLastError());
+    const int budget = maxit - *std::min_element(its_total.begin(), its_total.end());
+    // the loop graph, captured once per (rtol, maxit)
+    if (h->bgraph_state == 1 && (h->bgraph_rtol != rtol || h->bgraph_maxit != budget)) {
+      cudaGraphExecDestroy(h->bgraph);
+      h->bgraph = nullptr;
+      h->bgraph_state = 0;
+    }
+    if (h->bgraph_state == 0) {
+      cudaGraph_t g = nullptr;
+      CK(cudaGraphCreate(&g, 0));
+      cudaGraphConditionalHandle hdl;
+      CK(cudaGraphConditionalHandleCreate(&hdl, g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = hdl;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      bool ok = true;
+      try {
+        T* d = vcycle_body_batch<T>(h, true);
+        k_bvc_final<T><<<gv, 256, 0, s>>>((const T*)F.x, d, h->cz, n);
+        if (fcg) { seg_dot<double>(h, 0, h->cz, h->cq, S.zq); k_bscal<<<(np + 255) / 256, 256, 0, s>>>(S, np, BF_BETA_FCG); }
+        else { seg_dot<double>(h, 0, h->cz, h->cr, S.rzn); k_bscal<<<(np + 255) / 256, 256, 0, s>>>(S, np, BF_BETA_PCG); }
+        k_bp_update<<<gv, 256, 0, s>>>(h->cp, h->cz, S.beta, B0.rprob, n, fcg ? 1 : 0);
+        level_apply_dot<double>(h, F, h->cp, h->cq, nullptr, nullptr);
+        seg_dot<double>(h, 0, h->cp, h->cq, S.pq);
+        if (fcg) seg_dot<double>(h, 0, h->cp, h->cr, S.pr);
+        k_bscal<<<(np + 255) / 256, 256, 0, s>>>(S, np, fcg ? BF_ALPHA_FCG : BF_ALPHA_PCG);
+        k_bcg_update<T><<<gv, 256, 0, s>>>(h->cx, h->cr, h->cp, h->cq, S.alpha, B0.rprob, n, (T*)F.r, (T*)F.x,
+                                           (T*)F.d[0], Dinv<T>(F), B0.c0);
+        seg_dot<double>(h, 0, h->cr, nullptr, S.rr);
+        k_bconverge<<<1, 1024, 0, s>>>(S, np, rtol * rtol, budget);
+        k_set_condition<<<1, 32, 0, s>>>(hdl, S.any);
+        CK(cudaGetLastError());
+      } catch (Fail&) { ok = false; }
+      cudaGraph_t cap = body;
+      const bool ended = cudaStreamEndCapture(s, &cap) == cudaSuccess;
+      if (!ok || !ended || cudaGraphInstantiate(&h->bgraph, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        throw Fail{R3MG_E_CUDA, "batched solve: the conditional loop graph could not be built"};
+      }
+      cudaGraphDestroy(g);
+      h->bgraph_state = 1;
+      h->bgraph_rtol = rtol;
+      h->bgraph_maxit = budget;
+    }
+    CK(cudaGraphLaunch(h->bgraph, s));
+    std::vector<int> itsh(np);
+    int err = 0;
+    CK(cudaMemcpyAsync(itsh.data(), S.its, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&err, S.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err) {
+      CK(cudaMemsetAsync(S.err, 0, sizeof(int), s));
+      throw Fail{R3MG_E_BREAKDOWN, "batched CG breakdown: p^T A p <= 0 or non-finite scalar"};
+    }
+    for (int k = 0; k < np; ++k) its_total[k] += itsh[k];
+  }
+  // confirmed (true) residuals
+  level_apply_dot<double>(h, F, h->cx, h->cq, nullptr, nullptr);
+  k_residual<<<gv, 256, 0, s>>>(h->cb, h->cq, h->cr, n, h->part_a, nullptr);
+  CK(cudaGetLastError());
+  const std::vector<double>& rrt = seg_dot_read(h, 0, h->cr, nullptr);
+  bool all = true;
+  for (int k = 0; k < np; ++k) {
+    relres[k] = bbh[k] > 0.0 ? std::sqrt(rrt[k] / bbh[k]) : 0.0;
+    iters[k] = its_total[k];
+    if (relres[k] > rtol) all = false;
+  }
+  return all ? R3MG_OK : R3MG_E_NOCONV;
+}
+
+void build_batch(r3mg_hierarchy* h, int np, const int64_t* n, const double* const* coords,
+                 const int64_t* const* rowptr, const int32_t* const* colidx, const double* const* vals) {
+  const r3mg_params& prm = h->prm;
+  const int dim = h->dim;
+  h->b = 1;
+  for (int a = 0; a < dim; ++a) h->b *= (prm.pprime + 1);
+  h->fan = 1 << dim;
+  h->nprob = np;
+  const int b = h->b, L = prm.levels;
+  std::vector<ProbHost> ph(np);
+  for (int k = 0; k < np; ++k) {
+    try {
+      analyse_problem(prm, dim, b, h->fan, n[k], coords[k], rowptr[k], colidx[k], vals[k], ph[k]);
+    } catch (Fail& f) {
+      throw Fail{f.st, "problem " + std::to_string(k) + ": " + f.msg};
+    }
+  }
+  // offsets of every problem at every level
+  std::vector<int64_t> row0(np + 1, 0), nnz0(np + 1, 0), st0(np + 1, 0);
+  std::vector<std::vector<int64_t>> box0(L, std::vector<int64_t>(np + 1, 0)), pat0(L, std::vector<int64_t>(np + 1, 0));
+  for (int k = 0; k < np; ++k) {
+    row0[k + 1] = row0[k] + n[k];
+    nnz0[k + 1] = nnz0[k] + rowptr[k][n[k]];
+    st0[k + 1] = st0[k] + ph[k].lay.row_ptr[n[k]];
+    for (int l = 1; l < L; ++l) {
+      box0[l][k + 1] = box0[l][k] + ph[k].P.nbox(l);
+      pat0[l][k + 1] = pat0[l][k] + (int64_t)ph[k].pats[l].nbr.size();
+    }
+  }
+  const int64_t N = row0[np];
+  h->n = N;
+  // combined partition: every problem's boxes, in problem order
+  HostPartition& P = h->part;
+  P.n = N; P.dim = dim; P.levels = L; P.depth = 0;
+  P.perm.resize(N);
+  P.iperm.resize(N);
+  P.box_off.assign(L, {});
+  P.lo.assign(L, {});
+  P.hi.assign(L, {});
+  for (int k = 0; k < np; ++k) {
+    P.depth = std::max(P.depth, ph[k].P.depth);
+    for (int64_t t = 0; t < n[k]; ++t) P.perm[row0[k] + t] = ph[k].P.perm[t] + row0[k];
+  }
+  for (int64_t t = 0; t < N; ++t) P.iperm[P.perm[t]] = t;
+  for (int l = 1; l < L; ++l) {
+    P.box_off[l].push_back(0);
+    for (int k = 0; k < np; ++k) {
+      const auto& bo = ph[k].P.box_off[l];
+      for (size_t B = 1; B < bo.size(); ++B) P.box_off[l].push_back(bo[B] + row0[k]);
+      P.lo[l].insert(P.lo[l].end(), ph[k].P.lo[l].begin(), ph[k].P.lo[l].end());
+      P.hi[l].insert(P.hi[l].end(), ph[k].P.hi[l].begin(), ph[k].P.hi[l].end());
+    }
+  }
+  // combined block adjacency
+  std::vector<HostPattern> pats(L);
+  for (int l = 1; l < L; ++l) {
+    pats[l].ptr.push_back(0);
+    for (int k = 0; k < np; ++k) {
+      const auto& pt = ph[k].pats[l];
+      for (size_t B = 1; B < pt.ptr.size(); ++B) pats[l].ptr.push_back(pt.ptr[B] + pat0[l][k]);
+      for (int64_t c : pt.nbr) pats[l].nbr.push_back(c + box0[l][k]);
+    }
+  }
+  // combined fine layout
+  HostFineLayout lay;
+  lay.row_ptr.push_back(0);
+  for (int k = 0; k < np; ++k) {
+    const HostFineLayout& a = ph[k].lay;
+    for (int64_t t = 1; t <= n[k]; ++t) lay.row_ptr.push_back(a.row_ptr[t] + st0[k]);
+    lay.idx.insert(lay.idx.end(), a.idx.begin(), a.idx.end());
+    for (int64_t v : a.src) lay.src.push_back(v >= 0 ? v + nnz0[k] : -1);
+    for (int64_t v : a.diag_src) lay.diag_src.push_back(v + nnz0[k]);
+    lay.win_off.insert(lay.win_off.end(), a.win_off.begin(), a.win_off.end());
+    lay.win_size.insert(lay.win_size.end(), a.win_size.begin(), a.win_size.end());
+    lay.win_max = std::max(lay.win_max, a.win_max);
+    lay.nnz += a.nnz;
+  }
+  std::vector<double> cc(N * dim);
+  for (int k = 0; k < np; ++k) std::memcpy(cc.data() + row0[k] * dim, coords[k], sizeof(double) * n[k] * dim);
+  // per-level problem offsets and the coarsest blocks
+  h->bl.assign(L, Hier::BLevel());
+  h->bl[0].row_off = row0;
+  for (int l = 1; l < L; ++l) {
+    h->bl[l].row_off.resize(np + 1);
+    for (int k = 0; k <= np; ++k) h->bl[l].row_off[k] = box0[l][k] * b;
+  }
+  h->h_moff.assign(np + 1, 0);
+  h->h_mld.assign(np, 0);
+  h->h_cof = h->bl[L - 1].row_off;
+  for (int k = 0; k < np; ++k) {
+    const int64_t nc = h->h_cof[k + 1] - h->h_cof[k];
+    const int64_t ncp = (nc + kTile - 1) / kTile * kTile;
+    h->h_mld[k] = ncp;
+    h->h_moff[k + 1] = h->h_moff[k] + ncp * ncp;
+  }
+  h->batch_ainv_size = h->h_moff[np];
+  std::vector<std::pair<const double*, int64_t>> pieces;
+  for (int k = 0; k < np; ++k) pieces.emplace_back(vals[k], rowptr[k][n[k]]);
+  build_device(h, pats, lay, cc.data(), nullptr, nullptr, pieces);
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -1173,6 +1720,102 @@ r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int6
   return R3MG_OK;
 }
 
+r3mg_status r3mg_batch_setup(int nprob, int dim, const int64_t* n, const double* const* coords_host,
+                             const int64_t* const* rowptr_host, const int32_t* const* colidx_host,
+                             const double* const* vals_host, const r3mg_params* params, void* stream,
+                             r3mg_hierarchy** out) {
+  if (!out) { g_last_error = "batch_setup: null output"; return R3MG_E_ARG; }
+  *out = nullptr;
+  if (nprob < 1 || (dim != 2 && dim != 3) || !n || !coords_host || !rowptr_host || !colidx_host || !vals_host) {
+    g_last_error = "batch_setup: need nprob >= 1, dim in {2,3} and non-null arrays";
+    return R3MG_E_ARG;
+  }
+  for (int k = 0; k < nprob; ++k)
+    if (n[k] < 1 || !coords_host[k] || !rowptr_host[k] || !colidx_host[k] || !vals_host[k]) {
+      g_last_error = "batch_setup: problem " + std::to_string(k) + " is empty or has a null array";
+      return R3MG_E_ARG;
+    }
+  r3mg_hierarchy* h = new (std::nothrow) r3mg_hierarchy();
+  if (!h) return R3MG_E_OOM;
+  if (params) h->prm = *params; else r3mg_default_params(&h->prm);
+  const r3mg_params& p = h->prm;
+  int b = 1;
+  for (int a = 0; a < dim; ++a) b *= (p.pprime + 1);
+  if (p.pprime < 0 || p.pprime > 8 || b > 64 || p.leaf_size < b || p.levels < 2 || p.cheb_degree < 1 || p.sweeps < 1 ||
+      p.lanczos_steps < 1 || !(p.eig_safety > 0) || !(p.eig_ratio > 1) || (p.precision != 0 && p.precision != 1) ||
+      (p.group_lanes != 0 && p.group_lanes != 4 && p.group_lanes != 8 && p.group_lanes != 16 && p.group_lanes != 32) ||
+      p.kernel_form < 0 || p.kernel_form > 2) {
+    g_last_error = "batch_setup: invalid parameters";
+    delete h;
+    return R3MG_E_ARG;
+  }
+  h->dim = dim;
+  r3mg_status st = guarded(h, [&] {
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CK(cudaMallocHost(&h->host_scal, sizeof(double) * 16));
+    h->status = dalloc<int>(h, 1);
+    h->tma_err = dalloc<int>(h, 1);
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+    StreamJoin j(h, stream);
+    build_batch(h, nprob, n, coords_host, rowptr_host, colidx_host, vals_host);
+    CK(cudaStreamSynchronize(h->stream));
+  });
+  if (st != R3MG_OK) {
+    g_last_error = h->err;
+    r3mg_destroy(h);
+    return st;
+  }
+  *out = h;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_batch_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit,
+                           int* iters_out, double* relres_out, void* stream) {
+  if (!h || !b_dev || !x_dev || maxit < 0 || !(rtol >= 0.0) || !iters_out || !relres_out) return R3MG_E_ARG;
+  if (h->bl.empty()) {
+    int it = 0; double rel = 0.0;
+    r3mg_status s1 = r3mg_pcg(h, b_dev, x_dev, rtol, maxit, &it, &rel, stream);
+    iters_out[0] = it; relres_out[0] = rel;
+    return s1;
+  }
+  r3mg_status res = R3MG_OK;
+  r3mg_status st = guarded(h, [&] {
+    StreamJoin j(h, stream);
+    const int gv = grid_for(h->n);
+    k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(b_dev, h->perm, h->cb, h->n);
+    k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(x_dev, h->perm, h->cx, h->n);
+    CK(cudaGetLastError());
+    res = (h->prm.precision == 1) ? krylov_batch<float>(h, rtol, maxit, iters_out, relres_out)
+                                  : krylov_batch<double>(h, rtol, maxit, iters_out, relres_out);
+    k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cx, h->perm, x_dev, h->n);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+  });
+  if (st != R3MG_OK) return st;
+  if (res == R3MG_E_NOCONV) h->err = "batched PCG: a problem reached maxit";
+  return res;
+}
+
+r3mg_status r3mg_batch_offsets(const r3mg_hierarchy* h, int level, int* nprob_out, int64_t* row_off_host) {
+  if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
+  if (nprob_out) *nprob_out = h->nprob;
+  if (row_off_host) {
+    if (!h->bl.empty()) {
+      std::memcpy(row_off_host, h->bl[level].row_off.data(), sizeof(int64_t) * (h->nprob + 1));
+    } else {
+      row_off_host[0] = 0;
+      row_off_host[1] = h->lv[level].n;
+    }
+  }
+  return R3MG_OK;
+}
+
 r3mg_status r3mg_update_values(r3mg_hierarchy* h, const double* vals_dev, void* stream) {
   if (!h || !vals_dev) return R3MG_E_ARG;
   return guarded(h, [&] {
@@ -1198,6 +1841,7 @@ r3mg_status r3mg_vcycle(r3mg_hierarchy* h, const double* r_dev, double* z_dev, v
 r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_out,
                      double* relres_out, void* stream) {
   if (!h || !b_dev || !x_dev || maxit < 0 || !(rtol >= 0.0)) return R3MG_E_ARG;
+  if (!h->bl.empty()) { h->err = "pcg: batched hierarchy, use r3mg_batch_pcg"; return R3MG_E_ARG; }
   int it = 0;
   double rel = 0.0;
   r3mg_status res = R3MG_OK;
@@ -1366,6 +2010,7 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
 r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const double* u_dev, double alpha,
                                double* out_dev, void* stream) {
   if (!h || !lam_dev || !u_dev || !out_dev) return R3MG_E_ARG;
+  if (!h->csr_rowptr) { h->err = "sampled_outer: not available on batched hierarchies"; return R3MG_E_ARG; }
   return guarded(h, [&] {
     StreamJoin j(h, stream);
     k_sampled_outer<<<grid_for(h->n * 32), 256, 0, h->stream>>>(h->csr_rowptr, h->csr_col, lam_dev, u_dev, alpha,
@@ -1411,6 +2056,7 @@ void r3mg_destroy(r3mg_hierarchy* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
   for (auto& sl : h->slots) { cudaEventDestroy(sl.e0); cudaEventDestroy(sl.e1); }
   if (h->cg_slot.e0) { cudaEventDestroy(h->cg_slot.e0); cudaEventDestroy(h->cg_slot.e1); }
   for (void* p : h->allocs) cudaFree(p);

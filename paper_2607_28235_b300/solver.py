@@ -216,3 +216,59 @@ class Hierarchy:
             out = np.empty((nbox, self.b, self.b), np.float64)
         _check(lib().r3mg_get_prolongation(self._h, int(level), _p(out)), self._h)
         return out
+
+
+class BatchHierarchy(Hierarchy):
+    """Many independent problems (uneven sizes) in one block-diagonal hierarchy on the device."""
+
+    def __init__(self, problems, **params):
+        """problems: sequence of (coords, rowptr, colidx, vals), each in its own numbering."""
+        p = _Params()
+        lib().r3mg_default_params(ctypes.byref(p))
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = {f: getattr(p, f) for f, _ in _Params._fields_}
+        self._keep = []
+        ns, cs, rs, ks, vs = [], [], [], [], []
+        for coords, rowptr, colidx, vals in problems:
+            x = np.ascontiguousarray(coords, dtype=np.float64)
+            rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+            ci = np.ascontiguousarray(colidx, dtype=np.int32)
+            va = np.ascontiguousarray(vals, dtype=np.float64)
+            self._keep += [x, rp, ci, va]
+            ns.append(x.shape[0]); cs.append(x.ctypes.data); rs.append(rp.ctypes.data)
+            ks.append(ci.ctypes.data); vs.append(va.ctypes.data)
+        self.dim = np.asarray(problems[0][0]).shape[1]
+        self.nprob = len(ns)
+        narr = np.asarray(ns, np.int64)
+        arr = lambda v: (ctypes.c_void_p * len(v))(*v)
+        h = ctypes.c_void_p()
+        rc = lib().r3mg_batch_setup(self.nprob, self.dim, _p(narr), arr(cs), arr(rs), arr(ks), arr(vs),
+                                    ctypes.byref(p), _stream(), ctypes.byref(h))
+        self._keep = None
+        _check(rc)
+        self._h = h
+        self.n = int(narr.sum())
+        self.sizes = narr
+        self.offsets = np.concatenate([[0], np.cumsum(narr)])
+        self.b = (p.pprime + 1) ** self.dim
+        self.levels = self.info()["levels"]
+
+    def level_offsets(self, level: int) -> np.ndarray:
+        out = np.empty(self.nprob + 1, np.int64)
+        _check(lib().r3mg_batch_offsets(self._h, int(level), None, _p(out)), self._h)
+        return out
+
+    def pcg(self, b: torch.Tensor, x0: torch.Tensor | None = None, rtol: float = 1e-8, maxit: int = 500,
+            raise_on_noconv: bool = True):
+        b = b.contiguous()
+        assert b.is_cuda and b.dtype == torch.float64 and b.numel() == self.n
+        x = torch.zeros_like(b) if x0 is None else x0.clone().contiguous()
+        its = np.zeros(self.nprob, np.int32)
+        rel = np.zeros(self.nprob, np.float64)
+        rc = lib().r3mg_batch_pcg(self._h, _p(b), _p(x), float(rtol), int(maxit), _p(its), _p(rel), _stream())
+        if rc != 0 and not (rc == 7 and not raise_on_noconv):
+            _check(rc, self._h)
+        return x, its, rel

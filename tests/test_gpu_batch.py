@@ -1,0 +1,84 @@
+"""Batched solves: independent problems of uneven size in one block-diagonal hierarchy.
+
+Every problem of the batch must behave exactly as if solved alone: agglomerates bit-exact
+against the oracle's partition of that problem, one batched V-cycle equal (1e-12 relative) to
+the oracle V-cycle of each problem, PCG iteration counts within +-1 of the oracle's and
+solutions within 1e-10 (FP64 V-cycle) or reaching the tolerance (FP32 V-cycle).  The loop of
+the batched solve is one graph launch; a second call reuses the graph and reproduces the result.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from oracle.hierarchy import Params
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(10, 1), (13, 2), (6, 4), (16, 1), (9, 3), (7, 2)]   # (N, p) of uneven 2D problems
+PRM = dict(leaf_size=24, pprime=1, levels=3, cheb_degree=3)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import paper_2607_28235_b300 as R
+    probs = [W.poisson(2, N, p, perturb=0.15, seed=100 + k) for k, (N, p) in enumerate(SPECS)]
+    rng = np.random.default_rng(9)
+    bs = [rng.standard_normal(P.n) for P in probs]
+    H = R.BatchHierarchy([(P.coords, P.rowptr, P.colidx, P.vals) for P in probs], **PRM)
+    Hm = R.BatchHierarchy([(P.coords, P.rowptr, P.colidx, P.vals) for P in probs], precision=1, **PRM)
+    orc = [O.build_hierarchy(P.coords, P.scipy(), Params(PRM["leaf_size"], PRM["pprime"], PRM["levels"],
+                                                         cheb_degree=PRM["cheb_degree"])) for P in probs]
+    return probs, bs, H, Hm, orc
+
+
+def test_offsets_and_agglomerates(batch):
+    probs, bs, H, Hm, orc = batch
+    off = H.level_offsets(0)
+    assert np.array_equal(np.diff(off), [P.n for P in probs])
+    for lev in (1, 2):
+        agg = H.agglomerates(lev)
+        boxoff = H.level_offsets(lev) // H.b
+        for k, (P, Ho) in enumerate(zip(probs, orc)):
+            assert np.array_equal(agg[off[k]:off[k + 1]] - boxoff[k], Ho.part.box_of_point[lev])
+
+
+def test_batched_vcycle_equals_each_problem(batch):
+    probs, bs, H, Hm, orc = batch
+    off = H.level_offsets(0)
+    r = np.concatenate(bs)
+    z = H.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    for k, Ho in enumerate(orc):
+        ref = O.vcycle(Ho, bs[k])
+        zk = z[off[k]:off[k + 1]]
+        assert np.linalg.norm(zk - ref) <= 1e-12 * np.linalg.norm(ref), k
+
+
+def test_batched_pcg_fp64(batch):
+    probs, bs, H, Hm, orc = batch
+    off = H.level_offsets(0)
+    b = torch.tensor(np.concatenate(bs), device="cuda")
+    x, its, rel = H.pcg(b, rtol=1e-10)
+    x = x.cpu().numpy()
+    for k, (P, Ho) in enumerate(zip(probs, orc)):
+        ref = O.pcg(P.scipy(), bs[k], lambda v: O.vcycle(Ho, v), rtol=1e-10)
+        assert abs(int(its[k]) - ref.iterations) <= 1, (k, its[k], ref.iterations)
+        xk = x[off[k]:off[k + 1]]
+        assert np.linalg.norm(xk - ref.x) <= 1e-10 * np.linalg.norm(ref.x), k
+        assert rel[k] <= 1e-10
+    x2, its2, rel2 = H.pcg(b, rtol=1e-10)
+    assert np.array_equal(x2.cpu().numpy(), x) and np.array_equal(its2, its)
+
+
+def test_batched_fcg_mixed(batch):
+    probs, bs, H, Hm, orc = batch
+    off = Hm.level_offsets(0)
+    b = torch.tensor(np.concatenate(bs), device="cuda")
+    x, its, rel = Hm.pcg(b, rtol=1e-8)
+    x = x.cpu().numpy()
+    for k, (P, Ho) in enumerate(zip(probs, orc)):
+        xk = x[off[k]:off[k + 1]]
+        assert np.linalg.norm(bs[k] - P.scipy() @ xk) <= 1e-8 * np.linalg.norm(bs[k]), k
+        ref = O.pcg(P.scipy(), bs[k], lambda v: O.vcycle(Ho, v), rtol=1e-8)
+        assert its[k] <= ref.iterations + 3
