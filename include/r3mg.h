@@ -271,6 +271,13 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
  * and profiling).  Errors: R3MG_E_ARG for an unsupported combination.  Synchronises. */
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads);
 
+/* As r3mg_set_kernel_config, with the FP64 register kernels' unroll depth: 0 = default
+ * (2 steps of 4 entries in flight per lane), 4 = four steps (FP64 only). */
+r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads, int unroll);
+
+/* The unroll depth chosen for level l and precision (0 = default, 4). */
+r3mg_status r3mg_kernel_unroll(const r3mg_hierarchy* h, int level, int fp32, int* unroll);
+
 /* Message of the last failure on h (or of the last failed r3mg_setup /
  * r3mg_partition in this thread when h is NULL).  Never NULL. */
 const char* r3mg_last_error(const r3mg_hierarchy* h);

@@ -93,6 +93,8 @@ def lib():
                                     P(ctypes.c_float)]),
         "r3mg_level0_apply_noalloc": (ip, [vp, vp, vp, vp]),
         "r3mg_set_kernel_config": (ip, [vp, i32, i32, i32, i32, i32]),
+        "r3mg_set_kernel_config2": (ip, [vp, i32, i32, i32, i32, i32, i32]),
+        "r3mg_kernel_unroll": (ip, [vp, i32, i32, P(ctypes.c_int)]),
         "r3mg_sampled_outer": (ip, [vp, vp, vp, dbl, vp, vp]),
         "r3mg_batch_setup": (ip, [i32, i32, vp, vp, vp, vp, vp, P(_Params), vp, P(vp)]),
         "r3mg_batch_pcg": (ip, [vp, vp, vp, dbl, i32, vp, vp, vp]),

@@ -167,15 +167,37 @@ bool fine_layout(const HostPartition& P, const HostPattern& pat, const int64_t* 
                  HostFineLayout& lay, Error& err) {
   const std::vector<int64_t>& off = P.box_off[1];
   const int64_t nb = P.nbox(1), n = P.n;
+  std::vector<int64_t> box_of_tree(n);
+  for (int64_t B = 0; B < nb; ++B)
+    for (int64_t k = off[B]; k < off[B + 1]; ++k) box_of_tree[k] = B;
+  // the window keeps, for each neighbour box, only the run of its points between the first and
+  // the last one referenced by a row of the box (the rest would be staged for nothing)
+  std::vector<int64_t> seg_lo(pat.nbr.size()), seg_hi(pat.nbr.size());
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t B = 0; B < nb; ++B) {
+    const int64_t* nb0 = pat.nbr.data() + pat.ptr[B];
+    const int64_t nn = pat.ptr[B + 1] - pat.ptr[B];
+    for (int64_t e = pat.ptr[B]; e < pat.ptr[B + 1]; ++e) { seg_lo[e] = INT64_MAX; seg_hi[e] = -1; }
+    for (int64_t k = off[B]; k < off[B + 1]; ++k) {
+      const int64_t i = P.perm[k];
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int64_t t = P.iperm[colidx[e]], c = box_of_tree[t];
+        const int64_t s2 = pat.ptr[B] + (std::lower_bound(nb0, nb0 + nn, c) - nb0);
+        seg_lo[s2] = std::min(seg_lo[s2], t);
+        seg_hi[s2] = std::max(seg_hi[s2], t + 1);
+      }
+    }
+  }
   lay.win_off.resize(pat.nbr.size());
+  lay.win_src.resize(pat.nbr.size());
   lay.win_size.resize(nb);
   int64_t wmax = 0;
   for (int64_t B = 0; B < nb; ++B) {
     int64_t w = 0;
     for (int64_t e = pat.ptr[B]; e < pat.ptr[B + 1]; ++e) {
       lay.win_off[e] = (int32_t)std::min<int64_t>(w, INT32_MAX);
-      const int64_t c = pat.nbr[e];
-      w += off[c + 1] - off[c];
+      lay.win_src[e] = seg_lo[e];
+      w += seg_hi[e] - seg_lo[e];
     }
     if (w > kMaxWindow) {
       err = {R3MG_E_LIMIT, "fine window of box " + std::to_string(B) + " has " + std::to_string(w) +
@@ -197,9 +219,6 @@ bool fine_layout(const HostPartition& P, const HostPattern& pat, const int64_t* 
   lay.src.assign(tot, -1);
   lay.diag_src.assign(n, -1);
   lay.nnz = rowptr[n];
-  std::vector<int64_t> box_of_tree(n);
-  for (int64_t B = 0; B < nb; ++B)
-    for (int64_t k = off[B]; k < off[B + 1]; ++k) box_of_tree[k] = B;
 #pragma omp parallel
   {
     std::vector<std::pair<int64_t, int64_t>> ent;
@@ -214,8 +233,8 @@ bool fine_layout(const HostPartition& P, const HostPattern& pat, const int64_t* 
       const int64_t nn = pat.ptr[B + 1] - pat.ptr[B];
       for (auto& pe : ent) {
         const int64_t c = box_of_tree[pe.first];
-        const int64_t s = std::lower_bound(nb0, nb0 + nn, c) - nb0;
-        lay.idx[pos] = (uint16_t)(lay.win_off[pat.ptr[B] + s] + (pe.first - off[c]));
+        const int64_t e2 = pat.ptr[B] + (std::lower_bound(nb0, nb0 + nn, c) - nb0);
+        lay.idx[pos] = (uint16_t)(lay.win_off[e2] + (pe.first - lay.win_src[e2]));
         lay.src[pos] = pe.second;
         if (pe.first == k) lay.diag_src[k] = pe.second;
         ++pos;

@@ -41,6 +41,7 @@ struct HostFineLayout {
   std::vector<int64_t> src;       // CSR position of every stored entry, -1 for padding
   std::vector<int64_t> diag_src;  // CSR position of the diagonal of each tree row
   std::vector<int32_t> win_off;   // per (box, slot): start of that neighbour's points in the window
+  std::vector<int64_t> win_src;   // per (box, slot): first tree row of the neighbour's staged run
   std::vector<int32_t> win_size;  // per box: window length
   int32_t win_max = 0;
   int64_t nnz = 0;                // stored entries without padding

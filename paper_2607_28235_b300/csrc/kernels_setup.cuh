@@ -160,7 +160,8 @@ __global__ void k_ptilde_eval(const double* __restrict__ lo_c, const double* __r
 constexpr int kRapRows = 32;
 __global__ void __launch_bounds__(256) k_rap_fine(
     const int64_t* __restrict__ pair_box, const int64_t* __restrict__ nbr_ptr, const int64_t* __restrict__ nbr,
-    const int32_t* __restrict__ win_off, const int64_t* __restrict__ box_row, const int64_t* __restrict__ row_ptr,
+    const int32_t* __restrict__ win_off, const int64_t* __restrict__ slot_src, const int32_t* __restrict__ win_size,
+    const int64_t* __restrict__ box_row, const int64_t* __restrict__ row_ptr,
     const uint16_t* __restrict__ idx, const double* __restrict__ vals, const double* __restrict__ P0, int b,
     int64_t npairs, const int64_t* __restrict__ row_ptr1, double* __restrict__ vals1) {
   extern __shared__ double sm[];
@@ -171,10 +172,10 @@ __global__ void __launch_bounds__(256) k_rap_fine(
   for (int64_t e = blockIdx.x; e < npairs; e += gridDim.x) {
     const int64_t B = pair_box[e];
     const int s = (int)(e - nbr_ptr[B]);
-    const int64_t c = nbr[e];
+    // the slot's window run: tree rows [slot_src[e], slot_src[e] + w1 - w0) of the neighbour box
     const int w0 = win_off[e];
-    const int64_t cstart = box_row[c];
-    const int w1 = w0 + (int)(box_row[c + 1] - cstart);
+    const int64_t cstart = slot_src[e];
+    const int w1 = (e + 1 < nbr_ptr[B + 1]) ? win_off[e + 1] : win_size[B];
     double acc[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) acc[u] = 0.0;

@@ -53,11 +53,12 @@ struct Level {
   // 1 = TMA-streamed; G lanes per row; nt threads per CTA (TMA form)
   // form 0 = register, 1 = TMA-streamed, 2 = register persistent (double-buffered window),
   // 3 = register with an L2 bulk prefetch of each box's matrix slice
-  struct KConf { int form = 0; int G = 8; int nt = 256; float ms = 0.f; };
+  struct KConf { int form = 0; int G = 8; int nt = 256; float ms = 0.f; int u = 0; };   // u: 0 = default unroll
   int nsm = 148;
   KConf conf[2];
   int use_tma = 1;   // TMA work items could be built for this level
   std::vector<int64_t> h_box_row;   // host copy of box row offsets (fine) for item building
+  std::vector<int32_t> h_win_size;  // host copy of the window lengths (fine) for item building
 };
 
 }  // namespace
@@ -192,12 +193,24 @@ LevelView<T> view(const Level& L) {
 template <typename T, bool FINE>
 constexpr int unroll_for() { return sizeof(T) == 4 ? 4 : 2; }
 
+template <typename T, int G, bool FINE, class Ep, int U>
+void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
+                     int pf, int nt);
+
+// FP64 rows may use 2 or 4 steps of 32 bytes in flight per lane (autotuned); FP32 uses 4 x 16 bytes
 template <typename T, int G, bool FINE, class Ep>
 void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
-                    int pf, int nt) {
+                    int pf, int nt, int u) {
+  if (sizeof(T) == 8 && u == 4) launch_level_gu<T, G, FINE, Ep, 4>(v, xin, ep, part, s, pipe, nsm, pf, nt);
+  else launch_level_gu<T, G, FINE, Ep, unroll_for<T, FINE>()>(v, xin, ep, part, s, pipe, nsm, pf, nt);
+}
+
+template <typename T, int G, bool FINE, class Ep, int U>
+void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
+                     int pf, int nt) {
   if (pf) {
     const size_t sm = level_smem_bytes(v);
-    auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>(), false, true>;
+    auto kern = level_kernel<T, G, FINE, Ep, U, false, true>;
     static size_t configured = 48 * 1024;
     if (sm > configured) {
       CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -210,7 +223,7 @@ void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cu
   if (pipe) {
     // persistent form: two windows per CTA, grid sized to the CTAs that fit the SMs
     const size_t sm = 2 * level_smem_bytes(v);
-    auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>(), true, false>;
+    auto kern = level_kernel<T, G, FINE, Ep, U, true, false>;
     static size_t configured = 48 * 1024;
     if (sm > configured) {
       CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -223,7 +236,7 @@ void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cu
     return;
   }
   const size_t sm = level_smem_bytes(v);
-  auto kern = level_kernel<T, G, FINE, Ep, unroll_for<T, FINE>(), false, false>;
+  auto kern = level_kernel<T, G, FINE, Ep, U, false, false>;
   // opt in to more than 48 KB of dynamic shared memory per instantiation (the setup's warm-up
   // V-cycle does this before any graph capture)
   static size_t configured = 48 * 1024;
@@ -241,12 +254,12 @@ int launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t
   const LevelView<T> v = view<T>(L);
   const bool fine = (L.b == 0);
   const Level::KConf& c = L.conf[sizeof(T) == 4 ? 1 : 0];
-  const int pipe = (c.form == 2), pf = (c.form == 3), nsm = L.nsm, nt = (c.nt == 128) ? 128 : 256;
+  const int pipe = (c.form == 2), pf = (c.form == 3), nsm = L.nsm, nt = (c.nt == 128) ? 128 : 256, u = c.u;
   switch (c.G) {
-    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
-    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
-    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
-    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s, pipe, nsm, pf, nt) : launch_level_g<T, 32, false>(v, xin, ep, part, s, pipe, nsm, pf, nt); break;
+    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
+    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
+    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
+    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 32, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
   }
   if (!pipe) return (int)std::max<int64_t>(1, v.nbox);
   const size_t sm = 2 * level_smem_bytes(v);
@@ -388,8 +401,8 @@ void build_items(r3mg_hierarchy* h, Level& A, int prec_idx, const std::vector<in
       int64_t W = 0;
       for (int64_t s = 0; s < nn; ++s) {
         if (fine) {
-          const int64_t c = A.pat.nbr[q0 + s];
-          seg[s] = SegDesc{slot_src_h[q0 + s], win_off_h[q0 + s], (int32_t)(A.h_box_row[c + 1] - A.h_box_row[c])};
+          const int32_t wend = (s + 1 < nn) ? win_off_h[q0 + s + 1] : A.h_win_size[B];
+          seg[s] = SegDesc{slot_src_h[q0 + s], win_off_h[q0 + s], wend - win_off_h[q0 + s]};
         } else {
           seg[s] = SegDesc{A.pat.nbr[q0 + s] * A.b, (int32_t)(s * A.b), A.b};
         }
@@ -710,14 +723,16 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
   for (int G : {4, 8, 16, 32}) {
     if (fine && G == 32) continue;
     if (!fine && G < 16) continue;
-    for (int nt : {128, 256}) {
-      if (nt / G < 2) continue;
-      cand.push_back({0, G, nt, 0.f});
-      if (2 * level_smem_bytes(view<T>(A)) <= kMaxSmem) cand.push_back({2, G, nt, 0.f});
-      cand.push_back({3, G, nt, 0.f});
-    }
+    for (int nt : {128, 256})
+      for (int u : {0, 4}) {
+        if (nt / G < 2) continue;
+        if (u == 4 && sizeof(T) != 8) continue;   // deeper unroll is an FP64 option
+        cand.push_back({0, G, nt, 0.f, u});
+        if (2 * level_smem_bytes(view<T>(A)) <= kMaxSmem) cand.push_back({2, G, nt, 0.f, u});
+        cand.push_back({3, G, nt, 0.f, u});
+      }
     if (A.tma[pi].nitems > 0)
-      for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f});
+      for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f, 0});
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
@@ -767,7 +782,8 @@ void numeric(r3mg_hierarchy* h, const double* vals_dev) {
     Level& C = h->lv[1];
     const size_t sm = sizeof(double) * 2 * kRapRows * b;
     k_rap_fine<<<(int)std::min<int64_t>(C.npairs, 1 << 30), 256, sm, s>>>(
-        F.pair_box, F.nbr_ptr, F.nbr, F.win_off, F.box_row, F.row_ptr, F.idx, F.v64, h->P64[0], b, F.npairs, C.row_ptr,
+        F.pair_box, F.nbr_ptr, F.nbr, F.win_off, F.slot_src, F.win_size, F.box_row, F.row_ptr, F.idx, F.v64, h->P64[0], b,
+        F.npairs, C.row_ptr,
         C.v64);
     CK(cudaGetLastError());
   }
@@ -875,7 +891,7 @@ void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLay
     int ms = 0;
     for (int64_t B = 0; B < F.nbox; ++B) {
       ms = std::max<int>(ms, (int)(pats[1].ptr[B + 1] - pats[1].ptr[B]));
-      for (int64_t e = pats[1].ptr[B]; e < pats[1].ptr[B + 1]; ++e) { ss[e] = P.box_off[1][pats[1].nbr[e]]; pb[e] = B; }
+      for (int64_t e = pats[1].ptr[B]; e < pats[1].ptr[B + 1]; ++e) { ss[e] = lay.win_src[e]; pb[e] = B; }
     }
     F.slot_src = upload(h, ss);
     F.pair_box = upload(h, pb);
@@ -906,6 +922,7 @@ void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLay
       c.nt = 512;
     }
     F.h_box_row = P.box_off[1];
+    F.h_win_size = lay.win_size;
     F.use_tma = (prm.kernel_form != 1) && h->bl.empty();
     if (F.use_tma) build_items(h, F, 0, lay.row_ptr, lay.win_off, ss);
     if (F.use_tma && prm.precision == 1) build_items(h, F, 1, lay.row_ptr, lay.win_off, ss);
@@ -1616,6 +1633,7 @@ void build_batch(r3mg_hierarchy* h, int np, const int64_t* n, const double* cons
     for (int64_t v : a.src) lay.src.push_back(v >= 0 ? v + nnz0[k] : -1);
     for (int64_t v : a.diag_src) lay.diag_src.push_back(v + nnz0[k]);
     lay.win_off.insert(lay.win_off.end(), a.win_off.begin(), a.win_off.end());
+    for (int64_t v : a.win_src) lay.win_src.push_back(v + row0[k]);
     lay.win_size.insert(lay.win_size.end(), a.win_size.begin(), a.win_size.end());
     lay.win_max = std::max(lay.win_max, a.win_max);
     lay.nnz += a.nnz;
@@ -2020,6 +2038,14 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
 }
 
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads) {
+  return r3mg_set_kernel_config2(h, level, fp32, form, lanes, threads, 0);
+}
+
+r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads, int unroll) {
+  if (unroll != 0 && !(unroll == 4 && !fp32)) {
+    if (h) h->err = "set_kernel_config: unroll 4 is an FP64 option (0 = default)";
+    return R3MG_E_ARG;
+  }
   if (!h || level < 0 || level >= h->L || form < 0 || form > 3 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
       (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || (form == 1 && threads == 128)) {
     if (h) h->err = "set_kernel_config: invalid level, form (0..3), lanes (4,8,16,32) or threads (128 register forms only, 256, 512, 1024)";
@@ -2032,7 +2058,7 @@ r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int f
   if (form == 2 && 2 * level_smem_bytes(view<double>(A)) > kMaxSmem) { h->err = "set_kernel_config: windows too large"; return R3MG_E_ARG; }
   return guarded(h, [&] {
     CK(cudaStreamSynchronize(h->stream));
-    A.conf[pi] = Level::KConf{form, lanes, threads, 0.f};
+    A.conf[pi] = Level::KConf{form, lanes, threads, 0.f, unroll};
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     h->graph_state = 0;   // recaptured at the next V-cycle
   });
@@ -2047,6 +2073,12 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
   if (lanes) *lanes = c.G;
   if (threads) *threads = tma ? c.nt : (c.nt == 128 ? 128 : 256);
   if (tuned_ms) *tuned_ms = c.ms;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_kernel_unroll(const r3mg_hierarchy* h, int level, int fp32, int* unroll) {
+  if (!h || level < 0 || level >= h->L || !unroll) return R3MG_E_ARG;
+  *unroll = h->lv[level].conf[fp32 ? 1 : 0].u;
   return R3MG_OK;
 }
 

@@ -172,8 +172,10 @@ class Hierarchy:
                 f = ctypes.c_int(0); g = ctypes.c_int(0); t = ctypes.c_int(0); ms = ctypes.c_float(0)
                 _check(lib().r3mg_kernel_config(self._h, lev, fp32, ctypes.byref(f), ctypes.byref(g), ctypes.byref(t),
                                                 ctypes.byref(ms)), self._h)
+                un = ctypes.c_int(0)
+                _check(lib().r3mg_kernel_unroll(self._h, lev, fp32, ctypes.byref(un)), self._h)
                 row[key] = {"form": ["register", "tma", "register_persistent", "register_l2_prefetch"][f.value], "lanes": g.value,
-                            "threads": t.value,
+                            "threads": t.value, "unroll": un.value,
                             "tuned_ms": round(ms.value, 5)}
             out.append(row)
         return out
@@ -186,8 +188,8 @@ class Hierarchy:
                 if key not in row or (fp32 and self.params["precision"] != 1):
                     continue
                 c = row[key]
-                _check(lib().r3mg_set_kernel_config(self._h, lev, fp32, forms[c["form"]], int(c["lanes"]),
-                                                    int(c["threads"])), self._h)
+                _check(lib().r3mg_set_kernel_config2(self._h, lev, fp32, forms[c["form"]], int(c["lanes"]),
+                                                     int(c["threads"]), int(c.get("unroll", 0))), self._h)
 
     def agglomerates(self, level: int) -> np.ndarray:
         out = np.empty(self.n, np.int64)
