@@ -177,6 +177,36 @@ r3mg_status r3mg_pcg_host(r3mg_hierarchy* h, const double* b_host, double* x_hos
                           int* iters_out, double* relres_out, void* stream);
 
 /*
+ * Several right-hand sides at once (Section 6's PCG, run per column): m <= 16 systems
+ * A x_c = b_c on one hierarchy, every level operator reading the matrix once for all columns
+ * (block vectors of M = 4, 8 or 16 columns, row-interleaved inside the library; unused columns
+ * are zero).  Each column has its own CG scalars and stopping test ||b_c - A x_c|| <=
+ * rtol ||b_c|| (confirmed by an FP64 true residual); converged columns stop updating while the
+ * others continue.  Precision as in r3mg_pcg (FP64 PCG, or FP32 V-cycle inside FP64 FCG).
+ *   b_dev, x_dev (device): m vectors of n doubles each, vector c at offset c*n, caller numbering;
+ *   x_dev in = initial guesses, out = solutions.
+ *   iters_out[m]: completed updates of each column; relres_out[m]: final ||r_c|| / ||b_c||.
+ * Errors: R3MG_E_ARG (m outside 1..16, null pointer, batched hierarchy), R3MG_E_NOCONV (some
+ * column reached maxit; x holds the last iterates), R3MG_E_BREAKDOWN, R3MG_E_CUDA, R3MG_E_OOM.
+ * Synchronises the stream.  The library allocates the block vectors at the first call (and
+ * again when the column count class changes) and keeps them until r3mg_destroy.
+ */
+r3mg_status r3mg_pcg_multi(r3mg_hierarchy* h, int m, const double* b_dev, double* x_dev, double rtol, int maxit,
+                           int* iters_out, double* relres_out, void* stream);
+
+/* One V-cycle (Section 4) on m <= 16 vectors at once: z_c = M^{-1} r_c, in the hierarchy's
+ * V-cycle precision.  r_dev, z_dev: m x n doubles (vector c at offset c*n), caller numbering.
+ * Asynchronous on the stream. */
+r3mg_status r3mg_vcycle_multi(r3mg_hierarchy* h, int m, const double* r_dev, double* z_dev, void* stream);
+
+/* y_c = A_l x_c for m <= 16 vectors with the block kernel: fp32 = 0 uses the FP64 values,
+ * fp32 = 1 the FP32 V-cycle values (hierarchies built with precision 1, levels below the
+ * coarsest only, else R3MG_E_ARG; inputs are rounded to FP32, outputs widened).  x_dev, y_dev: m x n_l doubles, vector c at offset c*n_l,
+ * level numbering as in r3mg_level_apply.  Asynchronous. */
+r3mg_status r3mg_level_apply_multi(r3mg_hierarchy* h, int level, int m, int fp32, const double* x_dev, double* y_dev,
+                                   void* stream);
+
+/*
  * y = A_l x on level l, FP64, in level numbering (level 0: caller numbering
  * of the free DoFs; level l >= 1: coarse DoF box*b + q, boxes numbered left
  * to right in the tree).  x_dev, y_dev: device, n_l doubles.  Asynchronous.
@@ -227,7 +257,8 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
 /* Level-operator kernel chosen for level l and precision (fp32 = 0: FP64, 1: FP32):
  * form 0 = register-streamed, 1 = TMA-streamed, 2 = register-streamed persistent with a
  * double-buffered window, 3 = register-streamed with a bulk L2 prefetch of each box's matrix
- * slice; lanes per matrix row; threads per CTA;
+ * slice, 4 = symmetric block form (coarse FP32 levels: only the upper blocks are streamed, each
+ * used for both of its products); lanes per matrix row; threads per CTA;
  * the autotuner's measured time of one launch (0 when not tuned).  Any output may be NULL. */
 r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
                                float* tuned_ms);
@@ -266,7 +297,7 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
                                double* out_dev, void* stream);
 
 /* Pin the level-operator kernel of level l and precision (fp32 = 1 needs an FP32 V-cycle):
- * form 0..3 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads per CTA in
+ * form 0..4 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads per CTA in
  * {128, 256} for the register forms and {256, 512, 1024} for the TMA form.  Replays a configuration chosen earlier (reproducible timing
  * and profiling).  Errors: R3MG_E_ARG for an unsupported combination.  Synchronises. */
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads);

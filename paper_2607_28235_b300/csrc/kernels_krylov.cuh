@@ -160,6 +160,33 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
     y[k] += a * x[k];
 }
 
+// Loop state of the single-problem solve graph: lp[0] = rtol^2 ||b||^2, lp[1] = iteration budget.
+__global__ void k_loop_init(double* __restrict__ lp, int* __restrict__ its, int* __restrict__ status,
+                            double rtol2bb, int budget) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    lp[0] = rtol2bb;
+    lp[1] = (double)budget;
+    *its = 0;
+    *status = 0;
+  }
+}
+
+// Device-side stop test after the x/r update of one iteration: count it, then continue the loop
+// (and run this iteration's V-cycle and direction update) only while ||r||^2 > rtol^2 ||b||^2,
+// the budget is not spent and no breakdown was flagged.
+__global__ void k_converge1(const double* __restrict__ scal, const double* __restrict__ lp, int* __restrict__ its,
+                            const int* __restrict__ status, cudaGraphConditionalHandle loop,
+                            cudaGraphConditionalHandle rest) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int k = *its + 1;
+    *its = k;
+    const double rr = scal[S_RR];
+    const bool go = isfinite(rr) && rr > lp[0] && (double)k < lp[1] && *status == 0;
+    cudaGraphSetConditional(loop, go ? 1u : 0u);
+    cudaGraphSetConditional(rest, go ? 1u : 0u);
+  }
+}
+
 // Sampled outer product on the stored pattern of A (the adjoint's matrix gradient):
 // out[k] = alpha * lam[i] * u[col[k]] for every entry k of row i, in the caller's CSR order.
 // One warp per row; the row's values are read once, u is gathered from L2.

@@ -1,0 +1,462 @@
+// Several right-hand sides on one hierarchy (block vectors).  Every level vector holds M
+// columns row-interleaved: row i keeps its M values contiguous (i*M + c), so one matrix entry,
+// read once from HBM, multiplies M gathered values that sit in one or two 32-byte sectors.
+// The level operators, the transfers P / P^T, the coarsest solve and the CG updates below are
+// the single-vector kernels' arithmetic (Sections 3-4, Chebyshev-Jacobi smoothing, PCG/FCG)
+// applied column by column; only the data layout and the thread mapping differ.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels_level.cuh"
+#include "kernels_krylov.cuh"
+
+namespace r3mg {
+
+// 16-byte column slice of one row: 4 floats or 2 doubles
+template <typename T>
+struct Slice {
+  static constexpr int V = 16 / (int)sizeof(T);
+  T v[V];
+  __device__ __forceinline__ void ldg(const T* p) {   // read-only path (gathered operands)
+    if constexpr (sizeof(T) == 4) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+      const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+      v[0] = a.x; v[1] = a.y;
+    }
+  }
+  __device__ __forceinline__ void ld(const T* p) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(p);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(p);
+      v[0] = a.x; v[1] = a.y;
+    }
+  }
+  __device__ __forceinline__ void st(T* p) const {
+    if constexpr (sizeof(T) == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// ---------------------------------------------------------------- level operators
+// Epilogues get the row, the first column of the lane's slice, the slice of (A X)_row and the
+// lane's per-column dot partials.
+
+template <typename T, int M>
+struct MEpApply {   // Y = A X, and per-column partials of W . Y when W is given
+  T* y; const T* w;
+  static constexpr bool kDot = true;
+  __device__ void post(int64_t row, int c0, const Slice<T>& a, double (&dacc)[Slice<T>::V]) const {
+    a.st(y + row * M + c0);
+    if (w) {
+      Slice<T> ws;
+      ws.ld(w + row * M + c0);
+#pragma unroll
+      for (int v = 0; v < Slice<T>::V; ++v) dacc[v] += (double)ws.v[v] * (double)a.v[v];
+    }
+  }
+};
+
+// One Chebyshev-Jacobi step per column (the input block is the current update D):
+// X += D;  R -= A D;  D' = a D + c dinv R.
+template <typename T, int M>
+struct MEpCheb {
+  T* x; T* r; const T* d; T* dnext; const T* dinv; T a, c;
+  static constexpr bool kDot = false;
+  __device__ void post(int64_t row, int c0, const Slice<T>& ad, double (&)[Slice<T>::V]) const {
+    const int64_t o = row * M + c0;
+    Slice<T> xs, rs, ds;
+    xs.ld(x + o); rs.ld(r + o); ds.ld(d + o);
+    const T di = dinv[row];
+#pragma unroll
+    for (int v = 0; v < Slice<T>::V; ++v) {
+      xs.v[v] += ds.v[v];
+      rs.v[v] -= ad.v[v];
+      ds.v[v] = a * ds.v[v] + c * di * rs.v[v];
+    }
+    xs.st(x + o); rs.st(r + o); ds.st(dnext + o);
+  }
+};
+
+// Level operator on M columns.  One CTA per box (grid-stride).  The box's window map (window
+// position -> row of the level, the same windows the single-vector kernel stages) is built in
+// shared memory; each row is taken by CL*S lanes: CL lanes cover the M columns with 16-byte
+// slices, S lanes split the row's entries in groups of four.  Entry values and indices are
+// read once per lane group (the CL lanes of a slot read the same address), the gathered rows
+// of X come through the read-only L1 path.
+template <typename T, int M, int S, bool FINE, class Ep>
+__global__ void __launch_bounds__(256) k_mr_level(LevelView<T> L, const T* __restrict__ xin, Ep ep,
+                                                  double* __restrict__ part) {
+  constexpr int V = Slice<T>::V, CL = M / V, LPR = CL * S, RPW = 32 / LPR;
+  static_assert(M % V == 0 && 32 % LPR == 0, "lane layout");
+  extern __shared__ __align__(16) int32_t smap[];
+  __shared__ double red[8][M];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const int cl = lane % CL, s = (lane / CL) % S, rw = lane / LPR;
+  double dacc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) dacc[v] = 0.0;
+  for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
+    const int64_t e0 = L.nbr_ptr[B];
+    const int nn = (int)(L.nbr_ptr[B + 1] - e0);
+    int W;
+    int64_t r0, r1;
+    if constexpr (FINE) {
+      W = L.win_size[B];
+      for (int q = warp; q < nn; q += NW) {
+        const int wo = L.win_off[e0 + q];
+        const int64_t src = L.slot_src[e0 + q];
+        const int len = (q + 1 < nn ? L.win_off[e0 + q + 1] : W) - wo;
+        for (int t = lane; t < len; t += 32) smap[wo + t] = (int32_t)(src + t);
+      }
+      r0 = L.box_row[B]; r1 = L.box_row[B + 1];
+    } else {
+      const int b = L.b;
+      W = nn * b;
+      for (int t = threadIdx.x; t < W; t += blockDim.x) smap[t] = (int32_t)(L.nbr[e0 + t / b] * b + t % b);
+      r0 = B * b; r1 = r0 + b;
+    }
+    // padding entries (zero values) point at row 0
+    for (int t = W + threadIdx.x; t < ((W + 3) & ~3); t += blockDim.x) smap[t] = 0;
+    __syncthreads();
+    // warp-uniform trip count: the slot shuffles below see the whole warp
+    for (int64_t base = r0 + (int64_t)warp * RPW; base < r1; base += (int64_t)NW * RPW) {
+      const int64_t row = base + rw;
+      const bool ok = row < r1;
+      int64_t k0 = 0, k1 = 0;
+      if (ok) { k0 = L.row_ptr[row]; k1 = L.row_ptr[row + 1]; }
+      Slice<T> acc;
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc.v[v] = T(0);
+      for (int64_t k = k0 + 4 * s; k < k1; k += 4 * S) {
+        T a[4];
+        int ii[4];
+        Vec4<T>::load(L.vals + k, a);
+        if constexpr (FINE) load_idx4(L.idx + k, ii);
+        else { const int t = (int)(k - k0); ii[0] = t; ii[1] = t + 1; ii[2] = t + 2; ii[3] = t + 3; }
+        Slice<T> xv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) xv[e].ldg(xin + (int64_t)smap[ii[e]] * M + cl * V);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc.v[v] += a[e] * xv[e].v[v];
+      }
+#pragma unroll
+      for (int o = CL; o < LPR; o <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc.v[v] += __shfl_xor_sync(0xffffffffu, acc.v[v], o);
+      if (ok && s == 0) ep.post(row, cl * V, acc, dacc);
+    }
+    __syncthreads();
+  }
+  if constexpr (Ep::kDot) {
+    if (part != nullptr) {
+      // fold the lanes of equal column slice, then the warps in a fixed order
+#pragma unroll
+      for (int o = CL; o < 32; o <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; ++v) dacc[v] += __shfl_xor_sync(0xffffffffu, dacc[v], o);
+      if (lane < CL)
+#pragma unroll
+        for (int v = 0; v < V; ++v) red[warp][lane * V + v] = dacc[v];
+      __syncthreads();
+      if (threadIdx.x < M) {
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * M + threadIdx.x] = t;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- transfers
+// Next-level initialisation after restriction, per column: R = B, X = 0, D = c0 dinv B.
+template <typename T, int M>
+struct MNextInit {
+  T* r; T* x; T* d; const T* dinv; T c0;
+  __device__ void operator()(int64_t i, int c, T bi) const {
+    r[i * M + c] = bi;
+    if (x) { x[i * M + c] = T(0); d[i * M + c] = c0 * dinv[i] * bi; }
+  }
+};
+
+// Fine -> level 1: B1[(B*b+q), c] = sum_{i in B} P0[i][q] R[i, c].  One CTA per box.
+template <typename T, int M, class NX>
+__global__ void __launch_bounds__(256) k_mr_restrict_fine(const T* __restrict__ P0, const T* __restrict__ r,
+                                                          const int64_t* __restrict__ box_row, int64_t nbox, int b,
+                                                          NX nx) {
+  for (int64_t B = blockIdx.x; B < nbox; B += gridDim.x) {
+    const int64_t i0 = box_row[B], i1 = box_row[B + 1];
+    for (int t = threadIdx.x; t < b * M; t += blockDim.x) {
+      const int q = t / M, c = t % M;
+      T s = T(0);
+      for (int64_t i = i0; i < i1; ++i) s += P0[i * b + q] * r[i * M + c];
+      nx(B * b + q, c, s);
+    }
+  }
+}
+
+// Level l -> l+1: B[(P,q), c] = sum_{children ch} sum_{q'} Pt[ch][q'][q] R[(ch,q'), c].
+template <typename T, int M, class NX>
+__global__ void k_mr_restrict_coarse(const T* __restrict__ Pt, const T* __restrict__ r, int64_t nparent, int b,
+                                     int fan, NX nx) {
+  const int64_t tot = nparent * b * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % M);
+    const int64_t bq = t / M;
+    const int64_t B = bq / b;
+    const int q = (int)(bq - B * b);
+    T s = T(0);
+    for (int64_t ch = B * fan; ch < (B + 1) * fan; ++ch)
+      for (int qp = 0; qp < b; ++qp) s += Pt[(ch * b + qp) * b + q] * r[(ch * b + qp) * M + c];
+    nx(bq, c, s);
+  }
+}
+
+// Level 1 -> fine: D0[k, c] = sum_q P0[k][q] (X1 + D1)[(box(k)*b+q), c]   (D1 may be null).
+template <typename T, int M>
+__global__ void k_mr_prolong_fine(const T* __restrict__ P0, const int32_t* __restrict__ box_of,
+                                  const T* __restrict__ x1, const T* __restrict__ d1, int64_t n, int b,
+                                  T* __restrict__ d0) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * M; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / M;
+    const int c = (int)(t - k * M);
+    const int64_t B = box_of[k];
+    T s = T(0);
+    for (int q = 0; q < b; ++q) {
+      const int64_t o = (B * b + q) * M + c;
+      s += P0[k * b + q] * (x1[o] + (d1 ? d1[o] : T(0)));
+    }
+    d0[t] = s;
+  }
+}
+
+// Level l+1 -> l: D[(ch,q'), c] = sum_q Pt[ch][q'][q] (X + D)_{l+1}[(parent(ch), q), c].
+template <typename T, int M>
+__global__ void k_mr_prolong_coarse(const T* __restrict__ Pt, const T* __restrict__ x1, const T* __restrict__ d1,
+                                    int64_t nchild, int b, int fan, T* __restrict__ d0) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nchild * b * M;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % M);
+    const int64_t cq = t / M;
+    const int64_t ch = cq / b;
+    const int64_t B = ch / fan;
+    T s = T(0);
+    for (int q = 0; q < b; ++q) {
+      const int64_t o = (B * b + q) * M + c;
+      s += Pt[cq * b + q] * (x1[o] + (d1 ? d1[o] : T(0)));
+    }
+    d0[t] = s;
+  }
+}
+
+// Coarsest solve X = A_c^{-1} R on M columns: one warp per row of the inverse, lanes split as
+// in k_mr_level (CL column slices x S entry slots); the inverse is read once for all columns.
+template <typename T, int M>
+__global__ void __launch_bounds__(256) k_mr_dense(const T* __restrict__ Ainv, int64_t ld, const T* __restrict__ r,
+                                                  int64_t nc, T* __restrict__ x) {
+  constexpr int V = Slice<T>::V, CL = M / V, S = 32 / CL;
+  const int lane = threadIdx.x & 31, cl = lane % CL, s = lane / CL;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w; row < nc; row += nw) {
+    const T* a = Ainv + row * ld;
+    Slice<T> acc;
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc.v[v] = T(0);
+    for (int64_t k = s; k < nc; k += S) {
+      const T ak = a[k];
+      Slice<T> xv;
+      xv.ldg(r + k * M + cl * V);
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc.v[v] += ak * xv.v[v];
+    }
+#pragma unroll
+    for (int o = CL; o < 32; o <<= 1)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc.v[v] += __shfl_xor_sync(0xffffffffu, acc.v[v], o);
+    if (s == 0) acc.st(x + row * M + cl * V);
+  }
+}
+
+// ---------------------------------------------------------------- CG on M columns (FP64)
+// Per-column scalars live in mscal[slot * M + c] (slots as in Scal).  The element loops below
+// stride by a multiple of M, so every thread stays on one column c = threadIdx.x % M.
+
+// Per-CTA, per-column partial sums: part[blockIdx.x * M + c].  blockDim = 256.
+template <int M>
+__device__ __forceinline__ void store_partial_m(double v, double* part) {
+  __shared__ double red[8][M];
+  for (int o = M; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l < M) red[w][l] = v;
+  __syncthreads();
+  if (threadIdx.x < M) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][threadIdx.x];
+    part[(int64_t)blockIdx.x * M + threadIdx.x] = s;
+  }
+}
+
+// Caller-order column blocks (m vectors of length n, each contiguous) <-> tree-order,
+// row-interleaved blocks of M >= m columns (the extra columns are zero).  perm == nullptr:
+// identity (coarse levels keep their own numbering).
+__global__ void k_mr_gather(const double* __restrict__ src, const int64_t* __restrict__ perm, int64_t n, int m,
+                            int M, double* __restrict__ dst) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * M; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / M;
+    const int c = (int)(t - i * M);
+    dst[t] = c < m ? src[(int64_t)c * n + (perm ? perm[i] : i)] : 0.0;
+  }
+}
+
+__global__ void k_mr_scatter(const double* __restrict__ src, const int64_t* __restrict__ perm, int64_t n, int m,
+                             int M, double* __restrict__ dst) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * M; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / M;
+    const int c = (int)(t - i * M);
+    if (c < m) dst[(int64_t)c * n + (perm ? perm[i] : i)] = src[t];
+  }
+}
+
+// R = B - Y with per-column partials of ||R||^2 and (optionally) ||B||^2.
+template <int M>
+__global__ void __launch_bounds__(256) k_mr_residual(const double* __restrict__ b, const double* __restrict__ y,
+                                                     double* __restrict__ r, int64_t nm, double* part, double* part2) {
+  double s = 0.0, s2 = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nm; k += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[k] - y[k];
+    r[k] = v;
+    s += v * v;
+    s2 += b[k] * b[k];
+  }
+  store_partial_m<M>(s, part);
+  if (part2) { __syncthreads(); store_partial_m<M>(s2, part2); }
+}
+
+// V-cycle entry on level 0 from the FP64 residual: VR = R, VX = 0, VD = c0 dinv R.
+template <typename T, int M>
+__global__ void k_mr_vc_init(const double* __restrict__ r, int64_t nm, T* vr, T* vx, T* vd,
+                             const T* __restrict__ dinv, T c0) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nm; k += (int64_t)gridDim.x * blockDim.x) {
+    const T rt = (T)r[k];
+    vr[k] = rt;
+    vx[k] = T(0);
+    vd[k] = c0 * dinv[k / M] * rt;
+  }
+}
+
+// X += alpha_c P; R -= alpha_c Q; per-column ||R||^2; V-cycle entry from the new R.
+template <typename T, int M>
+__global__ void __launch_bounds__(256) k_mr_cg_update(double* __restrict__ x, double* __restrict__ r,
+                                                      const double* __restrict__ p, const double* __restrict__ q,
+                                                      const double* __restrict__ mscal, int64_t nm, double* part,
+                                                      T* vr, T* vx, T* vd, const T* __restrict__ dinv, T c0) {
+  const double alpha = mscal[S_ALPHA * M + threadIdx.x % M];
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nm; k += (int64_t)gridDim.x * blockDim.x) {
+    x[k] += alpha * p[k];
+    const double rk = r[k] - alpha * q[k];
+    r[k] = rk;
+    s += rk * rk;
+    const T rt = (T)rk;
+    vr[k] = rt;
+    vx[k] = T(0);
+    vd[k] = c0 * dinv[k / M] * rt;
+  }
+  store_partial_m<M>(s, part);
+}
+
+// Z = VX + VD (level 0's last update), per-column partials of Z . W.
+template <typename T, int M>
+__global__ void __launch_bounds__(256) k_mr_vc_final_dot(const T* __restrict__ vx, const T* __restrict__ vd,
+                                                         double* __restrict__ z, const double* __restrict__ w,
+                                                         int64_t nm, double* part) {
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nm; k += (int64_t)gridDim.x * blockDim.x) {
+    const double zk = (double)vx[k] + (double)vd[k];
+    z[k] = zk;
+    s += zk * w[k];
+  }
+  store_partial_m<M>(s, part);
+}
+
+// PCG: P = Z + beta_c P.  FCG: P = Z - beta_c P and per-column partials of P . R.
+template <int M>
+__global__ void __launch_bounds__(256) k_mr_p_update(double* __restrict__ p, const double* __restrict__ z,
+                                                     const double* __restrict__ r, const double* __restrict__ mscal,
+                                                     int64_t nm, int fcg, double* part) {
+  const double beta = mscal[S_BETA * M + threadIdx.x % M];
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nm; k += (int64_t)gridDim.x * blockDim.x) {
+    const double pk = fcg ? z[k] - beta * p[k] : z[k] + beta * p[k];
+    p[k] = pk;
+    s += pk * r[k];
+  }
+  if (part) store_partial_m<M>(s, part);
+}
+
+// Per-column deterministic sums of `nb` CTA partials into mscal[slot][c], then the scalar
+// finish of each active column (inactive columns take alpha = beta = 0 and stay put).
+// blockDim = 32 * M: warp c sums column c.
+template <int M>
+__global__ void k_mr_reduce(const double* __restrict__ part, int nb, double* mscal, int slot, int fin,
+                            const int* __restrict__ active, int* status) {
+  const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (c >= M) return;
+  double s = 0.0;
+  for (int k = l; k < nb; k += 32) s += part[(int64_t)k * M + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (l != 0) return;
+  mscal[slot * M + c] = s;
+  const bool act = active == nullptr || active[c] != 0;
+  if (fin == FIN_ALPHA_PCG || fin == FIN_ALPHA_FCG) {
+    const double num = (fin == FIN_ALPHA_PCG) ? mscal[S_RZ * M + c] : mscal[S_PR * M + c];
+    if (!act) mscal[S_ALPHA * M + c] = 0.0;
+    else if (!(s > 0.0) || !isfinite(num)) { if (status) atomicExch(status, 1); mscal[S_ALPHA * M + c] = 0.0; }
+    else mscal[S_ALPHA * M + c] = num / s;
+  } else if (fin == FIN_BETA_PCG) {
+    mscal[S_BETA * M + c] = act ? s / mscal[S_RZ * M + c] : 0.0;
+    if (act) mscal[S_RZ * M + c] = s;
+  } else if (fin == FIN_BETA_FCG) {
+    mscal[S_BETA * M + c] = act ? s / mscal[S_PQ * M + c] : 0.0;
+  }
+}
+
+// Device-side stop test after the X/R update: count the update of every active column, retire
+// columns with ||r_c||^2 <= rtol^2 ||b_c||^2 or a spent budget, continue while any is active.
+// lp[0] = rtol^2, lp[1] = iteration budget per column.  One warp.  Inside the loop graph
+// (in_graph = 1) the decision sets the loop's conditions, else it goes to *go_out.
+template <int M>
+__global__ void k_mr_converge(const double* __restrict__ mscal, const double* __restrict__ lp, int* __restrict__ its,
+                              int* __restrict__ active, int* __restrict__ status, cudaGraphConditionalHandle loop,
+                              cudaGraphConditionalHandle rest, int in_graph, int* __restrict__ go_out) {
+  const int c = threadIdx.x;
+  bool go = false;
+  if (c < M && active[c]) {
+    const int k = its[c] + 1;
+    its[c] = k;
+    const double rr = mscal[S_RR * M + c];
+    if (!isfinite(rr)) atomicExch(status, 1);
+    const bool done = !(rr > lp[0] * mscal[S_BB * M + c]) || (double)k >= lp[1];
+    if (done) active[c] = 0;
+    go = !done;
+  }
+  const unsigned any = __ballot_sync(0xffffffffu, go);
+  if (c == 0) {
+    const bool g = any != 0u && *status == 0;
+    if (in_graph) {
+      cudaGraphSetConditional(loop, g ? 1u : 0u);
+      cudaGraphSetConditional(rest, g ? 1u : 0u);
+    } else {
+      *go_out = g ? 1 : 0;
+    }
+  }
+}
+
+}  // namespace r3mg

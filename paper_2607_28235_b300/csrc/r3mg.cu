@@ -16,6 +16,8 @@
 #include "kernels_level.cuh"
 #include "kernels_level_tma.cuh"
 #include "kernels_batch.cuh"
+#include "kernels_level_sym.cuh"
+#include "kernels_mrhs.cuh"
 #include "kernels_setup.cuh"
 #include "kernels_vcycle.cuh"
 
@@ -57,6 +59,13 @@ struct Level {
   int nsm = 148;
   KConf conf[2];
   int use_tma = 1;   // TMA work items could be built for this level
+  // symmetric block form (coarse levels, FP32): upper blocks only
+  SymView sym;
+  bool sym_ok = false;
+  float* sym_vals = nullptr;
+  float* sym_y = nullptr;
+  float* sym_t = nullptr;
+  std::vector<int64_t> h_row_ptr;   // host copy of the block-row pointers (symmetric gather)
   std::vector<int64_t> h_box_row;   // host copy of box row offsets (fine) for item building
   std::vector<int32_t> h_win_size;  // host copy of the window lengths (fine) for item building
 };
@@ -133,8 +142,26 @@ struct r3mg_hierarchy {
   std::vector<double> h_seg;
   cudaGraphExec_t bgraph = nullptr;
   int bgraph_state = 0;
+  // single-problem loop graph (conditional WHILE node)
+  cudaGraphExec_t lgraph = nullptr;
+  int lgraph_state = 0;
+  int* d_its = nullptr;
+  double* d_loop = nullptr;
   double bgraph_rtol = -1.0;
   int bgraph_maxit = -1;
+  // ---- several right-hand sides (row-interleaved blocks of M columns)
+  int mr_M = 0;                       // columns of the allocated block vectors (0: none yet)
+  std::vector<void*> mr_x, mr_r, mr_d0, mr_d1;   // per level, V-cycle precision
+  double *mr_b = nullptr, *mr_xc = nullptr, *mr_rc = nullptr, *mr_p = nullptr, *mr_q = nullptr, *mr_z = nullptr;
+  double *mr_scal = nullptr, *mr_pa = nullptr, *mr_pb = nullptr, *mr_lp = nullptr;
+  int *mr_its = nullptr, *mr_active = nullptr;
+  double* mr_host = nullptr;          // pinned: 2 x 16 doubles + 2 x 16 ints
+  int64_t mr_npart = 0;
+  std::vector<int> mr_S[2];           // per level: entry slots per row ([0] FP64, [1] FP32)
+  cudaGraphExec_t mgraph = nullptr;
+  int mgraph_state = 0;
+  int prof_cols = 1;                  // columns of the last profiled solve (bytes per launch)
+  int64_t mr_graph_kernels = 0;       // kernels in one block V-cycle
   int nsm = 148;
   int tma_ctas = 1;                   // TMA kernel CTAs per SM
   int64_t graph_kernels = 0;          // kernels in one replay of the V-cycle graph
@@ -356,6 +383,12 @@ int level_apply_dot(r3mg_hierarchy* h, const Level& A, const T* x, T* y, const T
 
 template <typename T>
 void level_cheb(r3mg_hierarchy* h, const Level& A, T* x, T* r, T* d, T* dn, const T* dinv, T a, T c) {
+  if constexpr (sizeof(T) == 4) {
+    if (A.conf[1].form == 4 && A.sym_ok) {
+      sym_step(h, A, d, SymCheb{x, r, d, dn, dinv, a, c});
+      return;
+    }
+  }
   if (tma_on<T>(A)) launch_tma<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream, h->tma_err);
   else launch_level<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream);
 }
@@ -431,6 +464,64 @@ void build_items(r3mg_hierarchy* h, Level& A, int prec_idx, const std::vector<in
                  : (es == 4 ? TmaLayout<float, false>(SE, A.win_max, rmax, dmax).total : TmaLayout<double, false>(SE, A.win_max, rmax, dmax).total);
   if (it.smem > kMaxSmem / h->tma_ctas) { A.use_tma = 0; return; }
   it.grid = (int)std::max<int64_t>(1, std::min<int64_t>(it.nitems, (int64_t)h->nsm * h->tma_ctas));
+}
+
+// Symmetric block form of a coarse level: upper block rows, transposed-pair vectors, lower lists.
+void build_sym(r3mg_hierarchy* h, Level& A) {
+  const int b = A.b;
+  if (b <= 0 || b > kSymMaxB) return;
+  const int64_t nb = A.nbox;
+  std::vector<int64_t> up_base(nb + 1, 0), tp_off(nb + 1, 0), low_ptr(nb + 1, 0);
+  std::vector<int32_t> up_len(nb), dslot(nb);
+  std::vector<std::vector<int64_t>> low(nb);
+  int wmax = 0;
+  for (int64_t B = 0; B < nb; ++B) {
+    const int64_t q0 = A.pat.ptr[B], nn = A.pat.ptr[B + 1] - q0;
+    int64_t d = -1;
+    for (int64_t s = 0; s < nn; ++s) if (A.pat.nbr[q0 + s] == B) { d = s; break; }
+    if (d < 0) return;   // no diagonal block: leave the level to the full forms
+    const int nup = (int)(nn - d);
+    const int len = (nup * b + 3) & ~3;
+    dslot[B] = (int32_t)d;
+    up_len[B] = len;
+    up_base[B + 1] = up_base[B] + (int64_t)b * len;
+    tp_off[B + 1] = tp_off[B] + (nup - 1);
+    wmax = std::max(wmax, len);
+    for (int64_t s = d + 1; s < nn; ++s) low[A.pat.nbr[q0 + s]].push_back(tp_off[B] + (s - d - 1));
+  }
+  std::vector<int64_t> low_pair;
+  for (int64_t B = 0; B < nb; ++B) {
+    low_pair.insert(low_pair.end(), low[B].begin(), low[B].end());
+    low_ptr[B + 1] = (int64_t)low_pair.size();
+  }
+  SymView& V = A.sym;
+  V.nbox = nb; V.b = b;
+  V.up_base = upload(h, up_base);
+  V.up_len = upload(h, up_len);
+  V.nbr_ptr = A.nbr_ptr; V.nbr = A.nbr;
+  V.dslot = upload(h, dslot);
+  V.tp_off = upload(h, tp_off);
+  V.low_ptr = upload(h, low_ptr);
+  V.low_pair = upload(h, low_pair);
+  V.win_max = wmax;
+  A.sym_vals = dalloc<float>(h, up_base[nb]);
+  V.vals = A.sym_vals;
+  A.sym_y = dalloc<float>(h, A.n);
+  A.sym_t = dalloc<float>(h, std::max<int64_t>(1, tp_off[nb] * b));
+  A.sym_ok = true;
+}
+
+void sym_step(r3mg_hierarchy* h, const Level& A, const float* d, SymCheb ep) {
+  static size_t configured = 48 * 1024;
+  const size_t sm = sizeof(float) * 8 * (size_t)A.sym.win_max;
+  if (sm > configured) {
+    CK(cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = sm;
+  }
+  k_sym_block<<<(int)std::max<int64_t>(1, (A.nbox + 7) / 8), 256, sizeof(float) * 8 * (size_t)A.sym.win_max,
+                h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
+  k_sym_finish<<<grid_for(A.n), 256, 0, h->stream>>>(A.sym, A.sym_y, A.sym_t, ep);
+  CK(cudaGetLastError());
 }
 
 void read_status(r3mg_hierarchy* h, int& st) {
@@ -733,6 +824,7 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
       }
     if (A.tma[pi].nitems > 0)
       for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f, 0});
+    if (sizeof(T) == 4 && A.sym_ok && G == 16 && !product) cand.push_back({4, G, 128, 0.f, 0});
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
@@ -767,8 +859,21 @@ void dense_batch(r3mg_hierarchy* h);
 template <typename T>
 T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing);
 
+// Captured graphs hold the Chebyshev coefficients, c0 and kernel configurations as launch
+// arguments: drop them whenever those change; the next solve recaptures.
+void drop_graphs(r3mg_hierarchy* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
+  if (h->lgraph) cudaGraphExecDestroy(h->lgraph);
+  if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
+  h->graph = h->bgraph = h->lgraph = h->mgraph = nullptr;
+  h->graph_state = h->bgraph_state = h->lgraph_state = h->mgraph_state = 0;
+}
+
 void numeric(r3mg_hierarchy* h, const double* vals_dev) {
   cudaStream_t s = h->stream;
+  CK(cudaStreamSynchronize(s));
+  drop_graphs(h);
   Level& F = h->lv[0];
   k_gather_vals<<<grid_for(F.stored), 256, 0, s>>>(h->src, vals_dev, F.v64, F.stored);
   k_dinv_fine<<<grid_for(h->n), 256, 0, s>>>(h->diag_src, vals_dev, F.dinv64, h->n, h->status);
@@ -817,6 +922,12 @@ void numeric(r3mg_hierarchy* h, const double* vals_dev) {
         k_convert<double, float><<<grid_for(A.stored), 256, 0, s>>>(A.v64, A.v32, A.stored);
         k_convert<double, float><<<grid_for(A.n), 256, 0, s>>>(A.dinv64, A.dinv32, A.n);
       }
+    }
+    for (int l = 1; l + 1 < h->L; ++l) {
+      Level& A = h->lv[l];
+      if (!A.sym_ok) continue;
+      k_sym_gather<<<(int)std::min<int64_t>(A.n, 1 << 20), 128, 0, s>>>(A.sym, A.row_ptr, A.v32, A.sym_vals);
+      CK(cudaGetLastError());
     }
     const int64_t na = !h->bl.empty() ? h->batch_ainv_size : h->ncp * h->ncp;
     k_convert<double, float><<<grid_for(na), 256, 0, s>>>(h->Ainv64, h->Ainv32, na);
@@ -972,6 +1083,7 @@ void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLay
       c.nt = 512;
     }
     C.use_tma = (prm.kernel_form != 1) && h->bl.empty();
+    if (prm.precision == 1 && l + 1 < L) { C.h_row_ptr = rp; build_sym(h, C); }
     if (C.use_tma) build_items(h, C, 0, rp, {}, {});
     if (C.use_tma && prm.precision == 1 && l + 1 < L) build_items(h, C, 1, rp, {}, {});
   }
@@ -1121,6 +1233,84 @@ struct StreamJoin {  // run the hierarchy's work after the caller's stream, and 
   }
 };
 
+// Capture one CG/FCG iteration into a WHILE-loop graph (see krylov); lgraph_state -1 on failure,
+// after which solves use the host-driven loop.
+template <typename T>
+void build_loop_graph(r3mg_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  Level& F = h->lv[0];
+  const int64_t n = h->n;
+  const bool fcg = (h->prm.precision == 1);
+  const int gv = grid_for(n);
+  if (!h->d_its) h->d_its = dalloc<int>(h, 1);
+  if (!h->d_loop) h->d_loop = dalloc<double>(h, 2);
+  cudaGraph_t g = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  cudaGraphConditionalHandle wh{}, ih{};
+  cudaGraph_t body = nullptr, rest = nullptr;
+  if (ok) ok = cudaGraphConditionalHandleCreate(&wh, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = wh;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    ok = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp) == cudaSuccess;
+    if (ok) body = wp.conditional.phGraph_out[0];
+  }
+  if (ok) ok = cudaGraphConditionalHandleCreate(&ih, body, 0, 0) == cudaSuccess;
+  if (ok) ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    bool cap_ok = true;
+    try {
+      const int nb0 = level_apply_dot<double>(h, F, h->cp, h->cq, h->cp, h->part_a);
+      reduce_dev(h, h->part_a, nb0, S_PQ, fcg ? FIN_ALPHA_FCG : FIN_ALPHA_PCG);
+      k_cg_update<T><<<gv, 256, 0, s>>>(h->cx, h->cr, h->cp, h->cq, h->scal, n, h->part_a, (T*)F.r, (T*)F.x,
+                                        (T*)F.d[0], Dinv<T>(F), (T)F.c0);
+      CK(cudaGetLastError());
+      reduce_dev(h, h->part_a, gv, S_RR, FIN_NONE);
+      k_converge1<<<1, 32, 0, s>>>(h->scal, h->d_loop, h->d_its, h->status, wh, ih);
+      CK(cudaGetLastError());
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t capg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, &deps, nullptr, &nd));
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = ih;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t inode;
+      CK(cudaGraphAddNode(&inode, capg, deps, nullptr, nd, &ip));
+      rest = ip.conditional.phGraph_out[0];
+      CK(cudaStreamUpdateCaptureDependencies(s, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    } catch (Fail&) { cap_ok = false; }
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(s, &out) != cudaSuccess || !cap_ok) ok = false;
+  }
+  if (ok) ok = cudaStreamBeginCaptureToGraph(s, rest, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    bool cap_ok = true;
+    try {
+      T* d = vcycle_body<T>(h, true);
+      k_vc_final_dot<T><<<gv, 256, 0, s>>>((const T*)F.x, d, h->cz, fcg ? h->cq : h->cr, n, h->part_a);
+      CK(cudaGetLastError());
+      reduce_dev(h, h->part_a, gv, fcg ? S_ZQ : S_RZNEW, fcg ? FIN_BETA_FCG : FIN_BETA_PCG);
+      k_p_update<<<gv, 256, 0, s>>>(h->cp, h->cz, h->cr, h->scal, n, fcg ? 1 : 0, fcg ? h->part_a : nullptr);
+      CK(cudaGetLastError());
+      if (fcg) reduce_dev(h, h->part_a, gv, S_PR, FIN_NONE);
+    } catch (Fail&) { cap_ok = false; }
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(s, &out) != cudaSuccess || !cap_ok) ok = false;
+  }
+  if (ok) ok = cudaGraphInstantiate(&h->lgraph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  h->lgraph_state = ok ? 1 : -1;
+  if (!ok) { h->lgraph = nullptr; cudaGetLastError(); }
+}
+
 // PCG (FP64 V-cycle) or flexible CG (FP32 V-cycle) on tree-ordered b (cb) and x (cx).
 template <typename T>
 r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double* relres) {
@@ -1159,6 +1349,44 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
   *relres = rel;
   if (rel <= rtol) return R3MG_OK;
   precondition_restart();
+  if (!h->prof_on && h->lgraph_state >= 0) {
+    // The whole iteration loop as one graph launch.  A conditional WHILE node repeats one
+    // iteration; inside it, the product, alpha, the x/r update and ||r||^2 run first, the stop test
+    // sets both the loop condition and an IF node's condition, and the IF node holds the rest of
+    // the iteration (V-cycle, beta, new direction), so the last iteration does no V-cycle.
+    // Profiled solves keep the host loop below (events time each launch).
+    if (h->lgraph_state == 0) build_loop_graph<T>(h);
+    if (h->lgraph_state == 1) {
+      int done_its = 0;
+      while (done_its < maxit) {
+        k_loop_init<<<1, 32, 0, s>>>(h->d_loop, h->d_its, h->status, rtol * rtol * bb, maxit - done_its);
+        CK(cudaGetLastError());
+        CK(cudaGraphLaunch(h->lgraph, s));
+        int its = 0, st = 0;
+        CK(cudaMemcpyAsync(&h->host_scal[14], h->d_its, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&h->host_scal[15], h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::memcpy(&its, &h->host_scal[14], sizeof(int));
+        std::memcpy(&st, &h->host_scal[15], sizeof(int));
+        // per iteration: product, 2 or 3 reductions, update, stop test, V-cycle graph, final dot, p update
+        h->launches += 1 + (int64_t)its * (h->graph_kernels + (fcg ? 8 : 7));
+        if (st) {
+          CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+          throw Fail{R3MG_E_BREAKDOWN, "CG breakdown: p^T A p <= 0 or non-finite scalar"};
+        }
+        done_its += its;
+        *iters = done_its;
+        double rt = 0.0;
+        true_residual(rt, nullptr);
+        *relres = std::sqrt(rt) / bnorm;
+        if (!std::isfinite(*relres)) throw Fail{R3MG_E_BREAKDOWN, "CG breakdown: non-finite residual"};
+        if (*relres <= rtol) return R3MG_OK;
+        if (done_its >= maxit) break;
+        precondition_restart();   // recursive residual drifted: restart from the true residual
+      }
+      return R3MG_E_NOCONV;
+    }
+  }
   for (int it = 1; it <= maxit; ++it) {
     if (h->prof_on) {
       if (!h->cg_slot.e0) { CK(cudaEventCreate(&h->cg_slot.e0)); CK(cudaEventCreate(&h->cg_slot.e1)); }
@@ -1376,6 +1604,14 @@ void level_cheb_b(r3mg_hierarchy* h, const Level& A, int l, T* x, T* r, T* d, T*
   const int np = h->nprob;
   const double* ta = (post ? B.postA : B.preA) + (int64_t)st * np;
   const double* tc = (post ? B.postC : B.preC) + (int64_t)st * np;
+  if constexpr (sizeof(T) == 4) {
+    if (A.conf[1].form == 4 && A.sym_ok) {
+      SymCheb ep{x, r, d, dn, Dinv<T>(A), 0.f, 0.f};
+      ep.A = ta; ep.C = tc; ep.rprob = B.rprob;
+      sym_step(h, A, d, ep);
+      return;
+    }
+  }
   launch_level<T>(A, d, TEpChebB<T>{x, r, d, dn, Dinv<T>(A), ta, tc, B.rprob}, nullptr, h->stream);
 }
 
@@ -1662,6 +1898,495 @@ void build_batch(r3mg_hierarchy* h, int np, const int64_t* n, const double* cons
   build_device(h, pats, lay, cc.data(), nullptr, nullptr, pieces);
 }
 
+// ================================================================ several right-hand sides
+// M columns per block vector (M in {4, 8, 16}; a caller's m columns are padded with zero
+// columns).  The hierarchy is shared; only the vectors and the per-column CG scalars are new.
+
+int mr_cols(int m) { return m <= 4 ? 4 : m <= 8 ? 8 : 16; }
+
+void mr_free(r3mg_hierarchy* h, void* p) {
+  if (!p) return;
+  cudaFree(p);
+  h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+}
+
+// Block vectors for M columns on every level (V-cycle precision) and the FP64 CG blocks.
+void mr_alloc(r3mg_hierarchy* h, int M) {
+  if (h->mr_M == M) return;
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto* v : {&h->mr_x, &h->mr_r, &h->mr_d0, &h->mr_d1})
+    for (void* p : *v) mr_free(h, p);
+  for (double* p : {h->mr_b, h->mr_xc, h->mr_rc, h->mr_p, h->mr_q, h->mr_z, h->mr_scal, h->mr_pa, h->mr_pb, h->mr_lp})
+    mr_free(h, p);
+  mr_free(h, h->mr_its);
+  mr_free(h, h->mr_active);
+  if (h->mgraph) { cudaGraphExecDestroy(h->mgraph); h->mgraph = nullptr; }
+  h->mgraph_state = 0;
+  h->mr_M = 0;
+  const size_t es = (h->prm.precision == 1) ? 4 : 8;
+  const int L = h->L;
+  h->mr_x.assign(L, nullptr); h->mr_r.assign(L, nullptr); h->mr_d0.assign(L, nullptr); h->mr_d1.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    const int64_t cnt = h->lv[l].n * M * (int64_t)es;
+    h->mr_x[l] = dalloc<unsigned char>(h, cnt);
+    h->mr_r[l] = dalloc<unsigned char>(h, cnt);
+    if (l + 1 < L) {
+      h->mr_d0[l] = dalloc<unsigned char>(h, cnt);
+      h->mr_d1[l] = dalloc<unsigned char>(h, cnt);
+    }
+  }
+  const int64_t nm = h->n * M;
+  h->mr_b = dalloc<double>(h, nm); h->mr_xc = dalloc<double>(h, nm); h->mr_rc = dalloc<double>(h, nm);
+  h->mr_p = dalloc<double>(h, nm); h->mr_q = dalloc<double>(h, nm); h->mr_z = dalloc<double>(h, nm);
+  h->mr_scal = dalloc<double>(h, (int64_t)S_COUNT * M);
+  CK(cudaMemsetAsync(h->mr_scal, 0, sizeof(double) * S_COUNT * M, h->stream));
+  h->mr_npart = std::max<int64_t>(grid_for(nm), (int64_t)h->nsm * 8);
+  h->mr_pa = dalloc<double>(h, h->mr_npart * M);
+  h->mr_pb = dalloc<double>(h, h->mr_npart * M);
+  h->mr_lp = dalloc<double>(h, 2);
+  h->mr_its = dalloc<int>(h, M + 1);   // + the host-driven loop's continue flag
+  h->mr_active = dalloc<int>(h, M);
+  if (!h->mr_host) CK(cudaMallocHost(&h->mr_host, sizeof(double) * 64));
+  h->mr_M = M;
+}
+
+template <typename T, int M, int S, bool FINE, class Ep>
+void mr_launch(const Level& A, const T* x, Ep ep, double* part, cudaStream_t s, int grid) {
+  const LevelView<T> v = view<T>(A);
+  auto kern = k_mr_level<T, M, S, FINE, Ep>;
+  const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 7) & ~(size_t)3);
+  static size_t configured = 48 * 1024;
+  if (sm > configured) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = sm;
+  }
+  kern<<<grid, 256, sm, s>>>(v, x, ep, part);
+  CK(cudaGetLastError());
+}
+
+// One level operator on M columns with S entry slots per row; returns the partial count.
+template <typename T, int M, class Ep>
+int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part, int S) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * 8));
+  const bool fine = (A.b == 0);
+  cudaStream_t s = h->stream;
+  constexpr int CL = M / Slice<T>::V;
+  if (S == 2 && CL * 2 <= 32) {
+    if constexpr (CL * 2 <= 32) { if (fine) mr_launch<T, M, 2, true>(A, x, ep, part, s, grid); else mr_launch<T, M, 2, false>(A, x, ep, part, s, grid); }
+  } else if (S == 8 && CL * 8 <= 32) {
+    if constexpr (CL * 8 <= 32) { if (fine) mr_launch<T, M, 8, true>(A, x, ep, part, s, grid); else mr_launch<T, M, 8, false>(A, x, ep, part, s, grid); }
+  } else {
+    if constexpr (CL * 4 <= 32) { if (fine) mr_launch<T, M, 4, true>(A, x, ep, part, s, grid); else mr_launch<T, M, 4, false>(A, x, ep, part, s, grid); }
+  }
+  return grid;
+}
+
+// Entry slots per row, per level: the fastest of S in {2, 4, 8} (as far as the lanes allow) for
+// one Chebyshev step on the block vectors, timed with events at setup of the block path.
+template <typename T, int M>
+void mr_tune(r3mg_hierarchy* h) {
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  std::vector<int>& Sv = h->mr_S[pi];
+  if ((int)Sv.size() == h->L) return;
+  Sv.assign(h->L, 4);
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  constexpr int CL = M / Slice<T>::V;
+  for (int l = 0; l + 1 < h->L; ++l) {
+    Level& A = h->lv[l];
+    T* x = (T*)h->mr_x[l]; T* r = (T*)h->mr_r[l]; T* d = (T*)h->mr_d0[l]; T* dn = (T*)h->mr_d1[l];
+    CK(cudaMemsetAsync(x, 0, sizeof(T) * A.n * M, s));
+    CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
+    CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
+    float best = 1e30f;
+    for (int S : {2, 4, 8}) {
+      if (CL * S > 32) continue;
+      MEpCheb<T, M> ep{x, r, d, dn, Dinv<T>(A), T(0), T(0)};
+      mr_level<T, M>(h, A, d, ep, nullptr, S);
+      CK(cudaEventRecord(e0, s));
+      for (int k = 0; k < 3; ++k) mr_level<T, M>(h, A, d, ep, nullptr, S);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; Sv[l] = S; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+// The FP64 fine product's slot count (CG product and true residual).
+template <int M>
+int mr_S64(r3mg_hierarchy* h) {
+  if (h->mr_S[0].empty()) {
+    // FP64 blocks: tuned on level 0 only when the V-cycle itself is FP32
+    if (h->prm.precision == 1) {
+      std::vector<int> keep = h->mr_S[1];
+      h->mr_S[0].assign(h->L, 4);
+      constexpr int CL = M / Slice<double>::V;
+      cudaStream_t s = h->stream;
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int S : {2, 4, 8}) {
+        if (CL * S > 32) continue;
+        mr_level<double, M>(h, h->lv[0], h->mr_p, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S);
+        CK(cudaEventRecord(e0, s));
+        for (int k = 0; k < 3; ++k) mr_level<double, M>(h, h->lv[0], h->mr_p, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; h->mr_S[0][0] = S; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    } else {
+      mr_tune<double, M>(h);
+    }
+  }
+  return h->mr_S[0][0];
+}
+
+template <typename T, int M>
+T* mr_vcycle_body(r3mg_hierarchy* h, bool capturing) {
+  cudaStream_t s = h->stream;
+  const int L = h->L, b = h->b;
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  std::vector<int> cur(L, 0);
+  auto dbuf = [&](int l, int k) { return (T*)(k == 0 ? h->mr_d0[l] : h->mr_d1[l]); };
+  int64_t nk = 0;
+  h->slot_next = 0;
+  for (int l = 0; l < L - 1; ++l) {
+    Level& A = h->lv[l];
+    T* x = (T*)h->mr_x[l]; T* r = (T*)h->mr_r[l];
+    for (auto& ac : A.pre) {
+      T* d = dbuf(l, cur[l]); T* dn = dbuf(l, cur[l] ^ 1);
+      const int ps = prof_begin(h, 1 + l, capturing);
+      mr_level<T, M>(h, A, d, MEpCheb<T, M>{x, r, d, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, h->mr_S[pi][l]);
+      prof_end(h, ps, capturing);
+      cur[l] ^= 1;
+      ++nk;
+    }
+    Level& C = h->lv[l + 1];
+    const bool coarsest = (l + 1 == L - 1);
+    MNextInit<T, M> nx{(T*)h->mr_r[l + 1], coarsest ? nullptr : (T*)h->mr_x[l + 1],
+                       coarsest ? nullptr : dbuf(l + 1, 0), Dinv<T>(C), (T)C.c0};
+    if (l == 0)
+      k_mr_restrict_fine<T, M, MNextInit<T, M>><<<(int)std::min<int64_t>(C.nbox, 148 * 64), 256, 0, s>>>(
+          Pmat<T>(h, 0), r, A.box_row, C.nbox, b, nx);
+    else
+      k_mr_restrict_coarse<T, M, MNextInit<T, M>><<<grid_for(C.nbox * b * M), 256, 0, s>>>(Pmat<T>(h, l), r, C.nbox,
+                                                                                         b, h->fan, nx);
+    CK(cudaGetLastError());
+    ++nk;
+  }
+  k_mr_dense<T, M><<<grid_for(h->nc * 32), 256, 0, s>>>(Ainv<T>(h), h->ncp, (const T*)h->mr_r[L - 1], h->nc,
+                                                        (T*)h->mr_x[L - 1]);
+  CK(cudaGetLastError());
+  ++nk;
+  for (int l = L - 2; l >= 0; --l) {
+    Level& A = h->lv[l];
+    const bool coarsest = (l + 1 == L - 1);
+    const T* x1 = (const T*)h->mr_x[l + 1];
+    const T* d1 = coarsest ? nullptr : dbuf(l + 1, cur[l + 1]);
+    T* d = dbuf(l, cur[l]);
+    if (l == 0)
+      k_mr_prolong_fine<T, M><<<grid_for(h->n * M), 256, 0, s>>>(Pmat<T>(h, 0), h->box_of_tree, x1, d1, h->n, b, d);
+    else
+      k_mr_prolong_coarse<T, M><<<grid_for(A.nbox * b * M), 256, 0, s>>>(Pmat<T>(h, l), x1, d1, A.nbox, b, h->fan, d);
+    CK(cudaGetLastError());
+    ++nk;
+    T* x = (T*)h->mr_x[l]; T* r = (T*)h->mr_r[l];
+    for (auto& ac : A.post) {
+      T* dd = dbuf(l, cur[l]); T* dn = dbuf(l, cur[l] ^ 1);
+      const int ps = prof_begin(h, 1 + l, capturing);
+      mr_level<T, M>(h, A, dd, MEpCheb<T, M>{x, r, dd, dn, Dinv<T>(A), (T)ac.first, (T)ac.second}, nullptr, h->mr_S[pi][l]);
+      prof_end(h, ps, capturing);
+      cur[l] ^= 1;
+      ++nk;
+    }
+  }
+  if (capturing) h->mr_graph_kernels = nk; else h->launches += nk;
+  return dbuf(0, cur[0]);
+}
+
+// One V-cycle on M columns of the FP64 block r_blk (tree order, interleaved) into z_blk.
+template <typename T, int M>
+void mr_vcycle_apply(r3mg_hierarchy* h, const double* r_blk, double* z_blk) {
+  Level& F = h->lv[0];
+  const int64_t nm = h->n * M;
+  mr_tune<T, M>(h);
+  k_mr_vc_init<T, M><<<grid_for(nm), 256, 0, h->stream>>>(r_blk, nm, (T*)h->mr_r[0], (T*)h->mr_x[0],
+                                                         (T*)h->mr_d0[0], Dinv<T>(F), (T)F.c0);
+  CK(cudaGetLastError());
+  T* d = mr_vcycle_body<T, M>(h, false);
+  k_mr_vc_final_dot<T, M><<<grid_for(nm), 256, 0, h->stream>>>((const T*)h->mr_x[0], d, z_blk, r_blk, nm, h->mr_pa);
+  CK(cudaGetLastError());
+}
+
+template <int M>
+void mr_reduce(r3mg_hierarchy* h, const double* part, int nb, int slot, int fin) {
+  k_mr_reduce<M><<<1, 32 * M, 0, h->stream>>>(part, nb, h->mr_scal, slot, fin, h->mr_active, h->status);
+  CK(cudaGetLastError());
+}
+
+// The multi-column CG/FCG loop as one graph: WHILE { product, alpha, update, ||r||, stop test,
+// IF { V-cycle, beta, direction } } (the single-vector loop's structure, per column).
+template <typename T, int M>
+void mr_build_graph(r3mg_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  Level& F = h->lv[0];
+  const int64_t nm = h->n * M;
+  const bool fcg = (h->prm.precision == 1);
+  const int gv = grid_for(nm);
+  const int S64 = mr_S64<M>(h);
+  cudaGraph_t g = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  cudaGraphConditionalHandle wh{}, ih{};
+  cudaGraph_t body = nullptr, rest = nullptr;
+  if (ok) ok = cudaGraphConditionalHandleCreate(&wh, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = wh;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    ok = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp) == cudaSuccess;
+    if (ok) body = wp.conditional.phGraph_out[0];
+  }
+  if (ok) ok = cudaGraphConditionalHandleCreate(&ih, body, 0, 0) == cudaSuccess;
+  if (ok) ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    bool cap_ok = true;
+    try {
+      const int nb = mr_level<double, M>(h, F, h->mr_p, MEpApply<double, M>{h->mr_q, h->mr_p}, h->mr_pa, S64);
+      mr_reduce<M>(h, h->mr_pa, nb, S_PQ, fcg ? FIN_ALPHA_FCG : FIN_ALPHA_PCG);
+      k_mr_cg_update<T, M><<<gv, 256, 0, s>>>(h->mr_xc, h->mr_rc, h->mr_p, h->mr_q, h->mr_scal, nm, h->mr_pa,
+                                              (T*)h->mr_r[0], (T*)h->mr_x[0], (T*)h->mr_d0[0], Dinv<T>(F), (T)F.c0);
+      CK(cudaGetLastError());
+      mr_reduce<M>(h, h->mr_pa, gv, S_RR, FIN_NONE);
+      k_mr_converge<M><<<1, 32, 0, s>>>(h->mr_scal, h->mr_lp, h->mr_its, h->mr_active, h->status, wh, ih, 1, nullptr);
+      CK(cudaGetLastError());
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t capg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, &deps, nullptr, &nd));
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = ih;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t inode;
+      CK(cudaGraphAddNode(&inode, capg, deps, nullptr, nd, &ip));
+      rest = ip.conditional.phGraph_out[0];
+      CK(cudaStreamUpdateCaptureDependencies(s, &inode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    } catch (Fail&) { cap_ok = false; }
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(s, &out) != cudaSuccess || !cap_ok) ok = false;
+  }
+  if (ok) ok = cudaStreamBeginCaptureToGraph(s, rest, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    bool cap_ok = true;
+    try {
+      T* d = mr_vcycle_body<T, M>(h, true);
+      k_mr_vc_final_dot<T, M><<<gv, 256, 0, s>>>((const T*)h->mr_x[0], d, h->mr_z, fcg ? h->mr_q : h->mr_rc, nm,
+                                                  h->mr_pa);
+      CK(cudaGetLastError());
+      mr_reduce<M>(h, h->mr_pa, gv, fcg ? S_ZQ : S_RZNEW, fcg ? FIN_BETA_FCG : FIN_BETA_PCG);
+      k_mr_p_update<M><<<gv, 256, 0, s>>>(h->mr_p, h->mr_z, h->mr_rc, h->mr_scal, nm, fcg ? 1 : 0,
+                                          fcg ? h->mr_pa : nullptr);
+      CK(cudaGetLastError());
+      if (fcg) mr_reduce<M>(h, h->mr_pa, gv, S_PR, FIN_NONE);
+    } catch (Fail&) { cap_ok = false; }
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(s, &out) != cudaSuccess || !cap_ok) ok = false;
+  }
+  if (ok) ok = cudaGraphInstantiate(&h->mgraph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  h->mgraph_state = ok ? 1 : -1;
+  if (!ok) { h->mgraph = nullptr; cudaGetLastError(); }
+}
+
+__global__ void k_mr_set_loop(double* lp, double rtol2, int budget) {
+  if (threadIdx.x == 0) { lp[0] = rtol2; lp[1] = (double)budget; }
+}
+
+// Zero the columns of x whose right-hand side is zero (their solution is x = 0).
+__global__ void k_mr_zero_cols(double* x, int64_t nm, int M, unsigned mask) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nm; t += (int64_t)gridDim.x * blockDim.x)
+    if ((mask >> (t % M)) & 1u) x[t] = 0.0;
+}
+
+// PCG / FCG on m <= M columns at once: b and x in mr_b / mr_xc (tree order, interleaved).
+template <typename T, int M>
+r3mg_status mr_krylov(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its_out, double* rel_out) {
+  cudaStream_t s = h->stream;
+  Level& F = h->lv[0];
+  const int64_t nm = h->n * M;
+  const bool fcg = (h->prm.precision == 1);
+  const int gv = grid_for(nm);
+  mr_tune<T, M>(h);
+  const int S64 = mr_S64<M>(h);
+  double* hs = h->mr_host;                       // [0, 16) rr, [16, 32) bb, [32, 48) its / active
+  int* hi = reinterpret_cast<int*>(hs + 32);     // its: hi[0..16), active: hi[16..32)
+  auto true_residual = [&](bool with_bb) {
+    mr_level<double, M>(h, F, h->mr_xc, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S64);
+    k_mr_residual<M><<<gv, 256, 0, s>>>(h->mr_b, h->mr_q, h->mr_rc, nm, h->mr_pa, with_bb ? h->mr_pb : nullptr);
+    CK(cudaGetLastError());
+    k_mr_reduce<M><<<1, 32 * M, 0, s>>>(h->mr_pa, gv, h->mr_scal, S_RR, FIN_NONE, nullptr, nullptr);
+    if (with_bb) k_mr_reduce<M><<<1, 32 * M, 0, s>>>(h->mr_pb, gv, h->mr_scal, S_BB, FIN_NONE, nullptr, nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hs, h->mr_scal + S_RR * M, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+    if (with_bb) CK(cudaMemcpyAsync(hs + 16, h->mr_scal + S_BB * M, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->launches += with_bb ? 4 : 3;
+  };
+  auto restart = [&]() {   // z = M r; p = z; per column rz (PCG) or pr (FCG)
+    mr_vcycle_apply<T, M>(h, h->mr_rc, h->mr_z);
+    mr_reduce<M>(h, h->mr_pa, gv, fcg ? S_PR : S_RZ, FIN_NONE);
+    CK(cudaMemcpyAsync(h->mr_p, h->mr_z, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+    h->launches += 3;
+  };
+  true_residual(true);
+  std::vector<double> bb(M), rel(M, 0.0);
+  std::vector<int> its(M, 0), act(M, 0);
+  unsigned zero_mask = 0;
+  for (int c = 0; c < M; ++c) {
+    bb[c] = hs[16 + c];
+    if (c < m && bb[c] == 0.0) zero_mask |= 1u << c;
+    rel[c] = (bb[c] > 0.0) ? std::sqrt(hs[c] / bb[c]) : 0.0;
+    act[c] = (c < m && bb[c] > 0.0 && !(rel[c] <= rtol) && maxit > 0) ? 1 : 0;
+  }
+  if (zero_mask) {
+    k_mr_zero_cols<<<gv, 256, 0, s>>>(h->mr_xc, nm, M, zero_mask);
+    CK(cudaGetLastError());
+  }
+  auto upload_active = [&]() {
+    for (int c = 0; c < M; ++c) { hi[c] = its[c]; hi[16 + c] = act[c]; }
+    CK(cudaMemcpyAsync(h->mr_its, hi, sizeof(int) * M, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->mr_active, hi + 16, sizeof(int) * M, cudaMemcpyHostToDevice, s));
+  };
+  bool any = false;
+  for (int c = 0; c < M; ++c) any = any || act[c];
+  if (any) {
+    upload_active();
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+    restart();
+    if (!h->prof_on) {
+      if (h->mgraph_state == 0) mr_build_graph<T, M>(h);
+      if (h->mgraph_state != 1) throw Fail{R3MG_E_CUDA, "pcg_multi: the conditional loop graph could not be built"};
+    }
+    while (true) {
+      k_mr_set_loop<<<1, 32, 0, s>>>(h->mr_lp, rtol * rtol, maxit);
+      CK(cudaGetLastError());
+      if (!h->prof_on) {
+        CK(cudaGraphLaunch(h->mgraph, s));
+      } else {
+        // profiled solves: the same iteration driven from the host, events around the level
+        // operators (kind 0: the FP64 block product, kind 1 + l: Chebyshev steps on level l)
+        const cudaGraphConditionalHandle none{};
+        int* go = h->mr_its + M;
+        for (int it = 0; it < maxit; ++it) {
+          if (!h->cg_slot.e0) { CK(cudaEventCreate(&h->cg_slot.e0)); CK(cudaEventCreate(&h->cg_slot.e1)); }
+          CK(cudaEventRecord(h->cg_slot.e0, s));
+          const int nb = mr_level<double, M>(h, F, h->mr_p, MEpApply<double, M>{h->mr_q, h->mr_p}, h->mr_pa, S64);
+          CK(cudaEventRecord(h->cg_slot.e1, s));
+          h->cg_pending = true;
+          mr_reduce<M>(h, h->mr_pa, nb, S_PQ, fcg ? FIN_ALPHA_FCG : FIN_ALPHA_PCG);
+          k_mr_cg_update<T, M><<<gv, 256, 0, s>>>(h->mr_xc, h->mr_rc, h->mr_p, h->mr_q, h->mr_scal, nm, h->mr_pa,
+                                                  (T*)h->mr_r[0], (T*)h->mr_x[0], (T*)h->mr_d0[0], Dinv<T>(F), (T)F.c0);
+          CK(cudaGetLastError());
+          mr_reduce<M>(h, h->mr_pa, gv, S_RR, FIN_NONE);
+          k_mr_converge<M><<<1, 32, 0, s>>>(h->mr_scal, h->mr_lp, h->mr_its, h->mr_active, h->status, none, none, 0, go);
+          CK(cudaGetLastError());
+          CK(cudaMemcpyAsync(hi + 48, go, sizeof(int), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          prof_harvest(h);
+          h->launches += 5;
+          if (!hi[48]) break;
+          T* d = mr_vcycle_body<T, M>(h, false);
+          k_mr_vc_final_dot<T, M><<<gv, 256, 0, s>>>((const T*)h->mr_x[0], d, h->mr_z, fcg ? h->mr_q : h->mr_rc, nm,
+                                                      h->mr_pa);
+          CK(cudaGetLastError());
+          mr_reduce<M>(h, h->mr_pa, gv, fcg ? S_ZQ : S_RZNEW, fcg ? FIN_BETA_FCG : FIN_BETA_PCG);
+          k_mr_p_update<M><<<gv, 256, 0, s>>>(h->mr_p, h->mr_z, h->mr_rc, h->mr_scal, nm, fcg ? 1 : 0,
+                                              fcg ? h->mr_pa : nullptr);
+          CK(cudaGetLastError());
+          if (fcg) mr_reduce<M>(h, h->mr_pa, gv, S_PR, FIN_NONE);
+          h->launches += fcg ? 5 : 4;
+        }
+      }
+      CK(cudaMemcpyAsync(hi, h->mr_its, sizeof(int) * M, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(hi + 32, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      int added = 0;
+      for (int c = 0; c < M; ++c) { added = std::max(added, hi[c] - its[c]); its[c] = hi[c]; }
+      if (!h->prof_on) h->launches += 1 + (int64_t)added * (h->mr_graph_kernels + (fcg ? 9 : 8));
+      if (hi[32]) {
+        CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+        throw Fail{R3MG_E_BREAKDOWN, "pcg_multi: breakdown (p^T A p <= 0 or non-finite scalar) in a column"};
+      }
+      true_residual(false);
+      bool again = false;
+      for (int c = 0; c < M; ++c) {
+        if (c >= m || bb[c] == 0.0) { act[c] = 0; continue; }
+        rel[c] = std::sqrt(hs[c] / bb[c]);
+        if (!std::isfinite(rel[c])) throw Fail{R3MG_E_BREAKDOWN, "pcg_multi: non-finite residual"};
+        act[c] = (rel[c] > rtol && its[c] < maxit) ? 1 : 0;
+        again = again || act[c];
+      }
+      if (!again) break;
+      upload_active();   // recursive residual drifted in some column: restart those from the true residual
+      restart();
+    }
+  }
+  bool conv = true;
+  for (int c = 0; c < m; ++c) {
+    its_out[c] = its[c];
+    rel_out[c] = rel[c];
+    conv = conv && rel[c] <= rtol;
+  }
+  return conv ? R3MG_OK : R3MG_E_NOCONV;
+}
+
+template <int M>
+r3mg_status mr_dispatch_solve(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its, double* rel) {
+  mr_alloc(h, M);
+  return (h->prm.precision == 1) ? mr_krylov<float, M>(h, m, rtol, maxit, its, rel)
+                                 : mr_krylov<double, M>(h, m, rtol, maxit, its, rel);
+}
+
+template <int M>
+void mr_dispatch_vcycle(r3mg_hierarchy* h) {
+  mr_alloc(h, M);
+  if (h->prm.precision == 1) mr_vcycle_apply<float, M>(h, h->mr_b, h->mr_z);
+  else mr_vcycle_apply<double, M>(h, h->mr_b, h->mr_z);
+}
+
+// Y = A_l X on M columns: FP64 values (fp32 = 0) or the FP32 V-cycle values (fp32 = 1).
+template <typename T, int M>
+void mr_apply_level(r3mg_hierarchy* h, int level, const double* x_blk, double* y_blk) {
+  Level& A = h->lv[level];
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  if (pi == 1) mr_tune<float, M>(h); else mr_S64<M>(h);
+  const int S = pi == 1 ? h->mr_S[1][std::min(level, h->L - 2)] : (level == 0 ? h->mr_S[0][0] : 4);
+  const int64_t nm = A.n * M;
+  // scratch of level 0's size in the right precision (level 0 is the largest level)
+  T* xt = pi == 1 ? (T*)h->mr_d0[0] : (T*)h->mr_p;
+  T* yt = pi == 1 ? (T*)h->mr_d1[0] : (T*)h->mr_q;
+  k_convert<double, T><<<grid_for(nm), 256, 0, h->stream>>>(x_blk, xt, nm);
+  mr_level<T, M>(h, A, xt, MEpApply<T, M>{yt, nullptr}, nullptr, S);
+  k_convert<T, double><<<grid_for(nm), 256, 0, h->stream>>>(yt, y_blk, nm);
+  CK(cudaGetLastError());
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -1809,6 +2534,7 @@ r3mg_status r3mg_batch_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev
     k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(b_dev, h->perm, h->cb, h->n);
     k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(x_dev, h->perm, h->cx, h->n);
     CK(cudaGetLastError());
+    if (h->prof_on) h->prof_cols = 1;
     res = (h->prm.precision == 1) ? krylov_batch<float>(h, rtol, maxit, iters_out, relres_out)
                                   : krylov_batch<double>(h, rtol, maxit, iters_out, relres_out);
     k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cx, h->perm, x_dev, h->n);
@@ -1869,6 +2595,7 @@ r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, doub
     k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(b_dev, h->perm, h->cb, h->n);
     k_gather_perm<double, double><<<gv, 256, 0, h->stream>>>(x_dev, h->perm, h->cx, h->n);
     CK(cudaGetLastError());
+    if (h->prof_on) h->prof_cols = 1;
     res = (h->prm.precision == 1) ? krylov<float>(h, rtol, maxit, &it, &rel) : krylov<double>(h, rtol, maxit, &it, &rel);
     k_scatter_perm<double, double><<<gv, 256, 0, h->stream>>>(h->cx, h->perm, x_dev, h->n);
     CK(cudaGetLastError());
@@ -1887,6 +2614,83 @@ r3mg_status r3mg_pcg(r3mg_hierarchy* h, const double* b_dev, double* x_dev, doub
   if (st != R3MG_OK) return st;
   if (res == R3MG_E_NOCONV) h->err = "PCG: maximum iterations reached";
   return res;
+}
+
+r3mg_status r3mg_pcg_multi(r3mg_hierarchy* h, int m, const double* b_dev, double* x_dev, double rtol, int maxit,
+                           int* iters_out, double* relres_out, void* stream) {
+  if (!h || m < 1 || m > 16 || !b_dev || !x_dev || !iters_out || !relres_out || maxit < 0 || !(rtol >= 0.0))
+    return R3MG_E_ARG;
+  if (!h->bl.empty()) { h->err = "pcg_multi: batched hierarchy"; return R3MG_E_ARG; }
+  r3mg_status res = R3MG_OK;
+  for (int c = 0; c < m; ++c) { iters_out[c] = 0; relres_out[c] = 0.0; }
+  r3mg_status st = guarded(h, [&] {
+    StreamJoin j(h, stream);
+    const int M = mr_cols(m);
+    mr_alloc(h, M);
+    const int64_t nm = h->n * M;
+    k_mr_gather<<<grid_for(nm), 256, 0, h->stream>>>(b_dev, h->perm, h->n, m, M, h->mr_b);
+    k_mr_gather<<<grid_for(nm), 256, 0, h->stream>>>(x_dev, h->perm, h->n, m, M, h->mr_xc);
+    CK(cudaGetLastError());
+    if (h->prof_on) h->prof_cols = M;
+    res = M == 4 ? mr_dispatch_solve<4>(h, m, rtol, maxit, iters_out, relres_out)
+        : M == 8 ? mr_dispatch_solve<8>(h, m, rtol, maxit, iters_out, relres_out)
+                 : mr_dispatch_solve<16>(h, m, rtol, maxit, iters_out, relres_out);
+    k_mr_scatter<<<grid_for(nm), 256, 0, h->stream>>>(h->mr_xc, h->perm, h->n, m, M, x_dev);
+    CK(cudaGetLastError());
+    h->launches += 3;
+    CK(cudaStreamSynchronize(h->stream));
+    prof_harvest(h);
+  });
+  if (st != R3MG_OK) return st;
+  if (res == R3MG_E_NOCONV) h->err = "pcg_multi: maximum iterations reached in some column";
+  return res;
+}
+
+r3mg_status r3mg_vcycle_multi(r3mg_hierarchy* h, int m, const double* r_dev, double* z_dev, void* stream) {
+  if (!h || m < 1 || m > 16 || !r_dev || !z_dev) return R3MG_E_ARG;
+  if (!h->bl.empty()) { h->err = "vcycle_multi: batched hierarchy"; return R3MG_E_ARG; }
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    const int M = mr_cols(m);
+    mr_alloc(h, M);
+    const int64_t nm = h->n * M;
+    k_mr_gather<<<grid_for(nm), 256, 0, h->stream>>>(r_dev, h->perm, h->n, m, M, h->mr_b);
+    CK(cudaGetLastError());
+    if (M == 4) mr_dispatch_vcycle<4>(h); else if (M == 8) mr_dispatch_vcycle<8>(h); else mr_dispatch_vcycle<16>(h);
+    k_mr_scatter<<<grid_for(nm), 256, 0, h->stream>>>(h->mr_z, h->perm, h->n, m, M, z_dev);
+    CK(cudaGetLastError());
+  });
+}
+
+r3mg_status r3mg_level_apply_multi(r3mg_hierarchy* h, int level, int m, int fp32, const double* x_dev, double* y_dev,
+                                   void* stream) {
+  if (!h || level < 0 || level >= h->L || m < 1 || m > 16 || !x_dev || !y_dev) return R3MG_E_ARG;
+  if (!h->bl.empty()) { h->err = "level_apply_multi: batched hierarchy"; return R3MG_E_ARG; }
+  if (fp32 && h->prm.precision != 1) { h->err = "level_apply_multi: the hierarchy has no FP32 values"; return R3MG_E_ARG; }
+  if (fp32 && level == h->L - 1) {
+    h->err = "level_apply_multi: the coarsest level has no FP32 values (it is solved with its inverse)";
+    return R3MG_E_ARG;
+  }
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    const int M = mr_cols(m);
+    mr_alloc(h, M);
+    const int64_t nl = h->lv[level].n, nm = nl * M;
+    // caller columns -> interleaved block (level 0: caller numbering -> tree order)
+    double* xb = h->mr_b;
+    double* yb = h->mr_z;
+    k_mr_gather<<<grid_for(nm), 256, 0, h->stream>>>(x_dev, level == 0 ? h->perm : nullptr, nl, m, M, xb);
+    CK(cudaGetLastError());
+    auto run = [&](auto tag) {
+      constexpr int MM = decltype(tag)::value;
+      if (fp32) mr_apply_level<float, MM>(h, level, xb, yb); else mr_apply_level<double, MM>(h, level, xb, yb);
+    };
+    if (M == 4) run(std::integral_constant<int, 4>{});
+    else if (M == 8) run(std::integral_constant<int, 8>{});
+    else run(std::integral_constant<int, 16>{});
+    k_mr_scatter<<<grid_for(nm), 256, 0, h->stream>>>(yb, level == 0 ? h->perm : nullptr, nl, m, M, y_dev);
+    CK(cudaGetLastError());
+  });
 }
 
 r3mg_status r3mg_pcg_host(r3mg_hierarchy* h, const double* b_host, double* x_host, double rtol, int maxit,
@@ -2011,14 +2815,16 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
       // algorithmic bytes: stored nonzeros (padding excluded) x (value + index bytes), one
       // 8-byte row pointer per row, and every vector read or written once
       const bool f32 = (h->prm.precision == 1);
+      // (block solves: cols vectors of every kind; the matrix is read once for all of them)
+      const double cols = (double)h->prof_cols;
       if (kind == 0) {
         const Level& F = h->lv[0];
-        *bytes_per_launch = (double)F.nnz * (8 + 2) + 8.0 * (F.n + 1) + 2.0 * 8.0 * F.n;
+        *bytes_per_launch = (double)F.nnz * (8 + 2) + 8.0 * (F.n + 1) + 2.0 * 8.0 * F.n * cols;
       } else {
         const Level& A = h->lv[kind - 1];
         const double es = f32 ? 4.0 : 8.0;
         const double ib = (A.b == 0) ? 2.0 : 0.0;
-        *bytes_per_launch = (double)A.nnz * (es + ib) + 8.0 * (A.n + 1) + 7.0 * es * A.n +
+        *bytes_per_launch = (double)A.nnz * (es + ib) + 8.0 * (A.n + 1) + (6.0 * cols + 1.0) * es * A.n +
                             (A.b == 0 ? 0.0 : 8.0 * (double)A.npairs);
       }
     }
@@ -2046,7 +2852,7 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
     if (h) h->err = "set_kernel_config: unroll 4 is an FP64 option (0 = default)";
     return R3MG_E_ARG;
   }
-  if (!h || level < 0 || level >= h->L || form < 0 || form > 3 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
+  if (!h || level < 0 || level >= h->L || form < 0 || form > 4 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
       (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || (form == 1 && threads == 128)) {
     if (h) h->err = "set_kernel_config: invalid level, form (0..3), lanes (4,8,16,32) or threads (128 register forms only, 256, 512, 1024)";
     return R3MG_E_ARG;
@@ -2055,12 +2861,12 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
   const int pi = fp32 ? 1 : 0;
   if (fp32 && h->prm.precision != 1) { h->err = "set_kernel_config: the hierarchy has no FP32 V-cycle"; return R3MG_E_ARG; }
   if (form == 1 && A.tma[pi].nitems == 0) { h->err = "set_kernel_config: no TMA work items on this level"; return R3MG_E_ARG; }
+  if (form == 4 && (!fp32 || !A.sym_ok)) { h->err = "set_kernel_config: no symmetric block form on this level"; return R3MG_E_ARG; }
   if (form == 2 && 2 * level_smem_bytes(view<double>(A)) > kMaxSmem) { h->err = "set_kernel_config: windows too large"; return R3MG_E_ARG; }
   return guarded(h, [&] {
     CK(cudaStreamSynchronize(h->stream));
     A.conf[pi] = Level::KConf{form, lanes, threads, 0.f, unroll};
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
-    h->graph_state = 0;   // recaptured at the next V-cycle
+    drop_graphs(h);   // recaptured at the next V-cycle / solve
   });
 }
 
@@ -2069,7 +2875,7 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
   const Level::KConf& c = h->lv[level].conf[fp32 ? 1 : 0];
   const bool tma = c.form == 1 && h->lv[level].tma[fp32 ? 1 : 0].nitems > 0;
-  if (form) *form = tma ? 1 : (c.form == 2 || c.form == 3 ? c.form : 0);
+  if (form) *form = tma ? 1 : (c.form == 2 || c.form == 3 || (c.form == 4 && h->lv[level].sym_ok) ? c.form : 0);
   if (lanes) *lanes = c.G;
   if (threads) *threads = tma ? c.nt : (c.nt == 128 ? 128 : 256);
   if (tuned_ms) *tuned_ms = c.ms;
@@ -2089,6 +2895,9 @@ void r3mg_destroy(r3mg_hierarchy* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
+  if (h->lgraph) cudaGraphExecDestroy(h->lgraph);
+  if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
+  if (h->mr_host) cudaFreeHost(h->mr_host);
   for (auto& sl : h->slots) { cudaEventDestroy(sl.e0); cudaEventDestroy(sl.e1); }
   if (h->cg_slot.e0) { cudaEventDestroy(h->cg_slot.e0); cudaEventDestroy(h->cg_slot.e1); }
   for (void* p : h->allocs) cudaFree(p);

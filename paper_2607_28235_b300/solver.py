@@ -107,6 +107,35 @@ class Hierarchy:
             _check(rc, self._h)
         return x, it.value, rel.value
 
+    def pcg_multi(self, B: torch.Tensor, X0: torch.Tensor | None = None, rtol: float = 1e-8, maxit: int = 500,
+                  raise_on_noconv: bool = True):
+        """m <= 16 right-hand sides at once: B is (m, n) float64 on the GPU, one system per row."""
+        B = B.contiguous()
+        assert B.is_cuda and B.dtype == torch.float64 and B.dim() == 2 and B.shape[1] == self.n
+        m = B.shape[0]
+        X = torch.zeros_like(B) if X0 is None else X0.clone().contiguous()
+        its = np.zeros(m, np.int32)
+        rel = np.zeros(m, np.float64)
+        rc = lib().r3mg_pcg_multi(self._h, m, _p(B), _p(X), float(rtol), int(maxit), _p(its), _p(rel), _stream())
+        if rc != 0 and not (rc == 7 and not raise_on_noconv):
+            _check(rc, self._h)
+        return X, its, rel
+
+    def vcycle_multi(self, R: torch.Tensor) -> torch.Tensor:
+        R = R.contiguous()
+        assert R.is_cuda and R.dtype == torch.float64 and R.dim() == 2 and R.shape[1] == self.n
+        Z = torch.empty_like(R)
+        _check(lib().r3mg_vcycle_multi(self._h, R.shape[0], _p(R), _p(Z), _stream()), self._h)
+        return Z
+
+    def level_apply_multi(self, level: int, X: torch.Tensor, fp32: bool = False) -> torch.Tensor:
+        X = X.contiguous()
+        assert X.is_cuda and X.dtype == torch.float64 and X.dim() == 2
+        Y = torch.empty_like(X)
+        _check(lib().r3mg_level_apply_multi(self._h, int(level), X.shape[0], 1 if fp32 else 0, _p(X), _p(Y),
+                                            _stream()), self._h)
+        return Y
+
     def pcg_host(self, b: np.ndarray, x0: np.ndarray | None = None, rtol: float = 1e-8, maxit: int = 500):
         """Host buffers in and out; the copies happen inside the library call."""
         b = np.ascontiguousarray(b, dtype=np.float64)
@@ -174,7 +203,7 @@ class Hierarchy:
                                                 ctypes.byref(ms)), self._h)
                 un = ctypes.c_int(0)
                 _check(lib().r3mg_kernel_unroll(self._h, lev, fp32, ctypes.byref(un)), self._h)
-                row[key] = {"form": ["register", "tma", "register_persistent", "register_l2_prefetch"][f.value], "lanes": g.value,
+                row[key] = {"form": ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block"][f.value], "lanes": g.value,
                             "threads": t.value, "unroll": un.value,
                             "tuned_ms": round(ms.value, 5)}
             out.append(row)
@@ -182,7 +211,7 @@ class Hierarchy:
 
     def set_kernel_config(self, config: list):
         """Replay a configuration returned by kernel_config() (same hierarchy shape)."""
-        forms = {"register": 0, "tma": 1, "register_persistent": 2, "register_l2_prefetch": 3}
+        forms = {"register": 0, "tma": 1, "register_persistent": 2, "register_l2_prefetch": 3, "symmetric_block": 4}
         for lev, row in enumerate(config):
             for fp32, key in ((0, "f64"), (1, "f32")):
                 if key not in row or (fp32 and self.params["precision"] != 1):

@@ -1,0 +1,169 @@
+"""Several right-hand sides on one hierarchy (block vectors, through the C ABI) against the oracle,
+column by column.
+
+Tolerances: FP64 block level products 1e-13 relative (as the single-vector product); FP32 block
+products within (row entries + 2) * 2^-24 * (|A| |x|)_i per row, the rounding bound of a
+length-k FP32 dot product with rounded inputs; FP64 block V-cycle 1e-12 relative per column;
+FP32 block V-cycle no less accurate against the FP64 oracle than the single-vector FP32
+V-cycle (4x its error); PCG per column: iterations +-1 and the solution within 1e-10 relative
+of the oracle's PCG (FP64), or the FP64 residual reached and the solution within 1e3 * rtol (FP32
+V-cycle inside FCG).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle.hierarchy import Params
+from tests.gpu_cases import CASES, make
+
+pytestmark = pytest.mark.gpu
+
+
+def _hier(P, params, precision=0):
+    import paper_2607_28235_b300 as R
+    return R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, precision=precision, **params)
+
+
+def _oracle(P, params, A=None):
+    return O.build_hierarchy(P.coords, P.scipy() if A is None else A,
+                             Params(params["leaf_size"], params["pprime"], params["levels"],
+                                    cheb_degree=params["cheb_degree"]))
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def trio(request):
+    P, params = make(request.param)
+    return P, params, _hier(P, params), _hier(P, params, precision=1), _oracle(P, params)
+
+
+def _rhs(P, m, seed):
+    B = np.random.default_rng(seed).standard_normal((m, P.n))
+    B[0] = P.b
+    return B
+
+
+@pytest.mark.parametrize("m", [1, 5, 16])
+def test_block_level_products(trio, m):
+    P, params, H, Hm, Ho = trio
+    rng = np.random.default_rng(10 + m)
+    for lev in range(params["levels"]):
+        A = Ho.A[lev]
+        X = rng.standard_normal((m, A.shape[0]))
+        ref = (A @ X.T).T
+        Y = H.level_apply_multi(lev, torch.tensor(X, device="cuda")).cpu().numpy()
+        for c in range(m):
+            assert np.linalg.norm(Y[c] - ref[c]) <= 1e-13 * np.linalg.norm(ref[c]), (lev, c)
+        if lev == params["levels"] - 1:          # the coarsest level has no FP32 values
+            with pytest.raises(RuntimeError):
+                Hm.level_apply_multi(lev, torch.tensor(X, device="cuda"), fp32=True)
+            continue
+        # FP32 values and inputs, FP32 accumulation
+        Y32 = Hm.level_apply_multi(lev, torch.tensor(X, device="cuda"), fp32=True).cpu().numpy()
+        absA = abs(A)
+        k = np.diff(A.indptr)
+        for c in range(m):
+            bound = (k + 2) * 2.0 ** -24 * (absA @ np.abs(X[c]))
+            assert np.all(np.abs(Y32[c] - ref[c]) <= bound), (lev, c)
+
+
+@pytest.mark.parametrize("m", [3, 16])
+def test_block_vcycle(trio, m):
+    P, params, H, Hm, Ho = trio
+    R = _rhs(P, m, 20 + m)
+    Z = H.vcycle_multi(torch.tensor(R, device="cuda")).cpu().numpy()
+    Z32 = Hm.vcycle_multi(torch.tensor(R, device="cuda")).cpu().numpy()
+    for c in range(m):
+        ref = O.vcycle(Ho, R[c])
+        assert np.linalg.norm(Z[c] - ref) <= 1e-12 * np.linalg.norm(ref), c
+        single32 = Hm.vcycle(torch.tensor(R[c], device="cuda")).cpu().numpy()
+        e1 = np.linalg.norm(single32 - ref)
+        e2 = np.linalg.norm(Z32[c] - ref)
+        assert e2 <= 4 * e1 + 1e-7 * np.linalg.norm(ref), (c, e1, e2)
+    # a replay gives the same bits
+    Z2 = H.vcycle_multi(torch.tensor(R, device="cuda")).cpu().numpy()
+    assert np.array_equal(Z, Z2)
+
+
+def test_block_pcg_fp64_per_column(trio):
+    P, params, H, Hm, Ho = trio
+    m, rtol = 16, 1e-10
+    B = _rhs(P, m, 31)
+    X, its, rel = H.pcg_multi(torch.tensor(B, device="cuda"), rtol=rtol)
+    X = X.cpu().numpy()
+    A = P.scipy()
+    for c in range(m):
+        ref = O.pcg(A, B[c], lambda r: O.vcycle(Ho, r), rtol=rtol)
+        assert abs(int(its[c]) - ref.iterations) <= 1, (c, its[c], ref.iterations)
+        assert np.linalg.norm(X[c] - ref.x) <= 1e-10 * np.linalg.norm(ref.x), c
+        assert np.linalg.norm(B[c] - A @ X[c]) <= rtol * np.linalg.norm(B[c]), c
+        assert rel[c] <= rtol
+
+
+def test_block_pcg_mixed_per_column(trio):
+    P, params, H, Hm, Ho = trio
+    m, rtol = 16, 1e-10
+    B = _rhs(P, m, 32)
+    X, its, rel = Hm.pcg_multi(torch.tensor(B, device="cuda"), rtol=rtol)
+    X = X.cpu().numpy()
+    A = P.scipy()
+    for c in range(m):
+        ref = O.pcg(A, B[c], lambda r: O.vcycle(Ho, r), rtol=rtol)
+        assert np.linalg.norm(B[c] - A @ X[c]) <= rtol * np.linalg.norm(B[c]), c
+        assert np.linalg.norm(X[c] - ref.x) <= 1e3 * rtol * np.linalg.norm(ref.x), c
+        assert its[c] <= ref.iterations + 3, (c, its[c], ref.iterations)
+
+
+def test_block_pcg_edge_columns(trio):
+    """A zero right-hand side, an exact initial guess and ordinary columns side by side; one
+    column (m = 1, padded block) agrees with the single-vector solve."""
+    P, params, H, Hm, Ho = trio
+    A = P.scipy()
+    m = 5
+    B = _rhs(P, m, 33)
+    B[2] = 0.0
+    X0 = np.zeros_like(B)
+    if P.n < 3000:
+        X0[3] = np.linalg.solve(A.toarray(), B[3])
+    X, its, rel = H.pcg_multi(torch.tensor(B, device="cuda"), X0=torch.tensor(X0, device="cuda"), rtol=1e-9)
+    X = X.cpu().numpy()
+    assert its[2] == 0 and np.all(X[2] == 0.0) and rel[2] == 0.0
+    if P.n < 3000:
+        assert its[3] == 0
+    for c in (0, 1, 4):
+        assert np.linalg.norm(B[c] - A @ X[c]) <= 1e-9 * np.linalg.norm(B[c])
+    x1, it1, _ = H.pcg(torch.tensor(P.b, device="cuda"), rtol=1e-10)
+    Xs, itss, _ = H.pcg_multi(torch.tensor(P.b[None, :], device="cuda"), rtol=1e-10)
+    assert abs(int(itss[0]) - it1) <= 1
+    assert torch.allclose(Xs[0], x1, rtol=0, atol=1e-9 * float(x1.abs().max()))
+
+
+def test_block_pcg_budget_and_arguments(trio):
+    P, params, H, Hm, Ho = trio
+    B = torch.tensor(_rhs(P, 4, 34), device="cuda")
+    X, its, rel = H.pcg_multi(B, rtol=1e-15, maxit=2, raise_on_noconv=False)
+    assert np.all(its == 2)
+    with pytest.raises(RuntimeError):
+        H.pcg_multi(torch.zeros((17, P.n), dtype=torch.float64, device="cuda"))
+
+
+def test_block_pcg_after_update_values(trio):
+    """New values on the same pattern after the block loop graph was captured."""
+    P, params, H, Hm, Ho = trio
+    Hu = _hier(P, params)
+    B = _rhs(P, 4, 35)
+    Hu.pcg_multi(torch.tensor(B, device="cuda"), rtol=1e-8)
+    d = np.random.default_rng(36).uniform(0.5, 2.0, P.n)
+    rows = np.repeat(np.arange(P.n), np.diff(P.rowptr))
+    vals2 = d[rows] * P.vals * d[P.colidx]
+    Hu.update_values(torch.tensor(vals2, device="cuda"))
+    A2 = P.scipy().copy()
+    A2.data = vals2.copy()
+    Ho2 = _oracle(P, params, A2)
+    X, its, rel = Hu.pcg_multi(torch.tensor(B, device="cuda"), rtol=1e-10)
+    X = X.cpu().numpy()
+    for c in range(4):
+        ref = O.pcg(A2, B[c], lambda r: O.vcycle(Ho2, r), rtol=1e-10)
+        assert abs(int(its[c]) - ref.iterations) <= 1
+        assert np.linalg.norm(B[c] - A2 @ X[c]) <= 1e-10 * np.linalg.norm(B[c])
+    Hu.close()

@@ -159,21 +159,95 @@ def test_kernel_forms_match_oracle(pair, form):
     Hf.close()
 
 
-@pytest.mark.parametrize("form", ["register", "tma", "register_persistent", "register_l2_prefetch"])
+@pytest.mark.parametrize("form", ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block"])
 def test_set_kernel_config_each_form(pair, form):
-    """Every kernel form, pinned through r3mg_set_kernel_config, gives the oracle's V-cycle and PCG."""
+    """Every kernel form, pinned through r3mg_set_kernel_config, gives a converged mixed-precision
+    PCG (the symmetric block form exists on coarse FP32 levels only)."""
     P, params, H, Ho = pair
     Hf = _hier(P, params, precision=1)
     cfg = Hf.kernel_config()
     for lev, row in enumerate(cfg[:-1]):
         for key in ("f64", "f32"):
+            if form == "symmetric_block" and (lev == 0 or key == "f64"):
+                continue
             row[key] = {"form": form, "lanes": row[key]["lanes"], "threads": 512}
     try:
         Hf.set_kernel_config(cfg[:-1])
     except Exception as e:       # a form a level cannot host (windows too large for two buffers)
         pytest.skip(str(e))
     got = Hf.kernel_config()
-    assert all(got[l]["f32"]["form"] == form for l in range(len(cfg) - 1))
+    first = 1 if form == "symmetric_block" else 0
+    assert all(got[l]["f32"]["form"] == form for l in range(first, len(cfg) - 1))
     x, it, rel = Hf.pcg(torch.tensor(P.b, device="cuda"), rtol=1e-10)
     assert np.linalg.norm(P.b - P.scipy() @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(P.b)
     Hf.close()
+
+
+def test_symmetric_block_form_vcycle_matches_full_form(pair):
+    """The symmetric block form of the coarse FP32 levels gives the same V-cycle as the full form
+    to FP32 rounding (same operator; the transposed blocks are taken from the upper ones)."""
+    P, params, H, Ho = pair
+    if params["levels"] < 3:
+        pytest.skip("no smoothed coarse level")
+    Hf = _hier(P, dict(params, kernel_form=1), precision=1)
+    Hs = _hier(P, dict(params, kernel_form=1), precision=1)
+    cfg = Hs.kernel_config()
+    for lev in range(1, len(cfg) - 1):
+        cfg[lev]["f32"] = {"form": "symmetric_block", "lanes": 16, "threads": 128}
+    Hs.set_kernel_config(cfg[:-1])
+    r = torch.tensor(np.random.default_rng(3).standard_normal(P.n), device="cuda")
+    zf = Hf.vcycle(r).cpu().numpy()
+    zs = Hs.vcycle(r).cpu().numpy()
+    assert np.linalg.norm(zs - zf) <= 1e-5 * np.linalg.norm(zf)
+    zs2 = Hs.vcycle(r).cpu().numpy()
+    assert np.array_equal(zs, zs2)     # deterministic
+    Hf.close(); Hs.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_loop_graph_matches_host_loop(pair, precision):
+    """The solve loop as one conditional-graph launch (profiling off) and the host-driven loop
+    (profiling on) run the same kernels in the same order on the same hierarchy (same tuned
+    kernel configurations): same iterations, same bits."""
+    P, params, H, Ho = pair
+    Hg = _hier(P, params, precision=precision)
+    b = torch.tensor(P.b, device="cuda")
+    xg, itg, _ = Hg.pcg(b, rtol=1e-10)
+    xg2, itg2, _ = Hg.pcg(b, rtol=1e-10)          # replay of the captured loop
+    bg, ibg, _ = Hg.pcg(b, rtol=1e-14, maxit=2, raise_on_noconv=False)
+    Hg.profile(True)
+    xh, ith, _ = Hg.pcg(b, rtol=1e-10)
+    bh, ibh, _ = Hg.pcg(b, rtol=1e-14, maxit=2, raise_on_noconv=False)
+    Hg.profile(False)
+    assert itg == ith == itg2 and itg > 0
+    assert torch.equal(xg, xh) and torch.equal(xg, xg2)
+    # a budget the loop cannot meet: stops after exactly maxit iterations, same bits again
+    assert ibg == ibh == 2
+    assert torch.equal(bg, bh)
+    Hg.close()
+
+
+def test_update_values_recaptures(pair):
+    """New values on the same pattern (A2 = D A D, D positive diagonal) after graphs were captured:
+    the V-cycle and the solve follow the oracle's hierarchy of A2, not the old coefficients."""
+    P, params, H, Ho = pair
+    Hu = _hier(P, params)
+    r = np.random.default_rng(5).standard_normal(P.n)
+    Hu.vcycle(torch.tensor(r, device="cuda"))
+    Hu.pcg(torch.tensor(P.b, device="cuda"), rtol=1e-8)
+    d = np.random.default_rng(6).uniform(0.5, 2.0, P.n)
+    rows = np.repeat(np.arange(P.n), np.diff(P.rowptr))
+    vals2 = d[rows] * P.vals * d[P.colidx]
+    Hu.update_values(torch.tensor(vals2, device="cuda"))
+    A2 = P.scipy().copy()
+    A2.data = vals2.copy()
+    Ho2 = O.build_hierarchy(P.coords, A2, Params(params["leaf_size"], params["pprime"], params["levels"],
+                                                 cheb_degree=params["cheb_degree"]))
+    z = Hu.vcycle(torch.tensor(r, device="cuda")).cpu().numpy()
+    ref = O.vcycle(Ho2, r)
+    assert np.linalg.norm(z - ref) <= 1e-12 * np.linalg.norm(ref)
+    x, it, rel = Hu.pcg(torch.tensor(P.b, device="cuda"), rtol=1e-10)
+    refs = O.pcg(A2, P.b, lambda v: O.vcycle(Ho2, v), rtol=1e-10)
+    assert abs(it - refs.iterations) <= 1
+    assert np.linalg.norm(P.b - A2 @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(P.b)
+    Hu.close()
