@@ -206,6 +206,13 @@ r3mg_status r3mg_vcycle_multi(r3mg_hierarchy* h, int m, const double* r_dev, dou
 r3mg_status r3mg_level_apply_multi(r3mg_hierarchy* h, int level, int m, int fp32, const double* x_dev, double* y_dev,
                                    void* stream);
 
+/* Block-kernel configuration of level l (fp32 = 0: FP64 blocks, 1: FP32 V-cycle blocks), tuned
+ * by timing at the first block call: slots = 2, 4 or 8 entry slots per row (window gathered
+ * through L1), 0 = coarse-level kernel with the box window staged in shared memory, -1 = not
+ * tuned yet.  The setter pins one choice (R3MG_E_ARG for an invalid or untuned combination). */
+r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots);
+r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots);
+
 /*
  * y = A_l x on level l, FP64, in level numbering (level 0: caller numbering
  * of the free DoFs; level l >= 1: coarse DoF box*b + q, boxes numbered left

@@ -84,6 +84,8 @@ def lib():
         "r3mg_pcg_multi": (ip, [vp, i32, vp, vp, dbl, i32, vp, vp, vp]),
         "r3mg_vcycle_multi": (ip, [vp, i32, vp, vp, vp]),
         "r3mg_level_apply_multi": (ip, [vp, i32, i32, i32, vp, vp, vp]),
+        "r3mg_block_config": (ip, [vp, i32, i32, P(ctypes.c_int)]),
+        "r3mg_set_block_config": (ip, [vp, i32, i32, i32]),
         "r3mg_info": (ip, [vp, P(ctypes.c_int), P(ctypes.c_int), vp, vp, vp, vp]),
         "r3mg_get_agglomerates": (ip, [vp, i32, vp]),
         "r3mg_get_level_pattern": (ip, [vp, i32, vp, vp]),

@@ -5,6 +5,7 @@
 // the single-vector kernels' arithmetic (Sections 3-4, Chebyshev-Jacobi smoothing, PCG/FCG)
 // applied column by column; only the data layout and the thread mapping differ.
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -59,6 +60,10 @@ struct MEpApply {   // Y = A X, and per-column partials of W . Y when W is given
       for (int v = 0; v < Slice<T>::V; ++v) dacc[v] += (double)ws.v[v] * (double)a.v[v];
     }
   }
+  __device__ void post1(int64_t row, int col, T a, double& dacc) const {
+    y[row * M + col] = a;
+    if (w) dacc += (double)w[row * M + col] * (double)a;
+  }
 };
 
 // One Chebyshev-Jacobi step per column (the input block is the current update D):
@@ -79,6 +84,14 @@ struct MEpCheb {
       ds.v[v] = a * ds.v[v] + c * di * rs.v[v];
     }
     xs.st(x + o); rs.st(r + o); ds.st(dnext + o);
+  }
+  __device__ void post1(int64_t row, int col, T ad, double&) const {
+    const int64_t o = row * M + col;
+    const T di = d[o];
+    x[o] += di;
+    const T rn = r[o] - ad;
+    r[o] = rn;
+    dnext[o] = a * di + c * dinv[row] * rn;
   }
 };
 
@@ -172,6 +185,113 @@ __global__ void __launch_bounds__(256) k_mr_level(LevelView<T> L, const T* __res
       }
     }
   }
+}
+
+// Coarse-level operator on M columns with the box's window staged in shared memory.  Every
+// row of a box multiplies the same window (its neighbour boxes' rows, nn*b of them), so the
+// window's M columns are copied once per box (cp.async, 16-byte pieces) and each staged slice
+// feeds R rows held by one lane.  Lanes: ceil(b/R) row groups x CL column slices; the 8 warps
+// split the window's entries in groups of four and meet in shared memory for the sum.
+template <typename T, int M, int R, class Ep>
+__global__ void __launch_bounds__(256) k_mr_coarse(LevelView<T> L, const T* __restrict__ xin, Ep ep,
+                                                   double* __restrict__ part) {
+  constexpr int V = Slice<T>::V, CL = M / V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);                       // [Wpad][M]
+  const int b = L.b;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const int cl = lane % CL, rg = lane / CL;
+  const int ngroups = (b + R - 1) / R;
+  T* red = xs;                         // [NW][b][M] partial sums, over the window once it is consumed
+  double dacc = 0.0;
+  for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
+    const int64_t e0 = L.nbr_ptr[B];
+    const int nn = (int)(L.nbr_ptr[B + 1] - e0);
+    const int W = nn * b, Wp = (W + 3) & ~3;
+    // stage the window: row w of the window is level row nbr[e0 + w / b] * b + w % b
+    constexpr int PPR = M * (int)sizeof(T) / 16;                // 16-byte pieces per row
+    for (int t = threadIdx.x; t < W * PPR; t += blockDim.x) {
+      const int w = t / PPR, pc = t % PPR;
+      const int64_t src = (L.nbr[e0 + w / b] * b + w % b) * M + pc * (16 / (int)sizeof(T));
+      const unsigned d = (unsigned)__cvta_generic_to_shared(xs + (size_t)w * M + pc * (16 / (int)sizeof(T)));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(xin + src));
+    }
+    for (int t = W * M + threadIdx.x; t < Wp * M; t += blockDim.x) xs[t] = T(0);
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t r0 = B * b;
+    const int64_t kbase = L.row_ptr[r0];                          // rows of a box: equal length Wp
+    T acc[R][V];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[i][v] = T(0);
+    if (rg < ngroups) {
+      for (int g = warp; g * 4 < Wp; g += NW) {
+        const int w0 = g * 4;
+        Slice<T> xv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T* p = xs + (size_t)(w0 + e) * M + cl * V;
+          if constexpr (sizeof(T) == 4) {
+            const float4 a = *reinterpret_cast<const float4*>(p);
+            xv[e].v[0] = a.x; xv[e].v[1] = a.y; xv[e].v[2] = a.z; xv[e].v[3] = a.w;
+          } else {
+            const double2 a = *reinterpret_cast<const double2*>(p);
+            xv[e].v[0] = a.x; xv[e].v[1] = a.y;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const int row = rg * R + i;
+          if (row < b) {
+            T a[4];
+            Vec4<T>::load(L.vals + kbase + (int64_t)row * Wp + w0, a);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+              for (int v = 0; v < V; ++v) acc[i][v] += a[e] * xv[e].v[v];
+          }
+        }
+      }
+    }
+    __syncthreads();   // window reads done: the partial-sum area may follow
+    if (rg < ngroups) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int row = rg * R + i;
+        if (row < b)
+#pragma unroll
+          for (int v = 0; v < V; ++v) red[((size_t)warp * b + row) * M + cl * V + v] = acc[i][v];
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < b * M; t += blockDim.x) {
+      T s = T(0);
+      for (int w = 0; w < NW; ++w) s += red[(size_t)w * b * M + t];
+      ep.post1(r0 + t / M, t % M, s, dacc);
+    }
+    __syncthreads();
+  }
+  if constexpr (Ep::kDot) {
+    if (part != nullptr) {
+      // thread t always finishes elements of column t % M (blockDim is a multiple of M)
+      __shared__ double redd[8][M];
+      for (int o = M; o < 32; o <<= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+      if (lane < M) redd[warp][lane] = dacc;
+      __syncthreads();
+      if (threadIdx.x < M) {
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += redd[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * M + threadIdx.x] = t;
+      }
+    }
+  }
+}
+
+template <typename T, int M>
+inline size_t mr_coarse_smem(const LevelView<T>& L) {   // staged window, later the per-warp partial sums
+  return sizeof(T) * M * std::max<size_t>((size_t)L.win_max, 8 * (size_t)L.b);
 }
 
 // ---------------------------------------------------------------- transfers

@@ -1964,13 +1964,58 @@ void mr_launch(const Level& A, const T* x, Ep ep, double* part, cudaStream_t s, 
   CK(cudaGetLastError());
 }
 
-// One level operator on M columns with S entry slots per row; returns the partial count.
+// Rows per lane of the staged coarse kernel (a power of two with ceil(b/R) * CL <= 32), 0 when
+// the level cannot use it (row groups too long, or the window does not fit in shared memory).
+template <typename T, int M>
+int mr_coarse_rows(const Level& A) {
+  if (A.b == 0) return 0;
+  constexpr int CL = M / Slice<T>::V;
+  int R = 1;
+  while ((A.b + R - 1) / R * CL > 32) R *= 2;
+  if (R > 16) return 0;
+  if (mr_coarse_smem<T, M>(view<T>(A)) > kMaxSmem) return 0;
+  return R;
+}
+
+template <typename T, int M, int R, class Ep>
+void mr_launch_coarse(const Level& A, const T* x, Ep ep, double* part, cudaStream_t s, int grid) {
+  const LevelView<T> v = view<T>(A);
+  auto kern = k_mr_coarse<T, M, R, Ep>;
+  const size_t sm = mr_coarse_smem<T, M>(v);
+  static size_t configured = 48 * 1024;
+  if (sm > configured) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = sm;
+  }
+  kern<<<grid, 256, sm, s>>>(v, x, ep, part);
+  CK(cudaGetLastError());
+}
+
+// One level operator on M columns with S entry slots per row (S = 0 on a coarse level: the
+// staged-window kernel); returns the partial count.
 template <typename T, int M, class Ep>
 int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part, int S) {
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * 8));
   const bool fine = (A.b == 0);
   cudaStream_t s = h->stream;
   constexpr int CL = M / Slice<T>::V;
+  if (!fine && S == 0) {
+    const int R = mr_coarse_rows<T, M>(A);
+    if (R > 0) {
+      const size_t sm = mr_coarse_smem<T, M>(view<T>(A));
+      const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (kMaxSmem + 1024) / (sm + 1024)));
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * per_sm));
+      switch (R) {
+        case 1: mr_launch_coarse<T, M, 1>(A, x, ep, part, s, grid); break;
+        case 2: mr_launch_coarse<T, M, 2>(A, x, ep, part, s, grid); break;
+        case 4: mr_launch_coarse<T, M, 4>(A, x, ep, part, s, grid); break;
+        case 8: mr_launch_coarse<T, M, 8>(A, x, ep, part, s, grid); break;
+        default: mr_launch_coarse<T, M, 16>(A, x, ep, part, s, grid); break;
+      }
+      return grid;
+    }
+    S = 4;
+  }
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * 8));
   if (S == 2 && CL * 2 <= 32) {
     if constexpr (CL * 2 <= 32) { if (fine) mr_launch<T, M, 2, true>(A, x, ep, part, s, grid); else mr_launch<T, M, 2, false>(A, x, ep, part, s, grid); }
   } else if (S == 8 && CL * 8 <= 32) {
@@ -2001,8 +2046,8 @@ void mr_tune(r3mg_hierarchy* h) {
     CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
     CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
     float best = 1e30f;
-    for (int S : {2, 4, 8}) {
-      if (CL * S > 32) continue;
+    for (int S : {0, 2, 4, 8}) {
+      if (CL * S > 32 || (S == 0 && mr_coarse_rows<T, M>(A) == 0)) continue;
       MEpCheb<T, M> ep{x, r, d, dn, Dinv<T>(A), T(0), T(0)};
       mr_level<T, M>(h, A, d, ep, nullptr, S);
       CK(cudaEventRecord(e0, s));
@@ -2659,6 +2704,30 @@ r3mg_status r3mg_vcycle_multi(r3mg_hierarchy* h, int m, const double* r_dev, dou
     if (M == 4) mr_dispatch_vcycle<4>(h); else if (M == 8) mr_dispatch_vcycle<8>(h); else mr_dispatch_vcycle<16>(h);
     k_mr_scatter<<<grid_for(nm), 256, 0, h->stream>>>(h->mr_z, h->perm, h->n, m, M, z_dev);
     CK(cudaGetLastError());
+  });
+}
+
+r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots) {
+  if (!h || level < 0 || level >= h->L || !slots) return R3MG_E_ARG;
+  const auto& Sv = h->mr_S[fp32 ? 1 : 0];
+  *slots = level < (int)Sv.size() ? Sv[level] : -1;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots) {
+  if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
+  if (slots != 0 && slots != 2 && slots != 4 && slots != 8) { h->err = "set_block_config: slots must be 0, 2, 4 or 8"; return R3MG_E_ARG; }
+  if (slots == 0 && h->lv[level].b == 0) { h->err = "set_block_config: the staged-window form is for coarse levels"; return R3MG_E_ARG; }
+  if (fp32 && h->prm.precision != 1) { h->err = "set_block_config: the hierarchy has no FP32 V-cycle"; return R3MG_E_ARG; }
+  if (h->mr_M == 0) { h->err = "set_block_config: no block solve has run yet (nothing tuned)"; return R3MG_E_ARG; }
+  auto& Sv = h->mr_S[fp32 ? 1 : 0];
+  if ((int)Sv.size() != h->L) { h->err = "set_block_config: this precision is not tuned yet"; return R3MG_E_ARG; }
+  const int CL = h->mr_M / (fp32 ? 4 : 2);
+  if (CL * slots > 32) { h->err = "set_block_config: too many slots for the column count"; return R3MG_E_ARG; }
+  return guarded(h, [&] {
+    CK(cudaStreamSynchronize(h->stream));
+    Sv[level] = slots;
+    drop_graphs(h);
   });
 }
 

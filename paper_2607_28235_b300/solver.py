@@ -136,6 +136,18 @@ class Hierarchy:
                                             _stream()), self._h)
         return Y
 
+    def block_config(self, fp32: bool = False) -> list:
+        """Per level: entry slots of the block kernel (0 = staged coarse window, -1 = untuned)."""
+        out = []
+        for lev in range(self.levels):
+            s = ctypes.c_int(0)
+            _check(lib().r3mg_block_config(self._h, lev, 1 if fp32 else 0, ctypes.byref(s)), self._h)
+            out.append(s.value)
+        return out
+
+    def set_block_config(self, level: int, slots: int, fp32: bool = False):
+        _check(lib().r3mg_set_block_config(self._h, int(level), 1 if fp32 else 0, int(slots)), self._h)
+
     def pcg_host(self, b: np.ndarray, x0: np.ndarray | None = None, rtol: float = 1e-8, maxit: int = 500):
         """Host buffers in and out; the copies happen inside the library call."""
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -167,3 +167,41 @@ def test_block_pcg_after_update_values(trio):
         assert abs(int(its[c]) - ref.iterations) <= 1
         assert np.linalg.norm(B[c] - A2 @ X[c]) <= 1e-10 * np.linalg.norm(B[c])
     Hu.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_block_kernel_forms_on_coarse_levels(trio, fp32):
+    """Both coarse-level block kernels (window gathered through L1 with 2/4/8 entry slots, window
+    staged in shared memory) give the oracle's products."""
+    P, params, H, Hm, Ho = trio
+    Hx = Hm if fp32 else H
+    m = 16
+    rng = np.random.default_rng(40)
+    X0 = torch.tensor(rng.standard_normal((m, P.n)), device="cuda")
+    Hx.vcycle_multi(X0)                                     # tunes the block kernels
+    for lev in range(1, params["levels"] - 1):
+        A = Ho.A[lev]
+        X = rng.standard_normal((m, A.shape[0]))
+        ref = (A @ X.T).T
+        absA = abs(A)
+        k = np.diff(A.indptr)
+        for slots in (0, 2, 4, 8):
+            if not fp32 and slots == 8:
+                continue                                    # FP64, 16 columns: 8 lanes per row slice
+            Hx.set_block_config(lev, slots, fp32=fp32)
+            assert Hx.block_config(fp32=fp32)[lev] == slots
+            Y = Hx.level_apply_multi(lev, torch.tensor(X, device="cuda"), fp32=fp32).cpu().numpy()
+            for c in range(m):
+                if fp32:
+                    bound = (k + 2) * 2.0 ** -24 * (absA @ np.abs(X[c]))
+                    assert np.all(np.abs(Y[c] - ref[c]) <= bound), (lev, slots, c)
+                else:
+                    assert np.linalg.norm(Y[c] - ref[c]) <= 1e-13 * np.linalg.norm(ref[c]), (lev, slots, c)
+        # the V-cycle with the staged form on this level still matches the oracle (FP64) or
+        # converges (FP32 inside FCG)
+        Hx.set_block_config(lev, 0, fp32=fp32)
+    B = _rhs(P, 4, 41)
+    X, its, rel = Hx.pcg_multi(torch.tensor(B, device="cuda"), rtol=1e-10)
+    Xc = X.cpu().numpy()
+    for c in range(4):
+        assert np.linalg.norm(B[c] - P.scipy() @ Xc[c]) <= 1e-10 * np.linalg.norm(B[c])
