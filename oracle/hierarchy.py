@@ -13,7 +13,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .rng import splitmix64_uniform
-from .rtree import Partition, rtree_partition
+from .rtree import Partition, cell_partition, rtree_partition
 from .transfer import prolongation_coarse, prolongation_fine
 
 
@@ -136,10 +136,16 @@ class Hierarchy:
     patterns: list = field(default_factory=list)   # block adjacency per coarse level (l >= 1)
 
 
-def build_hierarchy(coords, A: sp.csr_matrix, prm: Params) -> Hierarchy:
-    """Setup: partition, transfers, Galerkin operators, smoother constants, coarsest Cholesky."""
+def build_hierarchy(coords, A: sp.csr_matrix, prm: Params, cells=None) -> Hierarchy:
+    """Setup: partition, transfers, Galerkin operators, smoother constants, coarsest Cholesky.
+
+    cells = (cell_ptr, cell_pts) selects cell-based agglomeration (leaf_size counts cells);
+    the default is point-based agglomeration (leaf_size counts support points)."""
     A0 = sp.csr_matrix(A, dtype=np.float64)
-    part = rtree_partition(coords, prm.leaf_size, prm.levels)
+    if cells is None:
+        part = rtree_partition(coords, prm.leaf_size, prm.levels)
+    else:
+        part = cell_partition(coords, cells[0], cells[1], prm.leaf_size, prm.levels)
     d = part.dim
     As, Ps, pats = [A0], [], [None]
     P0 = prolongation_fine(coords, part, prm.pprime)

@@ -137,3 +137,35 @@ def gaussian(n: int, seed: int, count: int = 1) -> np.ndarray:
     """Seeded standard-normal vectors (n,) or (count, n), float64."""
     g = np.random.default_rng(seed).standard_normal((count, n))
     return g[0] if count == 1 else g
+
+
+def cells(dim: int, N: int, p: int) -> tuple[np.ndarray, np.ndarray]:
+    """Cell -> support-point connectivity of the structured Q_p mesh in the free-DoF numbering.
+
+    Cell c = (c_0, ..., c_{d-1}) (lexicographic, c_0 fastest) holds the (p+1)^d grid nodes
+    i_a = c_a p + k_a, k_a = 0..p; the free DoFs are the interior nodes of the (Np+1)^d grid,
+    numbered lexicographically (x fastest), and eliminated boundary nodes appear as -1.
+    Returns (cell_ptr (ncells+1,), cell_pts (ncells*(p+1)^d,)), both int64.
+    """
+    M = N * p
+    k1 = np.arange(p + 1)
+    c1 = np.arange(N)
+    node1 = c1[:, None] * p + k1[None, :]                         # (N, p+1) grid index per axis
+    free1 = np.where((node1 >= 1) & (node1 <= M - 1), node1 - 1, -1)
+    per = (p + 1) ** dim
+    if dim == 2:
+        # cells (cy, cx) with cx fastest; nodes (ky, kx) with kx fastest
+        fx = free1[None, :, None, :]                               # (1, N, 1, p+1)
+        fy = free1[:, None, :, None]                               # (N, 1, p+1, 1)
+        idx = fx + fy * (M - 1)
+        ok = (fx >= 0) & (fy >= 0)
+        pts = np.where(ok, idx, -1).reshape(N * N, per)
+    else:
+        fx = free1[None, None, :, None, None, :]
+        fy = free1[None, :, None, None, :, None]
+        fz = free1[:, None, None, :, None, None]
+        idx = fx + fy * (M - 1) + fz * (M - 1) ** 2
+        ok = (fx >= 0) & (fy >= 0) & (fz >= 0)
+        pts = np.where(ok, idx, -1).reshape(N ** 3, per)
+    ptr = np.arange(pts.shape[0] + 1, dtype=np.int64) * per
+    return ptr, pts.reshape(-1).astype(np.int64)
