@@ -110,6 +110,37 @@ r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int6
                        void* stream, r3mg_hierarchy** out);
 
 /*
+ * Host-only cell-based agglomeration (Section 4): the bisection rule of r3mg_partition applied
+ * to cells (node MBR = union of the cells' MBRs; split key = the cell's MBR centre
+ * (m_a, m_{a+1}, ..., cell index); leaf_size counts cells, >= 2), then the level-1 agglomerates,
+ * visited in order, each take every support point of their cells that no earlier one took
+ * (the paper's three-step ownership procedure).  A point's level-l box is the level-l ancestor
+ * of its level-1 owner; a box's MBR is the union of its cells' MBRs.  Needs no GPU.
+ *   cell_ptr_host (ncells+1, int64), cell_pts_host (cell_ptr[ncells], int64): the support
+ *     points of every cell in the caller's numbering; an entry < 0 is a point not in the
+ *     system (an eliminated Dirichlet node).  A cell's MBR is taken over its points in the
+ *     system; cells without any take no part.
+ *   perm_out (n): caller index of the k-th point in tree order (by owner, then caller index).
+ *   box_offsets_out (2^D + 1, may be NULL): start of each level-1 box in tree order.
+ *   box_lo_out, box_hi_out (2^D * dim each, may be NULL): level-1 box MBRs.
+ * Errors: R3MG_E_ARG (bad sizes, an index >= n, a point in no cell, no valid cell),
+ *         R3MG_E_DEPTH.
+ */
+r3mg_status r3mg_partition_cells(int64_t n, int dim, const double* coords_host, int64_t ncells,
+                                 const int64_t* cell_ptr_host, const int64_t* cell_pts_host, int leaf_size, int levels,
+                                 int64_t* perm_out, int64_t* box_offsets_out, double* box_lo_out, double* box_hi_out,
+                                 int* depth_out);
+
+/* As r3mg_setup with cell-based agglomeration (r3mg_partition_cells) in place of the point
+ * bisection; leaf_size counts cells.  Everything after the partition (P on the agglomerates'
+ * boxes, Galerkin levels, smoother, solves) is the same.  Additional error: R3MG_E_UNISOLVENT
+ * when a late agglomerate is left with fewer than (p'+1)^d points. */
+r3mg_status r3mg_setup_cells(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_host,
+                             const int32_t* colidx_host, const double* vals_host, int64_t ncells,
+                             const int64_t* cell_ptr_host, const int64_t* cell_pts_host, const r3mg_params* params,
+                             void* stream, r3mg_hierarchy** out);
+
+/*
  * Batched setup: nprob independent problems (uneven sizes allowed), each with its own R-tree
  * partition, transfers, Galerkin levels, smoother intervals and coarsest factor, stored as one
  * block-diagonal hierarchy so that every V-cycle step of all problems is one kernel launch.

@@ -1,11 +1,11 @@
 """B300-native (sm_103a) R-tree algebraic-geometric multilevel preconditioned CG.
 
 Hot path: CG preconditioned by one V-cycle of the R-tree agglomerate
-hierarchy (point-based agglomeration, box Q^{p'} prolongation, Galerkin
+hierarchy (point- or cell-based agglomeration, box Q^{p'} prolongation, Galerkin
 levels, Chebyshev-Jacobi smoothing, dense Cholesky on the coarsest level),
 all inside libr3mg (``include/r3mg.h``).  This package is the thin Python
 binding: ``Hierarchy`` (setup / vcycle / pcg / introspection),
-``partition`` (host-only R-tree) and ``R3MGSolve`` (autograd).
+``partition`` / ``partition_cells`` (host-only R-tree) and ``R3MGSolve`` (autograd).
 """
 from ._lib import R3MGError, build as _build_lib, SO_PATH
 
@@ -15,7 +15,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("Hierarchy", "BatchHierarchy", "partition", "default_params"):
+    if name in ("Hierarchy", "BatchHierarchy", "partition", "partition_cells", "default_params"):
         from . import solver
         return getattr(solver, name)
     if name in ("R3MGSolve", "solve"):
@@ -24,4 +24,4 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["build", "Hierarchy", "BatchHierarchy", "partition", "default_params", "R3MGSolve", "solve", "R3MGError", "SO_PATH"]
+__all__ = ["build", "Hierarchy", "BatchHierarchy", "partition", "partition_cells", "default_params", "R3MGSolve", "solve", "R3MGError", "SO_PATH"]

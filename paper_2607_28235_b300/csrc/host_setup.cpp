@@ -98,6 +98,138 @@ bool partition_points(int64_t n, int dim, const double* x, int leaf, int levels,
   return true;
 }
 
+// ---------------------------------------------------------------- cell-based agglomeration
+// Section 4: an R-tree whose leaves are the cells' MBRs; the agglomerates, visited in their
+// listed order, each take the support points of their cells that no earlier agglomerate took.
+// Tree: the bisection above applied to cells (node MBR = union of cell MBRs, split key = the
+// cell's MBR centre (m_a, m_{a+1}, ..., cell index), leaf_size counts cells).  Cell MBRs are
+// taken over the cell's points that belong to the system (entries < 0 are eliminated points);
+// cells with no such point take no part.  A point's level-l box is the level-l ancestor of its
+// level-1 owner; points are listed by (level-1 owner, caller index); a box's MBR is the union
+// of its cells' MBRs.
+bool partition_cells(int64_t n, int dim, const double* x, int64_t ncells, const int64_t* cell_ptr,
+                     const int64_t* cell_pts, int leaf, int levels, HostPartition& P, Error& err) {
+  if (n < 1 || (dim != 2 && dim != 3) || leaf < 2 || levels < 2 || ncells < 1) {
+    err = {R3MG_E_ARG, "partition_cells: need n >= 1, dim in {2,3}, ncells >= 1, leaf_size >= 2, levels >= 2"};
+    return false;
+  }
+  if (cell_ptr[0] != 0) { err = {R3MG_E_ARG, "partition_cells: cell_ptr[0] != 0"}; return false; }
+  for (int64_t c = 0; c < ncells; ++c)
+    if (cell_ptr[c + 1] < cell_ptr[c]) { err = {R3MG_E_ARG, "partition_cells: cell_ptr not monotone"}; return false; }
+  for (int64_t k = 0; k < cell_ptr[ncells]; ++k)
+    if (cell_pts[k] >= n) { err = {R3MG_E_ARG, "partition_cells: point index out of range"}; return false; }
+  for (int64_t i = 0; i < n * dim; ++i)
+    if (!std::isfinite(x[i])) { err = {R3MG_E_ARG, "partition_cells: non-finite coordinate"}; return false; }
+  std::vector<double> clo(ncells * dim), chi(ncells * dim), cen(ncells * dim);
+  std::vector<int64_t> cells;
+  for (int64_t c = 0; c < ncells; ++c) {
+    bool any = false;
+    for (int64_t k = cell_ptr[c]; k < cell_ptr[c + 1]; ++k) {
+      const int64_t i = cell_pts[k];
+      if (i < 0) continue;
+      for (int a = 0; a < dim; ++a) {
+        const double v = x[i * dim + a];
+        if (!any) { clo[c * dim + a] = v; chi[c * dim + a] = v; }
+        else { clo[c * dim + a] = std::min(clo[c * dim + a], v); chi[c * dim + a] = std::max(chi[c * dim + a], v); }
+      }
+      any = true;
+    }
+    if (any) {
+      cells.push_back(c);
+      for (int a = 0; a < dim; ++a) cen[c * dim + a] = 0.5 * (clo[c * dim + a] + chi[c * dim + a]);
+    }
+  }
+  const int64_t ncv = (int64_t)cells.size();
+  if (ncv < 1) { err = {R3MG_E_ARG, "partition_cells: no cell holds a point of the system"}; return false; }
+  const int D = tree_depth(ncv, leaf);
+  if (D - dim * (levels - 2) < 0) {
+    err = {R3MG_E_DEPTH, "partition_cells: tree depth " + std::to_string(D) + " too shallow for " +
+                             std::to_string(levels) + " levels"};
+    return false;
+  }
+  std::vector<int64_t> bounds{0, ncv};
+  for (int t = 0; t < D; ++t) {
+    const int64_t nn = (int64_t)bounds.size() - 1;
+    std::vector<int64_t> next(2 * nn + 1);
+    next[0] = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nn; ++k) {
+      const int64_t s = bounds[k], e = bounds[k + 1];
+      double mn[3], mx[3];
+      for (int a = 0; a < dim; ++a) { mn[a] = clo[cells[s] * dim + a]; mx[a] = chi[cells[s] * dim + a]; }
+      for (int64_t i = s; i < e; ++i)
+        for (int a = 0; a < dim; ++a) {
+          mn[a] = std::min(mn[a], clo[cells[i] * dim + a]);
+          mx[a] = std::max(mx[a], chi[cells[i] * dim + a]);
+        }
+      int ax = 0; double best = mx[0] - mn[0];
+      for (int a = 1; a < dim; ++a)
+        if (mx[a] - mn[a] > best) { best = mx[a] - mn[a]; ax = a; }
+      std::sort(cells.begin() + s, cells.begin() + e, [&](int64_t u, int64_t v) {
+        for (int k2 = 0; k2 < dim; ++k2) {
+          const int a = (ax + k2) % dim;
+          const double cu = cen[u * dim + a], cv = cen[v * dim + a];
+          if (cu < cv) return true;
+          if (cv < cu) return false;
+        }
+        return u < v;
+      });
+      const int64_t h = (e - s + 1) / 2;
+      next[2 * k + 1] = s + h;
+      next[2 * k + 2] = e;
+    }
+    bounds.swap(next);
+  }
+  // first-come ownership by the level-1 agglomerates (the nodes at depth D), in order
+  const int64_t n1 = (int64_t)bounds.size() - 1;
+  std::vector<int64_t> owner(n, -1);
+  for (int64_t K = 0; K < n1; ++K)
+    for (int64_t j = bounds[K]; j < bounds[K + 1]; ++j) {
+      const int64_t c = cells[j];
+      for (int64_t k = cell_ptr[c]; k < cell_ptr[c + 1]; ++k) {
+        const int64_t i = cell_pts[k];
+        if (i >= 0 && owner[i] < 0) owner[i] = K;
+      }
+    }
+  for (int64_t i = 0; i < n; ++i)
+    if (owner[i] < 0) { err = {R3MG_E_ARG, "partition_cells: point " + std::to_string(i) + " is in no cell"}; return false; }
+  P.n = n; P.dim = dim; P.depth = D; P.levels = levels;
+  std::vector<int64_t> cnt(n1 + 1, 0);
+  for (int64_t i = 0; i < n; ++i) ++cnt[owner[i] + 1];
+  for (int64_t K = 0; K < n1; ++K) cnt[K + 1] += cnt[K];
+  P.leaf_off = cnt;
+  P.perm.assign(n, 0);
+  {
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t i = 0; i < n; ++i) P.perm[fill[owner[i]]++] = i;   // ascending caller index within an owner
+  }
+  P.iperm.resize(n);
+  for (int64_t k = 0; k < n; ++k) P.iperm[P.perm[k]] = k;
+  P.box_off.assign(levels, {});
+  P.lo.assign(levels, {});
+  P.hi.assign(levels, {});
+  for (int l = 1; l < levels; ++l) {
+    const int shift = dim * (l - 1);
+    const int64_t nb = n1 >> shift;
+    std::vector<int64_t>& off = P.box_off[l];
+    off.resize(nb + 1);
+    for (int64_t B = 0; B <= nb; ++B) off[B] = cnt[B << shift];
+    P.lo[l].resize(nb * dim); P.hi[l].resize(nb * dim);
+    for (int64_t B = 0; B < nb; ++B) {
+      const int64_t j0 = bounds[B << shift], j1 = bounds[(B + 1) << shift];
+      for (int a = 0; a < dim; ++a) {
+        double mn = clo[cells[j0] * dim + a], mx = chi[cells[j0] * dim + a];
+        for (int64_t j = j0; j < j1; ++j) {
+          mn = std::min(mn, clo[cells[j] * dim + a]);
+          mx = std::max(mx, chi[cells[j] * dim + a]);
+        }
+        P.lo[l][B * dim + a] = mn; P.hi[l][B * dim + a] = mx;
+      }
+    }
+  }
+  return true;
+}
+
 bool validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx, Error& err) {
   if (rowptr[0] != 0) { err = {R3MG_E_ARG, "CSR: rowptr[0] != 0"}; return false; }
   for (int64_t i = 0; i < n; ++i) {

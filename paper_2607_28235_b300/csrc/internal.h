@@ -16,7 +16,7 @@ struct Error {
   std::string msg;
 };
 
-// Point-based agglomeration by R-tree bisection (Section 3; Section 4).
+// Point- or cell-based agglomeration by R-tree bisection (Section 3; Section 4).
 struct HostPartition {
   int64_t n = 0;
   int dim = 0, depth = 0, levels = 0;
@@ -49,6 +49,8 @@ struct HostFineLayout {
 
 // Host-side steps (host_setup.cpp).
 bool partition_points(int64_t n, int dim, const double* coords, int leaf, int levels, HostPartition& P, Error& err);
+bool partition_cells(int64_t n, int dim, const double* coords, int64_t ncells, const int64_t* cell_ptr,
+                     const int64_t* cell_pts, int leaf, int levels, HostPartition& P, Error& err);
 void fine_pattern(const HostPartition& P, const int64_t* rowptr, const int32_t* colidx, HostPattern& pat);
 void coarse_pattern(const HostPattern& fine, int fan, int64_t nbox_coarse, HostPattern& out);
 bool fine_layout(const HostPartition& P, const HostPattern& pat, const int64_t* rowptr, const int32_t* colidx,

@@ -944,13 +944,26 @@ struct ProbHost {
   HostFineLayout lay;
 };
 
+// Cells of a problem for cell-based agglomeration (null: point-based).
+struct CellsIn {
+  int64_t ncells;
+  const int64_t* ptr;
+  const int64_t* pts;
+};
+
 void analyse_problem(const r3mg_params& prm, int dim, int b, int fan, int64_t n, const double* coords,
-                     const int64_t* rowptr, const int32_t* colidx, const double* vals, ProbHost& out) {
+                     const int64_t* rowptr, const int32_t* colidx, const double* vals, ProbHost& out,
+                     const CellsIn* cells = nullptr) {
   Error err;
   if (!validate_csr(n, rowptr, colidx, err)) throw Fail{err.status, err.msg};
   for (int64_t k = 0; k < rowptr[n]; ++k)
     if (!std::isfinite(vals[k])) throw Fail{R3MG_E_ARG, "CSR: non-finite value"};
-  if (!partition_points(n, dim, coords, prm.leaf_size, prm.levels, out.P, err)) throw Fail{err.status, err.msg};
+  if (cells) {
+    if (!partition_cells(n, dim, coords, cells->ncells, cells->ptr, cells->pts, prm.leaf_size, prm.levels, out.P, err))
+      throw Fail{err.status, err.msg};
+  } else if (!partition_points(n, dim, coords, prm.leaf_size, prm.levels, out.P, err)) {
+    throw Fail{err.status, err.msg};
+  }
   HostPartition& P = out.P;
   const int L = prm.levels;
   // admissibility (Section 4, Remark on (m, M)): enough points and non-degenerate boxes
@@ -1194,13 +1207,14 @@ void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLay
   CK(cudaStreamSynchronize(s));
 }
 
-void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const int32_t* colidx, const double* vals) {
+void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const int32_t* colidx, const double* vals,
+           const CellsIn* cells = nullptr) {
   const r3mg_params& prm = h->prm;
   h->b = 1;
   for (int a = 0; a < h->dim; ++a) h->b *= (prm.pprime + 1);
   h->fan = 1 << h->dim;
   ProbHost ph;
-  analyse_problem(prm, h->dim, h->b, h->fan, h->n, coords, rowptr, colidx, vals, ph);
+  analyse_problem(prm, h->dim, h->b, h->fan, h->n, coords, rowptr, colidx, vals, ph, cells);
   h->part = std::move(ph.P);
   build_device(h, ph.pats, ph.lay, coords, rowptr, colidx, {{vals, rowptr[h->n]}});
 }
@@ -2458,9 +2472,56 @@ r3mg_status r3mg_partition(int64_t n, int dim, const double* coords_host, int le
   return R3MG_OK;
 }
 
+static r3mg_status setup_common(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_host,
+                                const int32_t* colidx_host, const double* vals_host, const CellsIn* cells,
+                                const r3mg_params* params, void* stream, r3mg_hierarchy** out);
+
 r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_host,
                        const int32_t* colidx_host, const double* vals_host, const r3mg_params* params, void* stream,
                        r3mg_hierarchy** out) {
+  return setup_common(n, dim, coords_host, rowptr_host, colidx_host, vals_host, nullptr, params, stream, out);
+}
+
+r3mg_status r3mg_setup_cells(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_host,
+                             const int32_t* colidx_host, const double* vals_host, int64_t ncells,
+                             const int64_t* cell_ptr_host, const int64_t* cell_pts_host, const r3mg_params* params,
+                             void* stream, r3mg_hierarchy** out) {
+  if (ncells < 1 || !cell_ptr_host || !cell_pts_host) {
+    g_last_error = "setup_cells: need ncells >= 1 and non-null cell arrays";
+    if (out) *out = nullptr;
+    return R3MG_E_ARG;
+  }
+  const CellsIn cells{ncells, cell_ptr_host, cell_pts_host};
+  return setup_common(n, dim, coords_host, rowptr_host, colidx_host, vals_host, &cells, params, stream, out);
+}
+
+r3mg_status r3mg_partition_cells(int64_t n, int dim, const double* coords_host, int64_t ncells,
+                                 const int64_t* cell_ptr_host, const int64_t* cell_pts_host, int leaf_size, int levels,
+                                 int64_t* perm_out, int64_t* box_offsets_out, double* box_lo_out, double* box_hi_out,
+                                 int* depth_out) {
+  if (!coords_host || !cell_ptr_host || !cell_pts_host || !perm_out) {
+    g_last_error = "partition_cells: null pointer";
+    return R3MG_E_ARG;
+  }
+  HostPartition P;
+  Error err;
+  try {
+    if (!partition_cells(n, dim, coords_host, ncells, cell_ptr_host, cell_pts_host, leaf_size, levels, P, err)) {
+      g_last_error = err.msg;
+      return err.status;
+    }
+  } catch (std::bad_alloc&) { g_last_error = "host allocation failed"; return R3MG_E_OOM; }
+  std::memcpy(perm_out, P.perm.data(), sizeof(int64_t) * n);
+  if (box_offsets_out) std::memcpy(box_offsets_out, P.box_off[1].data(), sizeof(int64_t) * P.box_off[1].size());
+  if (box_lo_out) std::memcpy(box_lo_out, P.lo[1].data(), sizeof(double) * P.lo[1].size());
+  if (box_hi_out) std::memcpy(box_hi_out, P.hi[1].data(), sizeof(double) * P.hi[1].size());
+  if (depth_out) *depth_out = P.depth;
+  return R3MG_OK;
+}
+
+static r3mg_status setup_common(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_host,
+                                const int32_t* colidx_host, const double* vals_host, const CellsIn* cells,
+                                const r3mg_params* params, void* stream, r3mg_hierarchy** out) {
   if (!out) { g_last_error = "setup: null output"; return R3MG_E_ARG; }
   *out = nullptr;
   if (!coords_host || !rowptr_host || !colidx_host || !vals_host || n < 1 || (dim != 2 && dim != 3)) {
@@ -2473,11 +2534,13 @@ r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int6
   const r3mg_params& p = h->prm;
   int b = 1;
   for (int a = 0; a < dim; ++a) b *= (p.pprime + 1);
-  if (p.pprime < 0 || p.pprime > 8 || b > 64 || p.leaf_size < b || p.levels < 2 || p.cheb_degree < 1 || p.sweeps < 1 ||
+  // leaf_size counts points (>= (p'+1)^d) for point-based agglomeration, cells (>= 2) for cell-based
+  const bool leaf_ok = cells ? p.leaf_size >= 2 : p.leaf_size >= b;
+  if (p.pprime < 0 || p.pprime > 8 || b > 64 || !leaf_ok || p.levels < 2 || p.cheb_degree < 1 || p.sweeps < 1 ||
       p.lanczos_steps < 1 || !(p.eig_safety > 0) || !(p.eig_ratio > 1) || (p.precision != 0 && p.precision != 1) ||
       (p.group_lanes != 0 && p.group_lanes != 4 && p.group_lanes != 8 && p.group_lanes != 16 && p.group_lanes != 32) ||
       p.kernel_form < 0 || p.kernel_form > 2) {
-    g_last_error = "setup: invalid parameters (need 0 <= p' <= 8, (p'+1)^d <= 64, leaf >= (p'+1)^d, levels >= 2, "
+    g_last_error = "setup: invalid parameters (need 0 <= p' <= 8, (p'+1)^d <= 64, leaf >= (p'+1)^d points or >= 2 cells, levels >= 2, "
                    "degree >= 1, sweeps >= 1, lanes in {0,4,8,16,32}, precision in {0,1})";
     delete h;
     return R3MG_E_ARG;
@@ -2496,7 +2559,7 @@ r3mg_status r3mg_setup(int64_t n, int dim, const double* coords_host, const int6
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
     StreamJoin j(h, stream);
-    build(h, coords_host, rowptr_host, colidx_host, vals_host);
+    build(h, coords_host, rowptr_host, colidx_host, vals_host, cells);
     CK(cudaStreamSynchronize(h->stream));
   });
   if (st != R3MG_OK) {

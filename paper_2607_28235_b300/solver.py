@@ -48,10 +48,32 @@ def partition(coords: np.ndarray, leaf_size: int, levels: int):
     return perm, off[: (1 << depth.value) + 1].copy(), depth.value
 
 
+def partition_cells(coords: np.ndarray, cell_ptr: np.ndarray, cell_pts: np.ndarray, leaf_size: int, levels: int):
+    """Host-only cell-based agglomeration: (perm, level-1 box offsets, box lo, box hi, depth)."""
+    x = np.ascontiguousarray(coords, dtype=np.float64)
+    n, d = x.shape
+    cptr = np.ascontiguousarray(cell_ptr, dtype=np.int64)
+    cpts = np.ascontiguousarray(cell_pts, dtype=np.int64)
+    nc = len(cptr) - 1
+    perm = np.empty(n, np.int64)
+    cap = 1 << (max(int(np.ceil(np.log2(max(nc, 1)))), 0) + 1)
+    off = np.empty(cap + 1, np.int64)
+    lo = np.empty(cap * d, np.float64)
+    hi = np.empty(cap * d, np.float64)
+    depth = ctypes.c_int(0)
+    rc = lib().r3mg_partition_cells(n, d, _p(x), nc, _p(cptr), _p(cpts), int(leaf_size), int(levels), _p(perm),
+                                    _p(off), _p(lo), _p(hi), ctypes.byref(depth))
+    _check(rc)
+    nb = 1 << depth.value
+    return perm, off[:nb + 1].copy(), lo[:nb * d].reshape(nb, d).copy(), hi[:nb * d].reshape(nb, d).copy(), depth.value
+
+
 class Hierarchy:
     """R-tree multilevel hierarchy on the current CUDA device."""
 
-    def __init__(self, coords, rowptr, colidx, vals, **params):
+    def __init__(self, coords, rowptr, colidx, vals, cells=None, **params):
+        """cells = (cell_ptr, cell_pts) selects cell-based agglomeration (leaf_size counts
+        cells; entries < 0 in cell_pts are points not in the system)."""
         p = _Params()
         lib().r3mg_default_params(ctypes.byref(p))
         for k, v in params.items():
@@ -67,8 +89,14 @@ class Hierarchy:
         self.nnz = int(rp[-1])
         self.b = (p.pprime + 1) ** self.dim
         h = ctypes.c_void_p()
-        rc = lib().r3mg_setup(self.n, self.dim, _p(x), _p(rp), _p(ci), _p(va), ctypes.byref(p), _stream(),
-                              ctypes.byref(h))
+        if cells is None:
+            rc = lib().r3mg_setup(self.n, self.dim, _p(x), _p(rp), _p(ci), _p(va), ctypes.byref(p), _stream(),
+                                  ctypes.byref(h))
+        else:
+            cptr = np.ascontiguousarray(cells[0], dtype=np.int64)
+            cpts = np.ascontiguousarray(cells[1], dtype=np.int64)
+            rc = lib().r3mg_setup_cells(self.n, self.dim, _p(x), _p(rp), _p(ci), _p(va), len(cptr) - 1, _p(cptr),
+                                        _p(cpts), ctypes.byref(p), _stream(), ctypes.byref(h))
         _check(rc)
         self._h = h
         info = self.info()

@@ -74,3 +74,39 @@ def test_partition_errors(lib):
     with pytest.raises(R.R3MGError) as e:
         R.partition(x, 8, 2)
     assert e.value.name == "E_ARG"
+
+
+# ---------------------------------------------------------------- cell-based agglomeration
+CELL_CASES = [(2, 4, 1, 0.0, 0, 4, 2), (2, 8, 2, 0.2, 3, 4, 3), (2, 12, 1, 0.1, 4, 6, 3), (3, 4, 2, 0.2, 5, 4, 2),
+              (3, 4, 1, 0.15, 6, 2, 3), (3, 6, 3, 0.2, 7, 8, 3)]
+
+
+@pytest.mark.parametrize("d,N,p,pert,seed,leaf,L", CELL_CASES)
+def test_partition_cells_bit_exact_vs_oracle(lib, d, N, p, pert, seed, leaf, L):
+    import workloads as W
+    from oracle.rtree import cell_partition
+    P = W.poisson(d, N, p, perturb=pert, seed=seed)
+    ptr, pts = W.cells(d, N, p)
+    perm, off, lo, hi, D = R.partition_cells(P.coords, ptr, pts, leaf, L)
+    part = cell_partition(P.coords, ptr, pts, leaf, L)
+    assert D == part.depth
+    assert np.array_equal(perm, part.perm)
+    assert np.array_equal(off, part.box_offsets[1])
+    assert np.array_equal(lo, part.mbr_lo[1]) and np.array_equal(hi, part.mbr_hi[1])
+
+
+def test_partition_cells_errors(lib):
+    import workloads as W
+    P = W.poisson(2, 4, 1)
+    ptr, pts = W.cells(2, 4, 1)
+    with pytest.raises(RuntimeError):
+        R.partition_cells(P.coords, ptr, pts, 1, 2)            # leaf < 2
+    with pytest.raises(RuntimeError):
+        R.partition_cells(P.coords, ptr, pts, 4, 4)            # too shallow
+    bad = pts.copy()
+    bad[0] = P.n                                              # index out of range
+    with pytest.raises(RuntimeError):
+        R.partition_cells(P.coords, ptr, bad, 4, 2)
+    orphan = np.where(pts == 4, -1, pts)                      # point 4 in no cell
+    with pytest.raises(RuntimeError):
+        R.partition_cells(P.coords, ptr, orphan, 4, 2)
