@@ -42,6 +42,9 @@ def _one_thread():
 
 WORKLOAD = dict(name="poisson3d_q3_32cube_perturbed", dim=3, N=32, p=3, perturb=0.2, seed=1, leaf_size=128,
                 pprime=2, levels=4, cheb_degree=3, sweeps=2, rtol=1e-8)
+# the same problem with cell-based agglomeration: R-tree over the 32^3 cells, 4 cells per
+# level-1 agglomerate (8192 agglomerates, as many as the point-based boxes)
+CELLS = dict(WORKLOAD, name="poisson3d_q3_32cube_perturbed_cells", leaf_size=4, cells=True)
 # smaller instance for ncu captures (inputs still larger than L2, a few GB on the device)
 SMALL = dict(WORKLOAD, name="poisson3d_q3_24cube_perturbed", N=24)
 # bounded CPU sample of the same workload family for the oracle timing (8x fewer DoFs)
@@ -379,13 +382,17 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = SMALL if args.workload == "small" else WORKLOAD
+    w = {"small": SMALL, "cells": CELLS}.get(args.workload, WORKLOAD)
     P = _problem(w)
+    cells = None
+    if w.get("cells"):
+        import workloads as W
+        cells = W.cells(w["dim"], w["N"], w["p"])
     t0 = time.perf_counter()
-    Hm = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, **_hparams(w, 1))
+    Hm = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, cells=cells, **_hparams(w, 1))
     setup_mixed_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    Hd = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, **_hparams(w, 0))
+    Hd = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, cells=cells, **_hparams(w, 0))
     setup_fp64_s = time.perf_counter() - t0
     if args.kernel_config:
         cfg = json.load(open(args.kernel_config))
@@ -478,6 +485,7 @@ def run_ours(args):
         "config": {"workload": w["name"], "dofs_free": P.n, "nnz": P.nnz, "leaf_size": w["leaf_size"],
                    "pprime": w["pprime"], "levels": w["levels"], "cheb_degree": w["cheb_degree"],
                    "sweeps": w["sweeps"], "rtol": w["rtol"], "precision": "FP32 V-cycle in FP64 flexible CG",
+                   "agglomeration": "cell-based (leaf_size counts cells)" if cells is not None else "point-based",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (level matrices 0.6-1.4 GB)", "level_n": info["n"].tolist(),
                    "level_nnz": info["nnz"].tolist()},
@@ -499,7 +507,7 @@ def run_ours(args):
         "clocks": clocks.summary(),
     }
     print("gpu part: " + json.dumps(line), file=sys.stderr, flush=True)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and w is WORKLOAD:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
 
@@ -513,9 +521,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--save-config", default=None, help="write the autotuned kernel configuration (JSON)")
     ap.add_argument("--kernel-config", default=None, help="replay a saved kernel configuration (JSON)")
-    ap.add_argument("--workload", default="full", choices=["full", "small", "batch256", "rhs16"],
+    ap.add_argument("--workload", default="full", choices=["full", "small", "cells", "batch256", "rhs16"],
                     help="small: the 24^3 instance used for ncu captures (not a bench line); "
                          "batch256: 256 uneven 2D problems in one batched solve; "
+                         "cells: the full problem with cell-based agglomeration; "
                          "rhs16: 16 right-hand sides on the 64^3 Q3 problem in one block solve")
     args = ap.parse_args()
     if args.warmup < 3:
