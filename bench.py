@@ -61,6 +61,18 @@ def _problem(w):
     return W.poisson(w["dim"], w["N"], w["p"], perturb=w["perturb"], seed=w["seed"])
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The slowest replica's time: the max of `value` over the ranks of the default process group
+    (identity without one).  Replicas share nothing else: the single solve does not shard."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _hparams(w, precision):
     return dict(leaf_size=w["leaf_size"], pprime=w["pprime"], levels=w["levels"], cheb_degree=w["cheb_degree"],
                 sweeps=w["sweeps"], precision=precision)
@@ -339,6 +351,55 @@ def run_multi(args):
     print(json.dumps(line), flush=True)
 
 
+SWEEP = dict(MULTI, name="poisson3d_q3_64cube_perturbed_pprime_sweep", pprimes=(0, 1, 2, 3))
+
+
+def run_sweep(args):
+    """The 64^3 Q3 problem (6.97M DoFs, 849M nonzeros), one right-hand side, p' = 0..3: single
+    solves with the FP32 V-cycle (FCG) and the FP64 V-cycle (PCG), one JSON line per p'."""
+    import numpy as np
+    import torch
+    import paper_2607_28235_b300 as R
+    w = SWEEP
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    P = _problem(w)
+    t_asm = time.perf_counter() - t0
+    b = torch.tensor(P.b, device=dev)
+    A = P.scipy()
+    for pp in w["pprimes"]:
+        out = {"metric": "PCG solve ms to 1e-8 rel-res", "unit": "ms", "n_gpus": 1, "higher_is_better": False,
+               "data": "synthetic", "config": {"workload": w["name"], "dofs_free": P.n, "nnz": P.nnz, "pprime": pp,
+                                               "leaf_size": w["leaf_size"], "levels": w["levels"]},
+               "assembly_s": t_asm}
+        for prec, key in ((1, "mixed"), (0, "fp64")):
+            try:
+                t0 = time.perf_counter()
+                H = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, **dict(_hparams(w, prec), pprime=pp))
+                setup = time.perf_counter() - t0
+                for _ in range(2):
+                    H.pcg(b, rtol=w["rtol"])
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(args.steps):
+                    x, it, rel = H.pcg(b, rtol=w["rtol"])
+                e1.record()
+                torch.cuda.synchronize()
+                chk = float(np.linalg.norm(P.b - A @ x.cpu().numpy()) / np.linalg.norm(P.b))
+                info = H.info()
+                out[key] = {"ms": e0.elapsed_time(e1) / args.steps, "iterations": it, "relres_check": chk,
+                            "setup_s": setup, "level_n": info["n"].tolist(), "level_nnz": info["nnz"].tolist()}
+                H.close()
+                del H
+            except Exception as e:          # e.g. p' = 3: unisolvence or memory
+                out[key] = {"error": str(e)[:200]}
+            torch.cuda.empty_cache()
+        if "ms" in out.get("mixed", {}):
+            out["value"] = out["mixed"]["ms"]
+        print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -439,10 +500,7 @@ def run_ours(args):
                 torch.cuda.profiler.stop()
             prof = H.profile_read()
             H.profile(False)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         return ms, its, x, rel, prof
 
     clocks = Clocks(local)
@@ -521,11 +579,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--save-config", default=None, help="write the autotuned kernel configuration (JSON)")
     ap.add_argument("--kernel-config", default=None, help="replay a saved kernel configuration (JSON)")
-    ap.add_argument("--workload", default="full", choices=["full", "small", "cells", "batch256", "rhs16"],
+    ap.add_argument("--workload", default="full", choices=["full", "small", "cells", "batch256", "rhs16",
+                                                           "pprime_sweep"],
                     help="small: the 24^3 instance used for ncu captures (not a bench line); "
                          "batch256: 256 uneven 2D problems in one batched solve; "
                          "cells: the full problem with cell-based agglomeration; "
-                         "rhs16: 16 right-hand sides on the 64^3 Q3 problem in one block solve")
+                         "rhs16: 16 right-hand sides on the 64^3 Q3 problem in one block solve; "
+                         "pprime_sweep: the 64^3 Q3 problem with p' = 0..3")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -535,6 +595,8 @@ def main():
         run_batch(args)
     elif args.workload == "rhs16":
         run_multi(args)
+    elif args.workload == "pprime_sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 
