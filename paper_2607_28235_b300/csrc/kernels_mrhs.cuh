@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels_level.cuh"
+#include "kernels_level_tma.cuh"
 #include "kernels_krylov.cuh"
 
 namespace r3mg {
@@ -292,6 +293,166 @@ __global__ void __launch_bounds__(256) k_mr_coarse(LevelView<T> L, const T* __re
 template <typename T, int M>
 inline size_t mr_coarse_smem(const LevelView<T>& L) {   // staged window, later the per-warp partial sums
   return sizeof(T) * M * std::max<size_t>((size_t)L.win_max, 8 * (size_t)L.b);
+}
+
+// Coarse-level operator on M columns, streamed: persistent CTAs walk their boxes in chunks of
+// RC rows; the copy engine brings each chunk's block rows (contiguous, RC * Wp values) into one
+// of two shared-memory buffers (cp.async.bulk, mbarrier completion) while the previous chunk is
+// computed, and the box's window of X is staged once per box (16-byte cp.async).  Every operand
+// of the inner loop then comes from shared memory.  Every mbarrier wait is bounded: on expiry
+// the kernel raises *err and all threads leave.
+struct MrStreamLayout {
+  size_t xs = 0, vals0 = 0, vals1 = 0, red = 0, bar = 0, total = 0;
+  int RC = 0;
+  __host__ __device__ MrStreamLayout() {}
+  __host__ __device__ MrStreamLayout(int win_max, int b, int M, int es, int rc) {
+    RC = rc;
+    auto up = [](size_t v) { return (v + 127) & ~(size_t)127; };
+    xs = 0;
+    vals0 = up((size_t)win_max * M * es);
+    vals1 = vals0 + up((size_t)rc * win_max * es);
+    red = vals1 + up((size_t)rc * win_max * es);
+    bar = red + up((size_t)8 * rc * M * es);
+    total = bar + 16;
+  }
+};
+
+template <typename T, int M, int R, class Ep>
+__global__ void __launch_bounds__(256) k_mr_coarse_stream(LevelView<T> L, const T* __restrict__ xin, Ep ep,
+                                                          double* __restrict__ part, MrStreamLayout lay,
+                                                          int* __restrict__ err) {
+  constexpr int V = Slice<T>::V, CL = M / V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw + lay.xs);
+  T* red = reinterpret_cast<T*>(smem_raw + lay.red);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + lay.bar);
+  const int b = L.b, RC = lay.RC;
+  const int nch = (b + RC - 1) / RC;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
+  const int cl = lane % CL, rg = lane / CL;
+  const int ngroups = (RC + R - 1) / R;
+  double dacc = 0.0;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // item k of this CTA: box blockIdx.x + (k / nch) * gridDim.x, chunk k % nch
+  const int64_t nitems = L.nbox > blockIdx.x ? ((L.nbox - 1 - blockIdx.x) / gridDim.x + 1) * nch : 0;
+  auto issue = [&](int64_t k) {   // thread 0: bulk copy of item k's block rows into buffer k & 1
+    const int64_t B = blockIdx.x + (k / nch) * (int64_t)gridDim.x;
+    const int ch = (int)(k % nch);
+    const int64_t e0 = L.nbr_ptr[B];
+    const int Wp = ((int)(L.nbr_ptr[B + 1] - e0) * b + 3) & ~3;
+    const int q0 = ch * RC, q1 = min(b, q0 + RC);
+    const uint32_t bytes = (uint32_t)((int64_t)(q1 - q0) * Wp * (int64_t)sizeof(T));
+    T* dst = reinterpret_cast<T*>(smem_raw + ((k & 1) ? lay.vals1 : lay.vals0));
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&bar[k & 1], bytes);
+    bulk_g2s(dst, L.vals + L.row_ptr[B * b + q0], bytes, &bar[k & 1]);
+  };
+  if (tid == 0 && nitems > 0) issue(0);
+  for (int64_t k = 0; k < nitems; ++k) {
+    const int64_t B = blockIdx.x + (k / nch) * (int64_t)gridDim.x;
+    const int ch = (int)(k % nch);
+    const int64_t e0 = L.nbr_ptr[B];
+    const int nn = (int)(L.nbr_ptr[B + 1] - e0);
+    const int W = nn * b, Wp = (W + 3) & ~3;
+    if (ch == 0) {
+      // the box's window of X: row w of the window is level row nbr[e0 + w / b] * b + w % b
+      constexpr int PPR = M * (int)sizeof(T) / 16;
+      for (int t = tid; t < W * PPR; t += blockDim.x) {
+        const int w = t / PPR, pc = t % PPR;
+        const int64_t src = (L.nbr[e0 + w / b] * b + w % b) * M + pc * (16 / (int)sizeof(T));
+        const unsigned d = (unsigned)__cvta_generic_to_shared(xs + (size_t)w * M + pc * (16 / (int)sizeof(T)));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(xin + src));
+      }
+      for (int t = W * M + tid; t < Wp * M; t += blockDim.x) xs[t] = T(0);
+      cp_async_wait_all();
+    }
+    // the next item's block rows go into the other buffer (its last reader finished at the
+    // barrier that ended the previous item)
+    if (tid == 0 && k + 1 < nitems) issue(k + 1);
+    const bool alive = mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), err);
+    if (__syncthreads_or(!alive)) {
+      // leave only after the copy issued for the next item has landed (bounded as well)
+      if (tid == 0 && k + 1 < nitems) mbar_wait_bounded(&bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), err);
+      return;
+    }
+    const T* vb = reinterpret_cast<const T*>(smem_raw + ((k & 1) ? lay.vals1 : lay.vals0));
+    const int q0 = ch * RC, nr = min(b, q0 + RC) - q0;
+    T acc[R][V];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[i][v] = T(0);
+    if (rg < ngroups) {
+      for (int g = warp; g * 4 < Wp; g += NW) {
+        const int w0 = g * 4;
+        Slice<T> xv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const T* p = xs + (size_t)(w0 + e) * M + cl * V;
+          if constexpr (sizeof(T) == 4) {
+            const float4 a = *reinterpret_cast<const float4*>(p);
+            xv[e].v[0] = a.x; xv[e].v[1] = a.y; xv[e].v[2] = a.z; xv[e].v[3] = a.w;
+          } else {
+            const double2 a = *reinterpret_cast<const double2*>(p);
+            xv[e].v[0] = a.x; xv[e].v[1] = a.y;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const int row = rg * R + i;
+          if (row < nr) {
+            T a[4];
+            if constexpr (sizeof(T) == 4) {
+              const float4 t4 = *reinterpret_cast<const float4*>(vb + (size_t)row * Wp + w0);
+              a[0] = t4.x; a[1] = t4.y; a[2] = t4.z; a[3] = t4.w;
+            } else {
+              const double2 t0 = *reinterpret_cast<const double2*>(vb + (size_t)row * Wp + w0);
+              const double2 t1 = *reinterpret_cast<const double2*>(vb + (size_t)row * Wp + w0 + 2);
+              a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+              for (int v = 0; v < V; ++v) acc[i][v] += a[e] * xv[e].v[v];
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int row = rg * R + i;
+        if (row < nr)
+#pragma unroll
+          for (int v = 0; v < V; ++v) red[((size_t)warp * RC + row) * M + cl * V + v] = acc[i][v];
+      }
+    }
+    __syncthreads();
+    const int64_t r0 = B * b + q0;
+    for (int t = tid; t < nr * M; t += blockDim.x) {
+      const int row = t / M, col = t % M;
+      T s = T(0);
+      for (int w = 0; w < NW; ++w) s += red[((size_t)w * RC + row) * M + col];
+      ep.post1(r0 + row, col, s, dacc);
+    }
+    __syncthreads();   // red, xs (at a box change) and this item's buffer are free again
+  }
+  if constexpr (Ep::kDot) {
+    if (part != nullptr) {
+      __shared__ double redd[8][M];
+      for (int o = M; o < 32; o <<= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+      if (lane < M) redd[warp][lane] = dacc;
+      __syncthreads();
+      if (tid < M) {
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += redd[w][tid];
+        part[(int64_t)blockIdx.x * M + tid] = t;
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------- transfers

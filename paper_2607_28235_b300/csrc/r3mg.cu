@@ -2005,13 +2005,63 @@ void mr_launch_coarse(const Level& A, const T* x, Ep ep, double* part, cudaStrea
   CK(cudaGetLastError());
 }
 
-// One level operator on M columns with S entry slots per row (S = 0 on a coarse level: the
-// staged-window kernel); returns the partial count.
+// Streamed coarse block kernel: rows per chunk so that the window, two chunk buffers and the
+// partial sums fit the shared memory (0: does not fit), and rows per lane.
+template <typename T, int M>
+MrStreamLayout mr_stream_layout(const Level& A) {
+  for (int rc = A.b; rc >= 1; --rc) {
+    MrStreamLayout lay(A.win_max, A.b, M, (int)sizeof(T), rc);
+    if (lay.total <= kMaxSmem) return lay;
+  }
+  return MrStreamLayout();
+}
+
+template <typename T, int M>
+int mr_stream_rows(int RC) {
+  constexpr int CL = M / Slice<T>::V;
+  int R = 1;
+  while ((RC + R - 1) / R * CL > 32) R *= 2;
+  return R;
+}
+
+template <typename T, int M, int R, class Ep>
+void mr_launch_stream(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part, const MrStreamLayout& lay,
+                      int grid) {
+  const LevelView<T> v = view<T>(A);
+  auto kern = k_mr_coarse_stream<T, M, R, Ep>;
+  static size_t configured = 48 * 1024;
+  if (lay.total > configured) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
+    configured = lay.total;
+  }
+  kern<<<grid, 256, lay.total, h->stream>>>(v, x, ep, part, lay, h->tma_err);
+  CK(cudaGetLastError());
+}
+
+// One level operator on M columns with S entry slots per row (on a coarse level S = 0: the
+// staged-window kernel, S = 1: the streamed kernel); returns the partial count.
 template <typename T, int M, class Ep>
 int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part, int S) {
   const bool fine = (A.b == 0);
   cudaStream_t s = h->stream;
   constexpr int CL = M / Slice<T>::V;
+  if (!fine && S == 1) {
+    const MrStreamLayout lay = mr_stream_layout<T, M>(A);
+    const int R = lay.RC > 0 ? mr_stream_rows<T, M>(lay.RC) : 0;
+    if (R > 0 && R <= 16) {
+      const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (kMaxSmem + 1024) / (lay.total + 1024)));
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * per_sm));
+      switch (R) {
+        case 1: mr_launch_stream<T, M, 1>(h, A, x, ep, part, lay, grid); break;
+        case 2: mr_launch_stream<T, M, 2>(h, A, x, ep, part, lay, grid); break;
+        case 4: mr_launch_stream<T, M, 4>(h, A, x, ep, part, lay, grid); break;
+        case 8: mr_launch_stream<T, M, 8>(h, A, x, ep, part, lay, grid); break;
+        default: mr_launch_stream<T, M, 16>(h, A, x, ep, part, lay, grid); break;
+      }
+      return grid;
+    }
+    S = 0;
+  }
   if (!fine && S == 0) {
     const int R = mr_coarse_rows<T, M>(A);
     if (R > 0) {
@@ -2060,8 +2110,9 @@ void mr_tune(r3mg_hierarchy* h) {
     CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
     CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
     float best = 1e30f;
-    for (int S : {0, 2, 4, 8}) {
+    for (int S : {1, 0, 2, 4, 8}) {
       if (CL * S > 32 || (S == 0 && mr_coarse_rows<T, M>(A) == 0)) continue;
+      if (S == 1 && (A.b == 0 || mr_stream_layout<T, M>(A).RC == 0)) continue;
       MEpCheb<T, M> ep{x, r, d, dn, Dinv<T>(A), T(0), T(0)};
       mr_level<T, M>(h, A, d, ep, nullptr, S);
       CK(cudaEventRecord(e0, s));
@@ -2748,6 +2799,12 @@ r3mg_status r3mg_pcg_multi(r3mg_hierarchy* h, int m, const double* b_dev, double
     h->launches += 3;
     CK(cudaStreamSynchronize(h->stream));
     prof_harvest(h);
+    int terr = 0;
+    CK(cudaMemcpy(&terr, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (terr) {
+      CK(cudaMemset(h->tma_err, 0, sizeof(int)));
+      throw Fail{R3MG_E_TIMEOUT, "a bounded wait of the streamed block kernel expired"};
+    }
   });
   if (st != R3MG_OK) return st;
   if (res == R3MG_E_NOCONV) h->err = "pcg_multi: maximum iterations reached in some column";
@@ -2779,8 +2836,11 @@ r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots
 
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots) {
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
-  if (slots != 0 && slots != 2 && slots != 4 && slots != 8) { h->err = "set_block_config: slots must be 0, 2, 4 or 8"; return R3MG_E_ARG; }
-  if (slots == 0 && h->lv[level].b == 0) { h->err = "set_block_config: the staged-window form is for coarse levels"; return R3MG_E_ARG; }
+  if (slots < 0 || slots > 8 || (slots > 2 && slots != 4 && slots != 8)) {
+    h->err = "set_block_config: slots must be 0, 1, 2, 4 or 8";
+    return R3MG_E_ARG;
+  }
+  if (slots <= 1 && h->lv[level].b == 0) { h->err = "set_block_config: the staged and streamed forms are for coarse levels"; return R3MG_E_ARG; }
   if (fp32 && h->prm.precision != 1) { h->err = "set_block_config: the hierarchy has no FP32 V-cycle"; return R3MG_E_ARG; }
   if (h->mr_M == 0) { h->err = "set_block_config: no block solve has run yet (nothing tuned)"; return R3MG_E_ARG; }
   auto& Sv = h->mr_S[fp32 ? 1 : 0];
