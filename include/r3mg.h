@@ -241,8 +241,9 @@ r3mg_status r3mg_level_apply_multi(r3mg_hierarchy* h, int level, int m, int fp32
  * by timing at the first block call: slots = 2, 4 or 8 entry slots per row (window gathered
  * through L1), 0 = coarse-level kernel with the box window staged in shared memory, 1 = coarse-
  * level kernel with the window staged and the block rows streamed into shared memory by the
- * copy engine (cp.async.bulk, bounded mbarrier waits: R3MG_E_TIMEOUT if one expires), -1 = not
- * tuned yet.  The setter pins one choice (R3MG_E_ARG for an invalid or untuned combination). */
+ * copy engine (cp.async.bulk, bounded mbarrier waits: R3MG_E_TIMEOUT if one expires), 3 =
+ * coarse-level FP32 kernel on the tensor cores (8 or 16 columns; TF32 head/tail splitting keeps
+ * FP32 accuracy), -1 = not tuned yet.  The setter pins one choice (R3MG_E_ARG for an invalid or untuned combination). */
 r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots);
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots);
 

@@ -455,6 +455,96 @@ __global__ void __launch_bounds__(256) k_mr_coarse_stream(LevelView<T> L, const 
   }
 }
 
+// Coarse-level FP32 operator on M = 8 or 16 columns on the tensor cores.  A box's rows times its
+// window is a dense product D (b x M) = A_B (b x Wp) X_win (Wp x M); it is cut into 16 x 8 tiles
+// of mma.sync m16n8k8 (TF32 inputs, FP32 accumulation), one tile per warp over the whole
+// window.  FP32 accuracy is kept by splitting each operand into a TF32 head and a TF32 tail
+// (x = hi + lo, lo = tf32(x - hi)) and accumulating hi*hi + hi*lo + lo*hi: the dropped lo*lo
+// term and the splits cost at most a few units of 2^-22 relative per product.  The block rows
+// are read straight from global memory (each lane quad reads 32 contiguous bytes of a row per
+// step), the window rows of X through the read-only path by the shared-memory window map.
+// Products only (no dot partials): the Chebyshev step or a plain product.
+__device__ __forceinline__ uint32_t tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int M, class Ep>
+__global__ void __launch_bounds__(128) k_mr_coarse_mma(LevelView<float> L, const float* __restrict__ xin, Ep ep) {
+  static_assert(M % 8 == 0, "n tiles of 8 columns");
+  constexpr int NT = M / 8;
+  extern __shared__ __align__(16) int32_t smap[];
+  const int b = L.b;
+  const int MT = (b + 15) / 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  double unused = 0.0;
+  for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
+    const int64_t e0 = L.nbr_ptr[B];
+    const int nn = (int)(L.nbr_ptr[B + 1] - e0);
+    const int W = nn * b, Wp = (W + 3) & ~3, W8 = (W + 7) & ~7;
+    for (int t = threadIdx.x; t < W; t += blockDim.x) smap[t] = (int32_t)(L.nbr[e0 + t / b] * b + t % b);
+    for (int t = W + threadIdx.x; t < W8; t += blockDim.x) smap[t] = 0;   // zero A entries meet row 0
+    __syncthreads();
+    const int64_t kbase = L.row_ptr[B * b];                                // box rows: equal length Wp
+    for (int tile = warp; tile < MT * NT; tile += NW) {
+      const int mt = tile / NT, nt = tile % NT;
+      const int ra = mt * 16 + gid, rb = ra + 8;
+      const bool va = ra < b, vb = rb < b;
+      const float* Aa = L.vals + kbase + (int64_t)(va ? ra : 0) * Wp;
+      const float* Ab = L.vals + kbase + (int64_t)(vb ? rb : 0) * Wp;
+      const int n = nt * 8 + gid;
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      // U steps of 8 window positions are loaded before any is consumed (loads in flight)
+      constexpr int U = 4;
+      for (int k0 = 0; k0 < W8; k0 += 8 * U) {
+        float x[U][4], y[U][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int ka = k0 + 8 * u + tig, kb = ka + 4;
+          const bool in = ka < W8;                     // kb < W8 as well (W8 is a multiple of 8)
+          x[u][0] = (in && va && ka < Wp) ? __ldg(Aa + ka) : 0.f;
+          x[u][1] = (in && vb && ka < Wp) ? __ldg(Ab + ka) : 0.f;
+          x[u][2] = (in && va && kb < Wp) ? __ldg(Aa + kb) : 0.f;
+          x[u][3] = (in && vb && kb < Wp) ? __ldg(Ab + kb) : 0.f;
+          y[u][0] = in ? __ldg(xin + (int64_t)smap[ka] * M + n) : 0.f;
+          y[u][1] = in ? __ldg(xin + (int64_t)smap[kb] * M + n) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            ah[j] = tf32_hi(x[u][j]);
+            al[j] = tf32_hi(x[u][j] - __uint_as_float(ah[j]));
+          }
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            bh[j] = tf32_hi(y[u][j]);
+            bl[j] = tf32_hi(y[u][j] - __uint_as_float(bh[j]));
+          }
+          mma_tf32(c, al, bh);
+          mma_tf32(c, ah, bl);
+          mma_tf32(c, ah, bh);
+        }
+      }
+      const int col = nt * 8 + 2 * tig;
+      if (va) { ep.post1(B * b + ra, col, c[0], unused); ep.post1(B * b + ra, col + 1, c[1], unused); }
+      if (vb) { ep.post1(B * b + rb, col, c[2], unused); ep.post1(B * b + rb, col + 1, c[3], unused); }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- transfers
 // Next-level initialisation after restriction, per column: R = B, X = 0, D = c0 dinv B.
 template <typename T, int M>

@@ -2038,13 +2038,42 @@ void mr_launch_stream(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, doub
   CK(cudaGetLastError());
 }
 
+// Tensor-core coarse block kernel: FP32, M = 8 or 16, products without dot partials.
+template <typename T, int M, class Ep>
+constexpr bool mr_mma_ok() { return sizeof(T) == 4 && (M == 8 || M == 16); }
+
+template <typename T, int M, class Ep>
+void mr_launch_mma(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep) {
+  if constexpr (mr_mma_ok<T, M, Ep>()) {
+    const LevelView<float> v = view<float>(A);
+    auto kern = k_mr_coarse_mma<M, Ep>;
+    const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 15) & ~(size_t)7);
+    static size_t configured = 48 * 1024;
+    if (sm > configured) {
+      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      configured = sm;
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * 16));
+    kern<<<grid, 128, sm, h->stream>>>(v, x, ep);
+    CK(cudaGetLastError());
+  }
+}
+
 // One level operator on M columns with S entry slots per row (on a coarse level S = 0: the
-// staged-window kernel, S = 1: the streamed kernel); returns the partial count.
+// staged-window kernel, S = 1: the streamed kernel, S = 3: the tensor-core kernel); returns the
+// partial count.
 template <typename T, int M, class Ep>
 int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part, int S) {
   const bool fine = (A.b == 0);
   cudaStream_t s = h->stream;
   constexpr int CL = M / Slice<T>::V;
+  if (!fine && S == 3) {
+    if (mr_mma_ok<T, M, Ep>() && part == nullptr) {
+      mr_launch_mma<T, M, Ep>(h, A, x, ep);
+      return 1;
+    }
+    S = 2;
+  }
   if (!fine && S == 1) {
     const MrStreamLayout lay = mr_stream_layout<T, M>(A);
     const int R = lay.RC > 0 ? mr_stream_rows<T, M>(lay.RC) : 0;
@@ -2110,8 +2139,13 @@ void mr_tune(r3mg_hierarchy* h) {
     CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
     CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
     float best = 1e30f;
-    for (int S : {1, 0, 2, 4, 8}) {
-      if (CL * S > 32 || (S == 0 && mr_coarse_rows<T, M>(A) == 0)) continue;
+    for (int S : {3, 1, 0, 2, 4, 8}) {
+      if (S == 3) {
+        if (A.b == 0 || !mr_mma_ok<T, M, MEpCheb<T, M>>()) continue;
+      } else if (CL * S > 32) {
+        continue;
+      }
+      if (S == 0 && mr_coarse_rows<T, M>(A) == 0) continue;
       if (S == 1 && (A.b == 0 || mr_stream_layout<T, M>(A).RC == 0)) continue;
       MEpCheb<T, M> ep{x, r, d, dn, Dinv<T>(A), T(0), T(0)};
       mr_level<T, M>(h, A, d, ep, nullptr, S);
@@ -2836,17 +2870,24 @@ r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots
 
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots) {
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
-  if (slots < 0 || slots > 8 || (slots > 2 && slots != 4 && slots != 8)) {
-    h->err = "set_block_config: slots must be 0, 1, 2, 4 or 8";
+  if (slots < 0 || slots > 8 || (slots > 4 && slots != 8)) {
+    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4 or 8";
     return R3MG_E_ARG;
   }
-  if (slots <= 1 && h->lv[level].b == 0) { h->err = "set_block_config: the staged and streamed forms are for coarse levels"; return R3MG_E_ARG; }
+  if ((slots <= 1 || slots == 3) && h->lv[level].b == 0) {
+    h->err = "set_block_config: the staged, streamed and tensor-core forms are for coarse levels";
+    return R3MG_E_ARG;
+  }
+  if (slots == 3 && (!fp32 || (h->mr_M != 8 && h->mr_M != 16))) {
+    h->err = "set_block_config: the tensor-core form is FP32 with 8 or 16 columns";
+    return R3MG_E_ARG;
+  }
   if (fp32 && h->prm.precision != 1) { h->err = "set_block_config: the hierarchy has no FP32 V-cycle"; return R3MG_E_ARG; }
   if (h->mr_M == 0) { h->err = "set_block_config: no block solve has run yet (nothing tuned)"; return R3MG_E_ARG; }
   auto& Sv = h->mr_S[fp32 ? 1 : 0];
   if ((int)Sv.size() != h->L) { h->err = "set_block_config: this precision is not tuned yet"; return R3MG_E_ARG; }
   const int CL = h->mr_M / (fp32 ? 4 : 2);
-  if (CL * slots > 32) { h->err = "set_block_config: too many slots for the column count"; return R3MG_E_ARG; }
+  if (slots != 3 && CL * slots > 32) { h->err = "set_block_config: too many slots for the column count"; return R3MG_E_ARG; }
   return guarded(h, [&] {
     CK(cudaStreamSynchronize(h->stream));
     Sv[level] = slots;
