@@ -545,6 +545,93 @@ __global__ void __launch_bounds__(128) k_mr_coarse_mma(LevelView<float> L, const
   }
 }
 
+// Fine-level block operator on global column indices: the level rows taken in one flat sweep
+// (no per-box window map, no barriers), each stored entry carrying the level row of its column
+// (built once from the windowed layout by k_mr_build_gidx).  Lane layout as in k_mr_level.
+template <typename T, int M, int S, class Ep>
+__global__ void __launch_bounds__(256) k_mr_rows(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ gidx,
+                                                 const T* __restrict__ vals, int64_t nrows, const T* __restrict__ xin,
+                                                 Ep ep, double* __restrict__ part) {
+  constexpr int V = Slice<T>::V, CL = M / V, LPR = CL * S, RPW = 32 / LPR;
+  static_assert(M % V == 0 && 32 % LPR == 0, "lane layout");
+  __shared__ double red[8][M];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const int cl = lane % CL, s = (lane / CL) % S, rw = lane / LPR;
+  double dacc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) dacc[v] = 0.0;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gw * RPW; base < nrows; base += nwt * RPW) {   // warp-uniform trip count
+    const int64_t row = base + rw;
+    const bool ok = row < nrows;
+    int64_t k0 = 0, k1 = 0;
+    if (ok) { k0 = row_ptr[row]; k1 = row_ptr[row + 1]; }
+    Slice<T> acc;
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc.v[v] = T(0);
+    for (int64_t k = k0 + 4 * s; k < k1; k += 4 * S) {
+      T a[4];
+      Vec4<T>::load(vals + k, a);
+      const int4 g = __ldcs(reinterpret_cast<const int4*>(gidx + k));
+      Slice<T> xv[4];
+      xv[0].ldg(xin + (int64_t)g.x * M + cl * V);
+      xv[1].ldg(xin + (int64_t)g.y * M + cl * V);
+      xv[2].ldg(xin + (int64_t)g.z * M + cl * V);
+      xv[3].ldg(xin + (int64_t)g.w * M + cl * V);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc.v[v] += a[e] * xv[e].v[v];
+    }
+#pragma unroll
+    for (int o = CL; o < LPR; o <<= 1)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc.v[v] += __shfl_xor_sync(0xffffffffu, acc.v[v], o);
+    if (ok && s == 0) ep.post(row, cl * V, acc, dacc);
+  }
+  if constexpr (Ep::kDot) {
+    if (part != nullptr) {
+#pragma unroll
+      for (int o = CL; o < 32; o <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; ++v) dacc[v] += __shfl_xor_sync(0xffffffffu, dacc[v], o);
+      if (lane < CL)
+#pragma unroll
+        for (int v = 0; v < V; ++v) red[warp][lane * V + v] = dacc[v];
+      __syncthreads();
+      if (threadIdx.x < M) {
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * M + threadIdx.x] = t;
+      }
+    }
+  }
+}
+
+// Global column of every stored fine-level entry: the window map of its box applied to its
+// 16-bit window index (padding entries keep window position 0, a valid row with value 0).
+template <typename T>
+__global__ void __launch_bounds__(256) k_mr_build_gidx(LevelView<T> L, int32_t* __restrict__ gidx) {
+  extern __shared__ __align__(16) int32_t smap[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
+    const int64_t e0 = L.nbr_ptr[B];
+    const int nn = (int)(L.nbr_ptr[B + 1] - e0);
+    const int W = L.win_size[B];
+    for (int q = warp; q < nn; q += NW) {
+      const int wo = L.win_off[e0 + q];
+      const int64_t src = L.slot_src[e0 + q];
+      const int len = (q + 1 < nn ? L.win_off[e0 + q + 1] : W) - wo;
+      for (int t = lane; t < len; t += 32) smap[wo + t] = (int32_t)(src + t);
+    }
+    __syncthreads();
+    const int64_t k0 = L.row_ptr[L.box_row[B]], k1 = L.row_ptr[L.box_row[B + 1]];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) gidx[k] = smap[L.idx[k]];
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- transfers
 // Next-level initialisation after restriction, per column: R = B, X = 0, D = c0 dinv B.
 template <typename T, int M>

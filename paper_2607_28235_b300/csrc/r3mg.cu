@@ -162,6 +162,7 @@ struct r3mg_hierarchy {
   int mgraph_state = 0;
   int prof_cols = 1;                  // columns of the last profiled solve (bytes per launch)
   int64_t mr_graph_kernels = 0;       // kernels in one block V-cycle
+  int32_t* mr_gidx = nullptr;         // fine level: global column (tree row) of every stored entry
   int nsm = 148;
   int tma_ctas = 1;                   // TMA kernel CTAs per SM
   int64_t graph_kernels = 0;          // kernels in one replay of the V-cycle graph
@@ -1937,6 +1938,8 @@ void mr_alloc(r3mg_hierarchy* h, int M) {
   if (h->mgraph) { cudaGraphExecDestroy(h->mgraph); h->mgraph = nullptr; }
   h->mgraph_state = 0;
   h->mr_M = 0;
+  h->mr_S[0].clear();   // kernel choices were tuned for the old column count
+  h->mr_S[1].clear();
   const size_t es = (h->prm.precision == 1) ? 4 : 8;
   const int L = h->L;
   h->mr_x.assign(L, nullptr); h->mr_r.assign(L, nullptr); h->mr_d0.assign(L, nullptr); h->mr_d1.assign(L, nullptr);
@@ -1962,6 +1965,22 @@ void mr_alloc(r3mg_hierarchy* h, int M) {
   h->mr_active = dalloc<int>(h, M);
   if (!h->mr_host) CK(cudaMallocHost(&h->mr_host, sizeof(double) * 64));
   h->mr_M = M;
+}
+
+// Global column indices of the fine level for the flat block sweep (built once, kept).
+void mr_build_gidx(r3mg_hierarchy* h) {
+  if (h->mr_gidx) return;
+  Level& F = h->lv[0];
+  h->mr_gidx = dalloc<int32_t>(h, F.stored);
+  const LevelView<double> v = view<double>(F);
+  const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 7) & ~(size_t)3);
+  static size_t configured = 48 * 1024;
+  if (sm > configured) {
+    CK(cudaFuncSetAttribute(k_mr_build_gidx<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = sm;
+  }
+  k_mr_build_gidx<double><<<(int)std::min<int64_t>(F.nbox, (int64_t)h->nsm * 8), 256, sm, h->stream>>>(v, h->mr_gidx);
+  CK(cudaGetLastError());
 }
 
 template <typename T, int M, int S, bool FINE, class Ep>
@@ -2074,6 +2093,21 @@ int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part,
     }
     S = 2;
   }
+  if (fine && S > 8) {   // 10 + slots: the flat row sweep on global column indices
+    mr_build_gidx(h);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + 7) / 8, (int64_t)h->nsm * 8));
+    const LevelView<T> v = view<T>(A);
+    const int Sr = S - 10;
+    if (Sr == 2 && CL * 2 <= 32) {
+      if constexpr (CL * 2 <= 32) k_mr_rows<T, M, 2, Ep><<<grid, 256, 0, s>>>(v.row_ptr, h->mr_gidx, v.vals, A.n, x, ep, part);
+    } else if (Sr == 8 && CL * 8 <= 32) {
+      if constexpr (CL * 8 <= 32) k_mr_rows<T, M, 8, Ep><<<grid, 256, 0, s>>>(v.row_ptr, h->mr_gidx, v.vals, A.n, x, ep, part);
+    } else {
+      if constexpr (CL * 4 <= 32) k_mr_rows<T, M, 4, Ep><<<grid, 256, 0, s>>>(v.row_ptr, h->mr_gidx, v.vals, A.n, x, ep, part);
+    }
+    CK(cudaGetLastError());
+    return grid;
+  }
   if (!fine && S == 1) {
     const MrStreamLayout lay = mr_stream_layout<T, M>(A);
     const int R = lay.RC > 0 ? mr_stream_rows<T, M>(lay.RC) : 0;
@@ -2139,9 +2173,11 @@ void mr_tune(r3mg_hierarchy* h) {
     CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
     CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
     float best = 1e30f;
-    for (int S : {3, 1, 0, 2, 4, 8}) {
+    for (int S : {3, 1, 0, 2, 4, 8, 12, 14, 18}) {
       if (S == 3) {
         if (A.b == 0 || !mr_mma_ok<T, M, MEpCheb<T, M>>()) continue;
+      } else if (S > 8) {
+        if (A.b != 0 || CL * (S - 10) > 32) continue;
       } else if (CL * S > 32) {
         continue;
       }
@@ -2176,8 +2212,8 @@ int mr_S64(r3mg_hierarchy* h) {
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       float best = 1e30f;
-      for (int S : {2, 4, 8}) {
-        if (CL * S > 32) continue;
+      for (int S : {2, 4, 8, 12, 14, 18}) {
+        if (CL * (S > 8 ? S - 10 : S) > 32) continue;
         mr_level<double, M>(h, h->lv[0], h->mr_p, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S);
         CK(cudaEventRecord(e0, s));
         for (int k = 0; k < 3; ++k) mr_level<double, M>(h, h->lv[0], h->mr_p, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S);
@@ -2520,7 +2556,9 @@ void mr_apply_level(r3mg_hierarchy* h, int level, const double* x_blk, double* y
   Level& A = h->lv[level];
   const int pi = sizeof(T) == 4 ? 1 : 0;
   if (pi == 1) mr_tune<float, M>(h); else mr_S64<M>(h);
-  const int S = pi == 1 ? h->mr_S[1][std::min(level, h->L - 2)] : (level == 0 ? h->mr_S[0][0] : 4);
+  // the configured choice of this level (FP64 blocks of a mixed hierarchy are tuned on level 0 only)
+  const int lv = std::min(level, h->L - 2);
+  const int S = pi == 1 ? h->mr_S[1][lv] : (h->prm.precision == 0 || level == 0 ? h->mr_S[0][lv] : 4);
   const int64_t nm = A.n * M;
   // scratch of level 0's size in the right precision (level 0 is the largest level)
   T* xt = pi == 1 ? (T*)h->mr_d0[0] : (T*)h->mr_p;
@@ -2870,10 +2908,12 @@ r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots
 
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots) {
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
-  if (slots < 0 || slots > 8 || (slots > 4 && slots != 8)) {
-    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4 or 8";
+  if (!(slots == 0 || slots == 1 || slots == 2 || slots == 3 || slots == 4 || slots == 8 || slots == 12 ||
+        slots == 14 || slots == 18)) {
+    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4, 8, 12, 14 or 18";
     return R3MG_E_ARG;
   }
+  if (slots > 8 && h->lv[level].b != 0) { h->err = "set_block_config: the flat row sweep is for the fine level"; return R3MG_E_ARG; }
   if ((slots <= 1 || slots == 3) && h->lv[level].b == 0) {
     h->err = "set_block_config: the staged, streamed and tensor-core forms are for coarse levels";
     return R3MG_E_ARG;
@@ -2887,7 +2927,10 @@ r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int sl
   auto& Sv = h->mr_S[fp32 ? 1 : 0];
   if ((int)Sv.size() != h->L) { h->err = "set_block_config: this precision is not tuned yet"; return R3MG_E_ARG; }
   const int CL = h->mr_M / (fp32 ? 4 : 2);
-  if (slots != 3 && CL * slots > 32) { h->err = "set_block_config: too many slots for the column count"; return R3MG_E_ARG; }
+  if (slots != 3 && CL * (slots > 8 ? slots - 10 : slots) > 32) {
+    h->err = "set_block_config: too many slots for the column count";
+    return R3MG_E_ARG;
+  }
   return guarded(h, [&] {
     CK(cudaStreamSynchronize(h->stream));
     Sv[level] = slots;

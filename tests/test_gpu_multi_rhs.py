@@ -213,3 +213,36 @@ def test_block_kernel_forms_on_coarse_levels(trio, fp32):
     Xc = X.cpu().numpy()
     for c in range(4):
         assert np.linalg.norm(B[c] - P.scipy() @ Xc[c]) <= 1e-10 * np.linalg.norm(B[c])
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_block_kernel_forms_on_the_fine_level(trio, fp32):
+    """Fine-level block kernels: window map in shared memory (2/4/8 entry slots) and the flat
+    row sweep on global column indices (12/14/18) give the oracle's product."""
+    P, params, H, Hm, Ho = trio
+    Hx = Hm if fp32 else H
+    m = 16
+    rng = np.random.default_rng(42)
+    Hx.vcycle_multi(torch.tensor(rng.standard_normal((m, P.n)), device="cuda"))
+    A = Ho.A[0]
+    X = rng.standard_normal((m, P.n))
+    ref = (A @ X.T).T
+    absA = abs(A)
+    k = np.diff(A.indptr)
+    for slots in (2, 4, 8, 12, 14, 18):
+        if not fp32 and slots in (8, 18):
+            continue                                       # FP64, 16 columns: 8 lanes per row slice
+        Hx.set_block_config(0, slots, fp32=fp32)
+        Y = Hx.level_apply_multi(0, torch.tensor(X, device="cuda"), fp32=fp32).cpu().numpy()
+        for c in range(m):
+            if fp32:
+                bound = (k + 2) * 2.0 ** -24 * (absA @ np.abs(X[c]))
+                assert np.all(np.abs(Y[c] - ref[c]) <= bound), (slots, c)
+            else:
+                assert np.linalg.norm(Y[c] - ref[c]) <= 1e-13 * np.linalg.norm(ref[c]), (slots, c)
+    Hx.set_block_config(0, 14, fp32=fp32)
+    B = _rhs(P, 4, 43)
+    Xs, its, rel = Hx.pcg_multi(torch.tensor(B, device="cuda"), rtol=1e-10)
+    Xs = Xs.cpu().numpy()
+    for c in range(4):
+        assert np.linalg.norm(B[c] - P.scipy() @ Xs[c]) <= 1e-10 * np.linalg.norm(B[c])
