@@ -139,13 +139,13 @@ def _peaks():
     return 6400.0, "fallback"
 
 
-def _traffic(kernel_name):
+def _traffic(kernel_name, source="kernels_level.cuh"):
     """dram bytes per launch from a committed ncu summary, if it matches the current kernel source."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", f"{kernel_name}.md")
     if not os.path.exists(prof):
         return None
-    src = open(os.path.join(ROOT, "paper_2607_28235_b300", "csrc", "kernels_level.cuh"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2607_28235_b300", "csrc", source), "rb").read()
     digest = hashlib.sha256(src).hexdigest()[:16]
     vals = {}
     for line in open(prof):
@@ -249,6 +249,8 @@ def run_batch(args):
 
 MULTI = dict(WORKLOAD, name="poisson3d_q3_64cube_perturbed_16rhs", N=64, leaf_size=256, levels=5, nrhs=16,
              rhs_seed=500)
+# the same 16-column block solve on the 24^3 instance, for ncu captures (inputs > L2, a few GB)
+MULTI_SMALL = dict(MULTI, name="poisson3d_q3_24cube_perturbed_16rhs", N=24, leaf_size=128, levels=4)
 
 
 def run_multi(args):
@@ -258,7 +260,7 @@ def run_multi(args):
     import torch
     import workloads as W
     import paper_2607_28235_b300 as R
-    w = MULTI
+    w = MULTI_SMALL if args.workload == "rhs16_small" else MULTI
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
     P = _problem(w)
@@ -288,8 +290,10 @@ def run_multi(args):
         ms_block, (X, its, rel) = timed(lambda: Hm.pcg_multi(Bd, rtol=w["rtol"]), args.steps, args.warmup)
     # one profiled block solve: per-kind event times of the level operators
     Hm.profile(True)
+    torch.cuda.profiler.start()     # ncu --profile-from-start off sees this pass only
     for _ in range(args.steps):
         Hm.pcg_multi(Bd, rtol=w["rtol"])
+    torch.cuda.profiler.stop()
     prof = Hm.profile_read()
     Hm.profile(False)
     block_cfg = {"fp32": Hm.block_config(fp32=True), "fp64": Hm.block_config(fp32=False)}
@@ -323,6 +327,7 @@ def run_multi(args):
     tk = kinds[top]
     avg_ms = tk["ms"] / tk["launches"]
     achieved = tk["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    kname = f"block_{top}_{'f64' if top.startswith('cg') else 'f32'}"
     info = Hm.info()
     line = {
         "metric": "block PCG solve ms to 1e-8 rel-res (16 right-hand sides)", "value": ms_block, "unit": "ms",
@@ -339,9 +344,11 @@ def run_multi(args):
         "fp64_block": {"ms": ms_block64, "iterations_max": int(its64.max())},
         "mixed_vs_fp64_speedup": ms_block64 / ms_block,
         "setup_s": {"mixed": setup_m, "fp64": setup_d}, "assembly_s": t_asm,
-        "roofline": {"bound": "hbm", "kernel": f"block_{top}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_launch": tk["bytes_per_launch"], "avg_launch_ms": avg_ms, "traffic": None},
+                     "limiter": "the L1 data path serving the gathers of X (ncu: L1 throughput 80%, DRAM 17%)",
+                     "bytes_per_launch": tk["bytes_per_launch"], "avg_launch_ms": avg_ms,
+                     "traffic": _traffic(kname, "kernels_mrhs.cuh")},
         "kernel_time_share": {k: round(v["ms"] / (ms_block * args.steps), 4) for k, v in kinds.items()},
         "block_config": block_cfg,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * m * P.n, "d2h_bytes_per_step": 8 * m * P.n},
@@ -580,11 +587,12 @@ def main():
     ap.add_argument("--save-config", default=None, help="write the autotuned kernel configuration (JSON)")
     ap.add_argument("--kernel-config", default=None, help="replay a saved kernel configuration (JSON)")
     ap.add_argument("--workload", default="full", choices=["full", "small", "cells", "batch256", "rhs16",
-                                                           "pprime_sweep"],
+                                                           "rhs16_small", "pprime_sweep"],
                     help="small: the 24^3 instance used for ncu captures (not a bench line); "
                          "batch256: 256 uneven 2D problems in one batched solve; "
                          "cells: the full problem with cell-based agglomeration; "
-                         "rhs16: 16 right-hand sides on the 64^3 Q3 problem in one block solve; "
+                         "rhs16: 16 right-hand sides on the 64^3 Q3 problem in one block solve "
+                         "(rhs16_small: its 24^3 instance for ncu captures); "
                          "pprime_sweep: the 64^3 Q3 problem with p' = 0..3")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -593,7 +601,7 @@ def main():
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)
-    elif args.workload == "rhs16":
+    elif args.workload in ("rhs16", "rhs16_small"):
         run_multi(args)
     elif args.workload == "pprime_sweep":
         run_sweep(args)
