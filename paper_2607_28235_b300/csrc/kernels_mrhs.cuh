@@ -458,17 +458,16 @@ __global__ void __launch_bounds__(256) k_mr_coarse_stream(LevelView<T> L, const 
 // Coarse-level FP32 operator on M = 8 or 16 columns on the tensor cores.  A box's rows times its
 // window is a dense product D (b x M) = A_B (b x Wp) X_win (Wp x M); it is cut into 16 x 8 tiles
 // of mma.sync m16n8k8 (TF32 inputs, FP32 accumulation), one tile per warp over the whole
-// window.  FP32 accuracy is kept by splitting each operand into a TF32 head and a TF32 tail
-// (x = hi + lo, lo = tf32(x - hi)) and accumulating hi*hi + hi*lo + lo*hi: the dropped lo*lo
-// term and the splits cost at most a few units of 2^-22 relative per product.  The block rows
-// are read straight from global memory (each lane quad reads 32 contiguous bytes of a row per
-// step), the window rows of X through the read-only path by the shared-memory window map.
-// Products only (no dot partials): the Chebyshev step or a plain product.
-__device__ __forceinline__ uint32_t tf32_hi(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+// window.  FP32 accuracy is kept by splitting each operand into a TF32 head and tail by mantissa
+// truncation (hi = x with the low 13 mantissa bits cleared, lo = the same truncation of the
+// exact remainder x - hi) and accumulating hi*hi + hi*lo + lo*hi: the tail truncation and the
+// dropped lo*lo term cost at most 3 * 2^-20 relative per product.  The sum over k is taken in
+// a permuted order (any order of k gives the same product): for two consecutive MMA steps a
+// lane of quad position t holds the window positions 4t .. 4t+3 of its rows, so it reads them
+// as one 16-byte load; the window rows of X come through the read-only path by the
+// shared-memory window map.  Products only (no dot partials): the Chebyshev step or a plain
+// product.
+__device__ __forceinline__ uint32_t tf32_trunc(float x) { return __float_as_uint(x) & 0xffffe000u; }
 
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   asm volatile(
@@ -476,6 +475,24 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// head/tail split of four values, then one split MMA step: fragment element j of the step
+__device__ __forceinline__ void split3_mma(float (&c)[4], const float (&a)[4], const float (&b)[2]) {
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    ah[j] = tf32_trunc(a[j]);
+    al[j] = tf32_trunc(a[j] - __uint_as_float(ah[j]));
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    bh[j] = tf32_trunc(b[j]);
+    bl[j] = tf32_trunc(b[j] - __uint_as_float(bh[j]));
+  }
+  mma_tf32(c, al, bh);
+  mma_tf32(c, ah, bl);
+  mma_tf32(c, ah, bh);
 }
 
 template <int M, class Ep>
@@ -491,11 +508,11 @@ __global__ void __launch_bounds__(128) k_mr_coarse_mma(LevelView<float> L, const
   for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
     const int64_t e0 = L.nbr_ptr[B];
     const int nn = (int)(L.nbr_ptr[B + 1] - e0);
-    const int W = nn * b, Wp = (W + 3) & ~3, W8 = (W + 7) & ~7;
+    const int W = nn * b, Wp = (W + 3) & ~3, W16 = (W + 15) & ~15;
     for (int t = threadIdx.x; t < W; t += blockDim.x) smap[t] = (int32_t)(L.nbr[e0 + t / b] * b + t % b);
-    for (int t = W + threadIdx.x; t < W8; t += blockDim.x) smap[t] = 0;   // zero A entries meet row 0
+    for (int t = W + threadIdx.x; t < W16; t += blockDim.x) smap[t] = 0;   // zero A entries meet row 0
     __syncthreads();
-    const int64_t kbase = L.row_ptr[B * b];                                // box rows: equal length Wp
+    const int64_t kbase = L.row_ptr[B * b];                                 // box rows: equal length Wp
     for (int tile = warp; tile < MT * NT; tile += NW) {
       const int mt = tile / NT, nt = tile % NT;
       const int ra = mt * 16 + gid, rb = ra + 8;
@@ -504,37 +521,30 @@ __global__ void __launch_bounds__(128) k_mr_coarse_mma(LevelView<float> L, const
       const float* Ab = L.vals + kbase + (int64_t)(vb ? rb : 0) * Wp;
       const int n = nt * 8 + gid;
       float c[4] = {0.f, 0.f, 0.f, 0.f};
-      // U steps of 8 window positions are loaded before any is consumed (loads in flight)
-      constexpr int U = 4;
-      for (int k0 = 0; k0 < W8; k0 += 8 * U) {
-        float x[U][4], y[U][2];
+      // one pass = 16 window positions = two MMA steps; U passes of loads in flight
+      constexpr int U = 2;
+      for (int k0 = 0; k0 < W16; k0 += 16 * U) {
+        float4 xa[U], xb[U];
+        float y[U][4];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int ka = k0 + 8 * u + tig, kb = ka + 4;
-          const bool in = ka < W8;                     // kb < W8 as well (W8 is a multiple of 8)
-          x[u][0] = (in && va && ka < Wp) ? __ldg(Aa + ka) : 0.f;
-          x[u][1] = (in && vb && ka < Wp) ? __ldg(Ab + ka) : 0.f;
-          x[u][2] = (in && va && kb < Wp) ? __ldg(Aa + kb) : 0.f;
-          x[u][3] = (in && vb && kb < Wp) ? __ldg(Ab + kb) : 0.f;
-          y[u][0] = in ? __ldg(xin + (int64_t)smap[ka] * M + n) : 0.f;
-          y[u][1] = in ? __ldg(xin + (int64_t)smap[kb] * M + n) : 0.f;
+          const int p = k0 + 16 * u + 4 * tig;          // this lane's 4 window positions
+          const bool in = p < W16;
+          const bool inA = in && p < Wp;                // Wp is a multiple of 4: the 4 are all in or all out
+          xa[u] = (inA && va) ? __ldg(reinterpret_cast<const float4*>(Aa + p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          xb[u] = (inA && vb) ? __ldg(reinterpret_cast<const float4*>(Ab + p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) y[u][e] = in ? __ldg(xin + (int64_t)smap[p + e] * M + n) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          uint32_t ah[4], al[4], bh[2], bl[2];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            ah[j] = tf32_hi(x[u][j]);
-            al[j] = tf32_hi(x[u][j] - __uint_as_float(ah[j]));
-          }
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            bh[j] = tf32_hi(y[u][j]);
-            bl[j] = tf32_hi(y[u][j] - __uint_as_float(bh[j]));
-          }
-          mma_tf32(c, al, bh);
-          mma_tf32(c, ah, bl);
-          mma_tf32(c, ah, bh);
+          // step 0: fragment k = t <- position 4t, k = t+4 <- 4t+1; step 1: 4t+2 and 4t+3
+          const float a0[4] = {xa[u].x, xb[u].x, xa[u].y, xb[u].y};
+          const float b0[2] = {y[u][0], y[u][1]};
+          split3_mma(c, a0, b0);
+          const float a1[4] = {xa[u].z, xb[u].z, xa[u].w, xb[u].w};
+          const float b1[2] = {y[u][2], y[u][3]};
+          split3_mma(c, a1, b1);
         }
       }
       const int col = nt * 8 + 2 * tig;

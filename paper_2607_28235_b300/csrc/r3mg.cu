@@ -2066,7 +2066,7 @@ void mr_launch_mma(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep) {
   if constexpr (mr_mma_ok<T, M, Ep>()) {
     const LevelView<float> v = view<float>(A);
     auto kern = k_mr_coarse_mma<M, Ep>;
-    const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 15) & ~(size_t)7);
+    const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 31) & ~(size_t)15);
     static size_t configured = 48 * 1024;
     if (sm > configured) {
       CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
