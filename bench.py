@@ -183,7 +183,24 @@ def cpu_baseline(reps=2):
             "sample": (f"oracle PCG solve (setup excluded), 1 thread, on the same workload family at 16^3 cells "
                        f"({Ps.n} DoFs, {Ps.nnz} nnz, {its[0]} iterations), best of {reps}: {ms:.1f} ms, "
                        f"scaled by the fine-level nnz ratio {scale:.2f} to the 32^3 workload"),
-            "sample_ms": ms, "sample_iterations": its[0]}
+            "sample_ms": ms, "sample_iterations": its[0]}, (Ps, r)
+
+
+def error_vs_oracle(Ps, ref, dev):
+    """The GPU solves (mixed and FP64) of the oracle's sample problem against the oracle's own
+    PCG solution: relative 2-norm difference of the solutions and the iteration counts."""
+    import numpy as np
+    import torch
+    import paper_2607_28235_b300 as R
+    out = {"problem": f"{SAMPLE['name']} ({Ps.n} DoFs)", "oracle_iterations": ref.iterations}
+    b = torch.tensor(Ps.b, device=dev)
+    for prec, key in ((1, "mixed"), (0, "fp64")):
+        H = R.Hierarchy(Ps.coords, Ps.rowptr, Ps.colidx, Ps.vals, **_hparams(SAMPLE, prec))
+        x, it, rel = H.pcg(b, rtol=SAMPLE["rtol"])
+        xd = x.cpu().numpy()
+        out[key] = {"solution_reldiff": float(np.linalg.norm(xd - ref.x) / np.linalg.norm(ref.x)), "iterations": it}
+        H.close()
+    return out
 
 
 BATCH = dict(name="poisson2d_batch256_uneven", nprob=256, seed=4, leaf_size=64, pprime=1, levels=3, cheb_degree=3,
@@ -573,7 +590,8 @@ def run_ours(args):
     }
     print("gpu part: " + json.dumps(line), file=sys.stderr, flush=True)
     if not args.no_cpu_baseline and w is WORKLOAD:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"], (Ps, ref) = cpu_baseline()
+        line["error_vs_oracle"] = error_vs_oracle(Ps, ref, dev)
     print(json.dumps(line), flush=True)
 
 
