@@ -136,6 +136,14 @@ __global__ void k_reduce(const double* __restrict__ part, int m, double* scal, i
   }
 }
 
+// *flag = 1 if any entry of x is nonzero (a zero initial guess lets the solver skip A x0).
+__global__ void k_any_nonzero(const double* __restrict__ x, int64_t n, int* __restrict__ flag) {
+  bool any = false;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    any = any || (x[k] != 0.0);
+  if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 // y = dinv * x (Jacobi) for the Lanczos estimate; partial x . y.
 __global__ void k_jacobi_dot(const double* __restrict__ dinv, const double* __restrict__ x, double* __restrict__ y,
                              int64_t n, double* part) {

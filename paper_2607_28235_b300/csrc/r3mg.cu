@@ -147,6 +147,7 @@ struct r3mg_hierarchy {
   int lgraph_state = 0;
   int* d_its = nullptr;
   double* d_loop = nullptr;
+  int* d_flag = nullptr;              // zero-initial-guess test
   double bgraph_rtol = -1.0;
   int bgraph_maxit = -1;
   // ---- several right-hand sides (row-interleaved blocks of M columns)
@@ -1326,6 +1327,21 @@ void build_loop_graph(r3mg_hierarchy* h) {
   if (!ok) { h->lgraph = nullptr; cudaGetLastError(); }
 }
 
+// True when the n FP64 entries of x are all zero: the initial residual is then b itself, and
+// the product A x0 (a full pass over the fine matrix) is skipped.
+bool all_zero(r3mg_hierarchy* h, const double* x, int64_t n) {
+  if (!h->d_flag) h->d_flag = dalloc<int>(h, 1);
+  CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+  k_any_nonzero<<<grid_for(n), 256, 0, h->stream>>>(x, n, h->d_flag);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h->host_scal[13], h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int f = 0;
+  std::memcpy(&f, &h->host_scal[13], sizeof(int));
+  h->launches += 1;
+  return f == 0;
+}
+
 // PCG (FP64 V-cycle) or flexible CG (FP32 V-cycle) on tree-ordered b (cb) and x (cx).
 template <typename T>
 r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double* relres) {
@@ -1334,9 +1350,10 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
   const int64_t n = h->n;
   const bool fcg = (h->prm.precision == 1);
   const int gv = grid_for(n);
-  auto true_residual = [&](double& rr, double* bb) {
-    level_apply_dot<double>(h, F, h->cx, h->cq, nullptr, nullptr);
-    k_residual<<<gv, 256, 0, s>>>(h->cb, h->cq, h->cr, n, h->part_a, bb ? h->part_b : nullptr);
+  auto true_residual = [&](double& rr, double* bb, bool x_zero = false) {
+    // with x = 0, A x = 0 = x: the residual takes x itself in place of the product
+    if (!x_zero) level_apply_dot<double>(h, F, h->cx, h->cq, nullptr, nullptr);
+    k_residual<<<gv, 256, 0, s>>>(h->cb, x_zero ? h->cx : h->cq, h->cr, n, h->part_a, bb ? h->part_b : nullptr);
     CK(cudaGetLastError());
     rr = reduce_read(h, h->part_a, gv, S_RR);
     if (bb) *bb = reduce_read(h, h->part_b, gv, S_BB);
@@ -1352,7 +1369,7 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
     CK(cudaMemcpyAsync(h->cp, h->cz, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   };
   double rr = 0.0, bb = 0.0;
-  true_residual(rr, &bb);
+  true_residual(rr, &bb, all_zero(h, h->cx, n));
   const double bnorm = std::sqrt(bb);
   *iters = 0;
   if (bnorm == 0.0) {
@@ -2416,9 +2433,11 @@ r3mg_status mr_krylov(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its
   const int S64 = mr_S64<M>(h);
   double* hs = h->mr_host;                       // [0, 16) rr, [16, 32) bb, [32, 48) its / active
   int* hi = reinterpret_cast<int*>(hs + 32);     // its: hi[0..16), active: hi[16..32)
-  auto true_residual = [&](bool with_bb) {
-    mr_level<double, M>(h, F, h->mr_xc, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S64);
-    k_mr_residual<M><<<gv, 256, 0, s>>>(h->mr_b, h->mr_q, h->mr_rc, nm, h->mr_pa, with_bb ? h->mr_pb : nullptr);
+  auto true_residual = [&](bool with_bb, bool x_zero = false) {
+    // with X = 0 the residual takes X itself in place of the product A X
+    if (!x_zero) mr_level<double, M>(h, F, h->mr_xc, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S64);
+    k_mr_residual<M><<<gv, 256, 0, s>>>(h->mr_b, x_zero ? h->mr_xc : h->mr_q, h->mr_rc, nm, h->mr_pa,
+                                        with_bb ? h->mr_pb : nullptr);
     CK(cudaGetLastError());
     k_mr_reduce<M><<<1, 32 * M, 0, s>>>(h->mr_pa, gv, h->mr_scal, S_RR, FIN_NONE, nullptr, nullptr);
     if (with_bb) k_mr_reduce<M><<<1, 32 * M, 0, s>>>(h->mr_pb, gv, h->mr_scal, S_BB, FIN_NONE, nullptr, nullptr);
@@ -2434,7 +2453,7 @@ r3mg_status mr_krylov(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its
     CK(cudaMemcpyAsync(h->mr_p, h->mr_z, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
     h->launches += 3;
   };
-  true_residual(true);
+  true_residual(true, all_zero(h, h->mr_xc, nm));
   std::vector<double> bb(M), rel(M, 0.0);
   std::vector<int> its(M, 0), act(M, 0);
   unsigned zero_mask = 0;
