@@ -160,6 +160,19 @@ def _traffic(kernel_name, source="kernels_level.cuh"):
         return None
 
 
+def _host_cpu():
+    """CPU model and logical core count of the host the oracle runs on."""
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"model": model, "logical_cores": os.cpu_count()}
+
+
 def cpu_baseline(reps=2):
     """The oracle as it stands on the host cores (1 thread), bounded sample, scaled to the workload."""
     import oracle as O
@@ -179,7 +192,7 @@ def cpu_baseline(reps=2):
             its.append(r.iterations)
     ms = min(times)
     scale = nfull / Ps.nnz
-    return {"value": ms * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+    return {"value": ms * scale, "unit": "ms", "cores": 1, "kind": "oracle", "host": _host_cpu(),
             "sample": (f"oracle PCG solve (setup excluded), 1 thread, on the same workload family at 16^3 cells "
                        f"({Ps.n} DoFs, {Ps.nnz} nnz, {its[0]} iterations), best of {reps}: {ms:.1f} ms, "
                        f"scaled by the fine-level nnz ratio {scale:.2f} to the 32^3 workload"),
