@@ -255,6 +255,15 @@ r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int sl
  */
 r3mg_status r3mg_level_apply(r3mg_hierarchy* h, int level, const double* x_dev, double* y_dev, void* stream);
 
+/*
+ * The coarsest-level solve of the V-cycle on its own: z = A_{L-1}^{-1} r with the explicit
+ * inverse formed at setup from the dense Cholesky factor (the paper's coarse direct solve,
+ * Section 6, read as a dense Cholesky), FP64.  r_dev, z_dev: device, n_{L-1} doubles in
+ * coarsest-level numbering (box * b + q); no aliasing.  Asynchronous.
+ * Errors: R3MG_E_ARG (null pointer, batched hierarchy), R3MG_E_CUDA.
+ */
+r3mg_status r3mg_coarse_solve(r3mg_hierarchy* h, const double* r_dev, double* z_dev, void* stream);
+
 /* Level sizes: n_out[l] rows, nnz_out[l] stored values (padding excluded),
  * nbox_out[l] boxes (level 0: number of level-1 boxes), lam_out[l] upper
  * Chebyshev interval end (0 on the coarsest level).  Arrays hold `levels`

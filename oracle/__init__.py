@@ -33,7 +33,7 @@ computation; none is "parity unpinned".
 from .basis import gll_nodes01, lagrange_1d, box_basis
 from .rtree import Partition, cell_partition, rtree_partition
 from .transfer import prolongation_fine, prolongation_coarse, coarse_nodes
-from .hierarchy import Hierarchy, build_hierarchy, galerkin, block_pattern, lanczos_lmax, cholesky_lower
+from .hierarchy import Hierarchy, build_hierarchy, galerkin, block_pattern, lanczos_lmax, cholesky_lower, cholesky_solve
 from .solve import chebyshev_sweep, vcycle, pcg, fcg, PCGResult
 from .adjoint import solve_adjoint_grads
 from .rng import splitmix64_uniform
@@ -41,6 +41,6 @@ from .rng import splitmix64_uniform
 __all__ = [
     "gll_nodes01", "lagrange_1d", "box_basis", "Partition", "rtree_partition", "cell_partition", "prolongation_fine",
     "prolongation_coarse", "coarse_nodes", "Hierarchy", "build_hierarchy", "galerkin", "block_pattern",
-    "lanczos_lmax", "cholesky_lower", "chebyshev_sweep", "vcycle", "pcg", "fcg", "PCGResult",
+    "lanczos_lmax", "cholesky_lower", "cholesky_solve", "chebyshev_sweep", "vcycle", "pcg", "fcg", "PCGResult",
     "solve_adjoint_grads", "splitmix64_uniform",
 ]

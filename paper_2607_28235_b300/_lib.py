@@ -83,6 +83,7 @@ def lib():
         "r3mg_pcg": (ip, [vp, vp, vp, dbl, i32, P(ctypes.c_int), P(ctypes.c_double), vp]),
         "r3mg_pcg_host": (ip, [vp, vp, vp, dbl, i32, P(ctypes.c_int), P(ctypes.c_double), vp]),
         "r3mg_level_apply": (ip, [vp, i32, vp, vp, vp]),
+        "r3mg_coarse_solve": (ip, [vp, vp, vp, vp]),
         "r3mg_pcg_multi": (ip, [vp, i32, vp, vp, dbl, i32, vp, vp, vp]),
         "r3mg_vcycle_multi": (ip, [vp, i32, vp, vp, vp]),
         "r3mg_level_apply_multi": (ip, [vp, i32, i32, i32, vp, vp, vp]),

@@ -3006,6 +3006,16 @@ r3mg_status r3mg_pcg_host(r3mg_hierarchy* h, const double* b_host, double* x_hos
   return res == R3MG_OK ? st2 : res;
 }
 
+r3mg_status r3mg_coarse_solve(r3mg_hierarchy* h, const double* r_dev, double* z_dev, void* stream) {
+  if (!h || !r_dev || !z_dev) return R3MG_E_ARG;
+  if (!h->bl.empty()) { h->err = "coarse_solve: batched hierarchy"; return R3MG_E_ARG; }
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    k_dense_gemv<double><<<grid_for(h->nc * 32), 256, 0, h->stream>>>(h->Ainv64, h->ncp, r_dev, h->nc, z_dev);
+    CK(cudaGetLastError());
+  });
+}
+
 r3mg_status r3mg_level_apply(r3mg_hierarchy* h, int level, const double* x_dev, double* y_dev, void* stream) {
   if (!h || level < 0 || level >= h->L || !x_dev || !y_dev) return R3MG_E_ARG;
   return guarded(h, [&] {

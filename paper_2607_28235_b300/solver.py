@@ -192,6 +192,14 @@ class Hierarchy:
         assert vals.is_cuda and vals.dtype == torch.float64 and vals.numel() == self.nnz
         _check(lib().r3mg_update_values(self._h, _p(vals), _stream()), self._h)
 
+    def coarse_solve(self, r: torch.Tensor) -> torch.Tensor:
+        """z = A_{L-1}^{-1} r on the coarsest level (FP64, coarsest-level numbering)."""
+        r = r.contiguous()
+        assert r.is_cuda and r.dtype == torch.float64
+        z = torch.empty_like(r)
+        _check(lib().r3mg_coarse_solve(self._h, _p(r), _p(z), _stream()), self._h)
+        return z
+
     def level_apply(self, level: int, x: torch.Tensor) -> torch.Tensor:
         x = x.contiguous()
         y = torch.empty_like(x)

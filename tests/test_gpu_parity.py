@@ -92,6 +92,20 @@ def test_level_apply_and_lambda(pair):
             assert abs(info["lam_hi"][lev] - Ho.lam[lev][1]) <= 1e-11 * Ho.lam[lev][1]
 
 
+def test_coarsest_solve(pair):
+    """The coarsest solve (explicit inverse from the dense Cholesky factor) against the oracle's
+    Cholesky solve, within cond(A_c) * 1e-14 relative (forming and applying the inverse and the
+    two triangular solves each err by a modest multiple of cond(A_c) * eps)."""
+    P, params, H, Ho = pair
+    Ac = Ho.A[-1].toarray()
+    r = np.random.default_rng(9).standard_normal(Ac.shape[0])
+    z = H.coarse_solve(torch.tensor(r, device="cuda")).cpu().numpy()
+    ref = O.cholesky_solve(Ho.Lc, r)
+    tol = 1e-14 * np.linalg.cond(Ac)
+    assert np.linalg.norm(z - ref) <= tol * np.linalg.norm(ref), (np.linalg.norm(z - ref) / np.linalg.norm(ref), tol)
+    assert np.linalg.norm(Ac @ z - r) <= tol * np.linalg.norm(Ac) * np.linalg.norm(z)
+
+
 def test_vcycle_fp64_parity(pair):
     P, params, H, Ho = pair
     rng = np.random.default_rng(2)
