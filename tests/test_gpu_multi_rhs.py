@@ -58,13 +58,16 @@ def test_block_level_products(trio, m):
             with pytest.raises(RuntimeError):
                 Hm.level_apply_multi(lev, torch.tensor(X, device="cuda"), fp32=True)
             continue
-        # FP32 values and inputs, FP32 accumulation
+        # FP32 values and inputs, FP32 accumulation; the bound of the form the tuner chose
+        # (the tensor-core form adds its TF32 head/tail splitting error, see below)
         Y32 = Hm.level_apply_multi(lev, torch.tensor(X, device="cuda"), fp32=True).cpu().numpy()
         absA = abs(A)
         k = np.diff(A.indptr)
+        form = Hm.block_config(fp32=True)[min(lev, params["levels"] - 2)]
+        kk = 2 * k + 64 if form == 3 else k + 2
         for c in range(m):
-            bound = (k + 2) * 2.0 ** -24 * (absA @ np.abs(X[c]))
-            assert np.all(np.abs(Y32[c] - ref[c]) <= bound), (lev, c)
+            bound = kk * 2.0 ** -24 * (absA @ np.abs(X[c]))
+            assert np.all(np.abs(Y32[c] - ref[c]) <= bound), (lev, c, form)
 
 
 @pytest.mark.parametrize("m", [3, 16])
@@ -247,3 +250,18 @@ def test_block_kernel_forms_on_the_fine_level(trio, fp32):
     Xs = Xs.cpu().numpy()
     for c in range(4):
         assert np.linalg.norm(B[c] - P.scipy() @ Xs[c]) <= 1e-10 * np.linalg.norm(B[c])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_block_loop_graph_matches_host_loop(trio, precision):
+    """The block solve loop as one conditional-graph launch and the profiled, host-driven loop run
+    the same kernels in the same order: same iterations per column, same bits."""
+    P, params, H, Hm, Ho = trio
+    Hx = Hm if precision else H
+    B = torch.tensor(_rhs(P, 6, 44), device="cuda")
+    Xg, itg, _ = Hx.pcg_multi(B, rtol=1e-10)
+    Hx.profile(True)
+    Xh, ith, _ = Hx.pcg_multi(B, rtol=1e-10)
+    Hx.profile(False)
+    assert np.array_equal(itg, ith) and np.all(itg > 0)
+    assert torch.equal(Xg, Xh)
