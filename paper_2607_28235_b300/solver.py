@@ -176,10 +176,19 @@ class Hierarchy:
     def set_block_config(self, level: int, slots: int, fp32: bool = False):
         _check(lib().r3mg_set_block_config(self._h, int(level), 1 if fp32 else 0, int(slots)), self._h)
 
-    def pcg_host(self, b: np.ndarray, x0: np.ndarray | None = None, rtol: float = 1e-8, maxit: int = 500):
-        """Host buffers in and out; the copies happen inside the library call."""
+    def pcg_host(self, b: np.ndarray, x0: np.ndarray | None = None, rtol: float = 1e-8, maxit: int = 500,
+                 out: np.ndarray | None = None):
+        """Host buffers in and out; the copies happen inside the library call.  `out` (optional,
+        float64, n, e.g. a view of pinned memory) holds the initial guess on entry (x0 is copied
+        into it when given) and receives the solution."""
         b = np.ascontiguousarray(b, dtype=np.float64)
-        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+        if out is not None:
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == b.shape
+            x = out
+            if x0 is not None:
+                x[:] = x0
+        else:
+            x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
         it = ctypes.c_int(0)
         rel = ctypes.c_double(0)
         rc = lib().r3mg_pcg_host(self._h, _p(b), _p(x), float(rtol), int(maxit), ctypes.byref(it),
