@@ -458,10 +458,11 @@ __global__ void __launch_bounds__(256) k_mr_coarse_stream(LevelView<T> L, const 
 // Coarse-level FP32 operator on M = 8 or 16 columns on the tensor cores.  A box's rows times its
 // window is a dense product D (b x M) = A_B (b x Wp) X_win (Wp x M); it is cut into 16 x 8 tiles
 // of mma.sync m16n8k8 (TF32 inputs, FP32 accumulation), one tile per warp over the whole
-// window.  FP32 accuracy is kept by splitting each operand into a TF32 head and tail by mantissa
-// truncation (hi = x with the low 13 mantissa bits cleared, lo = the same truncation of the
-// exact remainder x - hi) and accumulating hi*hi + hi*lo + lo*hi: the tail truncation and the
-// dropped lo*lo term cost at most 3 * 2^-20 relative per product.  The sum over k is taken in
+// window.  Near-FP32 accuracy is kept by splitting each operand into a TF32 head and tail by
+// mantissa truncation (hi = x with the low 13 mantissa bits cleared, lo = the same truncation
+// of the exact remainder x - hi) and accumulating hi*hi + hi*lo + lo*hi: the tail truncation
+// and the dropped lo*lo term cost at most 3 * 2^-20 relative per product (about 22 bits where
+// FP32 rounding keeps 24; plain TF32 would keep 11).  The sum over k is taken in
 // a permuted order (any order of k gives the same product): for two consecutive MMA steps a
 // lane of quad position t holds the window positions 4t .. 4t+3 of its rows, so it reads them
 // as one 16-byte load; the window rows of X come through the read-only path by the

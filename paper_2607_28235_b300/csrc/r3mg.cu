@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <limits>
+#include <map>
 #include <mutex>
 #include <cmath>
 #include <cstdio>
@@ -218,6 +219,23 @@ LevelView<T> view(const Level& L) {
   return v;
 }
 
+// The opt-in dynamic shared-memory limit is an attribute of a kernel on one device: raise it once
+// per (kernel, device) to the largest size launched there (before any graph capture: the
+// setup's warm-up launches do this).
+void ensure_smem(const void* func, size_t sm) {
+  if (sm <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = done[{func, dev}];
+  if (sm > cur) {
+    CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    cur = sm;
+  }
+}
+
 // loads in flight per lane: 4 x 16-byte steps (FP32) or 2 x 32-byte steps (FP64)
 template <typename T, bool FINE>
 constexpr int unroll_for() { return sizeof(T) == 4 ? 4 : 2; }
@@ -240,11 +258,7 @@ void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, c
   if (pf) {
     const size_t sm = level_smem_bytes(v);
     auto kern = level_kernel<T, G, FINE, Ep, U, false, true>;
-    static size_t configured = 48 * 1024;
-    if (sm > configured) {
-      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      configured = sm;
-    }
+    ensure_smem((const void*)kern, sm);
     kern<<<(int)std::max<int64_t>(1, v.nbox), nt, sm, s>>>(v, xin, ep, part);
     CK(cudaGetLastError());
     return;
@@ -253,11 +267,7 @@ void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, c
     // persistent form: two windows per CTA, grid sized to the CTAs that fit the SMs
     const size_t sm = 2 * level_smem_bytes(v);
     auto kern = level_kernel<T, G, FINE, Ep, U, true, false>;
-    static size_t configured = 48 * 1024;
-    if (sm > configured) {
-      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      configured = sm;
-    }
+    ensure_smem((const void*)kern, sm);
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / nt, (kMaxSmem + 1024) / (sm + 1024)));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(v.nbox, (int64_t)nsm * per_sm));
     kern<<<grid, nt, sm, s>>>(v, xin, ep, part);
@@ -268,11 +278,7 @@ void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, c
   auto kern = level_kernel<T, G, FINE, Ep, U, false, false>;
   // opt in to more than 48 KB of dynamic shared memory per instantiation (the setup's warm-up
   // V-cycle does this before any graph capture)
-  static size_t configured = 48 * 1024;
-  if (sm > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    configured = sm;
-  }
+  ensure_smem((const void*)kern, sm);
   const int grid = (int)std::max<int64_t>(1, v.nbox);
   kern<<<grid, nt, sm, s>>>(v, xin, ep, part);
   CK(cudaGetLastError());
@@ -346,11 +352,7 @@ void launch_tma_g(const Level& A, const Level::Items& it, const T* xin, Ep ep, d
   v.desc = it.desc; v.desc_off = it.desc_off; v.nitems = it.nitems; v.stage_entries = it.SE; v.max_item_rows = it.rmax;
   v.desc_max = it.dmax; v.err = err;
   auto kern = level_kernel_tma<T, G, FINE, Ep>;
-  static size_t configured = 48 * 1024;
-  if (it.smem > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)it.smem));
-    configured = it.smem;
-  }
+  ensure_smem((const void*)kern, it.smem);
   kern<<<it.grid, A.conf[sizeof(T) == 4 ? 1 : 0].nt, it.smem, s>>>(v, xin, ep, part);
   CK(cudaGetLastError());
 }
@@ -514,12 +516,8 @@ void build_sym(r3mg_hierarchy* h, Level& A) {
 }
 
 void sym_step(r3mg_hierarchy* h, const Level& A, const float* d, SymCheb ep) {
-  static size_t configured = 48 * 1024;
   const size_t sm = sizeof(float) * 8 * (size_t)A.sym.win_max;
-  if (sm > configured) {
-    CK(cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    configured = sm;
-  }
+  ensure_smem((const void*)k_sym_block, sm);
   k_sym_block<<<(int)std::max<int64_t>(1, (A.nbox + 7) / 8), 256, sizeof(float) * 8 * (size_t)A.sym.win_max,
                 h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
   k_sym_finish<<<grid_for(A.n), 256, 0, h->stream>>>(A.sym, A.sym_y, A.sym_t, ep);
@@ -1991,11 +1989,7 @@ void mr_build_gidx(r3mg_hierarchy* h) {
   h->mr_gidx = dalloc<int32_t>(h, F.stored);
   const LevelView<double> v = view<double>(F);
   const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 7) & ~(size_t)3);
-  static size_t configured = 48 * 1024;
-  if (sm > configured) {
-    CK(cudaFuncSetAttribute(k_mr_build_gidx<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    configured = sm;
-  }
+  ensure_smem((const void*)k_mr_build_gidx<double>, sm);
   k_mr_build_gidx<double><<<(int)std::min<int64_t>(F.nbox, (int64_t)h->nsm * 8), 256, sm, h->stream>>>(v, h->mr_gidx);
   CK(cudaGetLastError());
 }
@@ -2005,11 +1999,7 @@ void mr_launch(const Level& A, const T* x, Ep ep, double* part, cudaStream_t s, 
   const LevelView<T> v = view<T>(A);
   auto kern = k_mr_level<T, M, S, FINE, Ep>;
   const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 7) & ~(size_t)3);
-  static size_t configured = 48 * 1024;
-  if (sm > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    configured = sm;
-  }
+  ensure_smem((const void*)kern, sm);
   kern<<<grid, 256, sm, s>>>(v, x, ep, part);
   CK(cudaGetLastError());
 }
@@ -2032,11 +2022,7 @@ void mr_launch_coarse(const Level& A, const T* x, Ep ep, double* part, cudaStrea
   const LevelView<T> v = view<T>(A);
   auto kern = k_mr_coarse<T, M, R, Ep>;
   const size_t sm = mr_coarse_smem<T, M>(v);
-  static size_t configured = 48 * 1024;
-  if (sm > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    configured = sm;
-  }
+  ensure_smem((const void*)kern, sm);
   kern<<<grid, 256, sm, s>>>(v, x, ep, part);
   CK(cudaGetLastError());
 }
@@ -2065,11 +2051,7 @@ void mr_launch_stream(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, doub
                       int grid) {
   const LevelView<T> v = view<T>(A);
   auto kern = k_mr_coarse_stream<T, M, R, Ep>;
-  static size_t configured = 48 * 1024;
-  if (lay.total > configured) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
-    configured = lay.total;
-  }
+  ensure_smem((const void*)kern, lay.total);
   kern<<<grid, 256, lay.total, h->stream>>>(v, x, ep, part, lay, h->tma_err);
   CK(cudaGetLastError());
 }
@@ -2084,11 +2066,7 @@ void mr_launch_mma(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep) {
     const LevelView<float> v = view<float>(A);
     auto kern = k_mr_coarse_mma<M, Ep>;
     const size_t sm = sizeof(int32_t) * (((size_t)v.win_max + 31) & ~(size_t)15);
-    static size_t configured = 48 * 1024;
-    if (sm > configured) {
-      CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      configured = sm;
-    }
+    ensure_smem((const void*)kern, sm);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * 16));
     kern<<<grid, 128, sm, h->stream>>>(v, x, ep);
     CK(cudaGetLastError());

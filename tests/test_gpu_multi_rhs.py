@@ -5,7 +5,8 @@ Tolerances: FP64 block level products 1e-13 relative (as the single-vector produ
 products within (row entries + 2) * 2^-24 * (|A| |x|)_i per row, the rounding bound of a
 length-k FP32 dot product with rounded inputs; FP64 block V-cycle 1e-12 relative per column;
 FP32 block V-cycle no less accurate against the FP64 oracle than the single-vector FP32
-V-cycle (4x its error); PCG per column: iterations +-1 and the solution within 1e-10 relative
+V-cycle (4x its error, plus 4 x 3 * 2^-20 relative where a coarse level runs on the tensor
+cores, whose TF32 operand splitting costs up to 3 * 2^-20 per product); PCG per column: iterations +-1 and the solution within 1e-10 relative
 of the oracle's PCG (FP64), or the FP64 residual reached and the solution within 1e3 * rtol (FP32
 V-cycle inside FCG).
 """
@@ -76,13 +77,18 @@ def test_block_vcycle(trio, m):
     R = _rhs(P, m, 20 + m)
     Z = H.vcycle_multi(torch.tensor(R, device="cuda")).cpu().numpy()
     Z32 = Hm.vcycle_multi(torch.tensor(R, device="cuda")).cpu().numpy()
+    # where the tuner put a coarse level on the tensor cores, their operand splitting costs up
+    # to 3 * 2^-20 relative per product (against 2^-24 for FP32 rounding): allow 4x that,
+    # relative to the result, on top of the single-vector FP32 V-cycle's error
+    cfg = Hm.block_config(fp32=True)
+    extra = 4 * 3 * 2.0 ** -20 if any(f == 3 for f in cfg[1:params["levels"] - 1]) else 1e-7
     for c in range(m):
         ref = O.vcycle(Ho, R[c])
         assert np.linalg.norm(Z[c] - ref) <= 1e-12 * np.linalg.norm(ref), c
         single32 = Hm.vcycle(torch.tensor(R[c], device="cuda")).cpu().numpy()
         e1 = np.linalg.norm(single32 - ref)
         e2 = np.linalg.norm(Z32[c] - ref)
-        assert e2 <= 4 * e1 + 1e-7 * np.linalg.norm(ref), (c, e1, e2)
+        assert e2 <= 4 * e1 + extra * np.linalg.norm(ref), (c, e1, e2, cfg)
     # a replay gives the same bits
     Z2 = H.vcycle_multi(torch.tensor(R, device="cuda")).cpu().numpy()
     assert np.array_equal(Z, Z2)
