@@ -110,3 +110,29 @@ def test_partition_cells_errors(lib):
     orphan = np.where(pts == 4, -1, pts)                      # point 4 in no cell
     with pytest.raises(RuntimeError):
         R.partition_cells(P.coords, ptr, orphan, 4, 2)
+
+
+def test_null_handles_and_pointers_are_argument_errors(lib):
+    """Every solve-path entry point refuses a null hierarchy or null buffers with R3MG_E_ARG before
+    touching the GPU (so these checks run without one)."""
+    import ctypes
+    null = ctypes.c_void_p(0)
+    one = ctypes.c_void_p(8)          # a non-null pointer that is never dereferenced
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    E_ARG = 1
+    assert lib.r3mg_pcg(null, one, one, 1e-8, 10, ctypes.byref(it), ctypes.byref(rel), null) == E_ARG
+    assert lib.r3mg_vcycle(null, one, one, null) == E_ARG
+    assert lib.r3mg_level_apply(null, 0, one, one, null) == E_ARG
+    assert lib.r3mg_coarse_solve(null, one, one, null) == E_ARG
+    assert lib.r3mg_update_values(null, one, null) == E_ARG
+    its = np.zeros(4, np.int32)
+    rels = np.zeros(4)
+    assert lib.r3mg_pcg_multi(null, 4, one, one, 1e-8, 10, its.ctypes.data, rels.ctypes.data, null) == E_ARG
+    assert lib.r3mg_vcycle_multi(null, 4, one, one, null) == E_ARG
+    assert lib.r3mg_level_apply_multi(null, 0, 4, 0, one, one, null) == E_ARG
+    s = ctypes.c_int(0)
+    assert lib.r3mg_block_config(null, 0, 1, ctypes.byref(s)) == E_ARG
+    assert lib.r3mg_set_block_config(null, 0, 1, 4) == E_ARG
+    assert lib.r3mg_level0_apply_noalloc(null, one, one, null) == E_ARG
+    lib.r3mg_destroy(null)            # a no-op
