@@ -16,9 +16,12 @@ sharing no code, table or constant generator with the CUDA library:
                 (Section 4; Section 5, eq. (localinterpolation))
   transfer.py   fine-to-level-1 prolongation P and inter-level P~ (Section 4)
   hierarchy.py  Galerkin operators A_{l+1} = P^T A_l P, diagonal, Lanczos
-                eigenvalue estimate, coarsest Cholesky (Sections 1, 4, 6)
-  solve.py      Chebyshev-Jacobi smoother, V-cycle, PCG, flexible CG
-                (Section 4; Section 5, Remark on the smoother; Section 6)
+                eigenvalue estimate, coarsest Cholesky, the tables' H and h
+                (Sections 1, 4, 6)
+  solve.py      Chebyshev-Jacobi smoother, V-cycle (FP64, or FP32 for the
+                mixed-precision path), PCG and flexible CG with their
+                condition estimates and stop tests (Section 4; Section 5,
+                Remark on the smoother; Section 6)
   adjoint.py    gradient of a quadratic loss through the solve
 
 Everything is float64 numpy/scipy.  A library primitive (sparse product,
@@ -33,8 +36,9 @@ computation; none is "parity unpinned".
 from .basis import gll_nodes01, lagrange_1d, box_basis
 from .rtree import Partition, cell_partition, rtree_partition
 from .transfer import prolongation_fine, prolongation_coarse, coarse_nodes
-from .hierarchy import Hierarchy, build_hierarchy, galerkin, block_pattern, lanczos_lmax, cholesky_lower, cholesky_solve
-from .solve import chebyshev_sweep, vcycle, pcg, fcg, PCGResult
+from .hierarchy import (Hierarchy, build_hierarchy, galerkin, block_pattern, lanczos_lmax, cholesky_lower, cholesky_solve,
+                        mesh_stats)
+from .solve import chebyshev_sweep, vcycle, pcg, fcg, PCGResult, as_precision
 from .adjoint import solve_adjoint_grads
 from .rng import splitmix64_uniform
 
@@ -42,5 +46,5 @@ __all__ = [
     "gll_nodes01", "lagrange_1d", "box_basis", "Partition", "rtree_partition", "cell_partition", "prolongation_fine",
     "prolongation_coarse", "coarse_nodes", "Hierarchy", "build_hierarchy", "galerkin", "block_pattern",
     "lanczos_lmax", "cholesky_lower", "cholesky_solve", "chebyshev_sweep", "vcycle", "pcg", "fcg", "PCGResult",
-    "solve_adjoint_grads", "splitmix64_uniform",
+    "solve_adjoint_grads", "splitmix64_uniform", "mesh_stats", "as_precision",
 ]

@@ -100,15 +100,34 @@ def cholesky_lower(M: np.ndarray) -> np.ndarray:
 
 
 def cholesky_solve(L: np.ndarray, r: np.ndarray) -> np.ndarray:
-    """z = L^{-T} L^{-1} r by forward then back substitution (textbook loops)."""
+    """z = L^{-T} L^{-1} r by forward then back substitution (textbook loops), in the precision
+    of L and r (float64 unless both are float32)."""
     n = L.shape[0]
-    y = np.empty(n)
+    dt = np.result_type(L.dtype, np.asarray(r).dtype)
+    y = np.empty(n, dt)
     for i in range(n):
         y[i] = (r[i] - L[i, :i] @ y[:i]) / L[i, i]
-    z = np.empty(n)
+    z = np.empty(n, dt)
     for i in reversed(range(n)):
         z[i] = (y[i] - L[i + 1:, i] @ z[i + 1:]) / L[i, i]
     return z
+
+
+def mesh_stats(coords, A: sp.csr_matrix, part: Partition) -> dict:
+    """The mesh quantities of the paper's tables (Section 6, table legend): H = the largest box
+    size on the coarsest level, read as the diameter (Euclidean length of the MBR diagonal) of a
+    coarsest-level box, the paper's "maximal diameter of an agglomerate" (Section 1); h = the
+    largest element size on the fine level.  The method sees support points, not elements:
+    two support points share a stored entry of A exactly when they share an element, so h is
+    read as the largest distance between two points coupled by a stored entry (the largest
+    element diameter over the elements whose vertices are all unknowns)."""
+    x = np.asarray(coords, np.float64)
+    Ac = sp.csr_matrix(A).tocoo()
+    h = float(np.sqrt(np.max(np.sum((x[Ac.row] - x[Ac.col]) ** 2, axis=1))))
+    L = part.levels
+    ext = np.asarray(part.mbr_hi[L - 1]) - np.asarray(part.mbr_lo[L - 1])
+    H = float(np.sqrt(np.max(np.sum(ext ** 2, axis=1))))
+    return {"H": H, "h": h, "H_over_h": H / h}
 
 
 @dataclass

@@ -18,7 +18,7 @@ Reading taken: one smoothing "step" of the paper is one such degree-k
 sweep; pre- and post-smoothing use the same polynomial, so the V-cycle is
 a symmetric operator.  The coarsest level is solved exactly (Cholesky).
 """
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -61,6 +61,18 @@ def vcycle(H, r, level: int = 0):
     return x
 
 
+def as_precision(H, dtype):
+    """The hierarchy H with its operators (A_l, P_l, D_l^{-1}, the coarsest Cholesky factor)
+    rounded to `dtype`.  With float32, ``vcycle`` on it runs every step in single precision
+    with single-precision accumulation (numpy and scipy keep float32 operands in float32), which
+    is the FP32 V-cycle of the mixed-precision solver: the benchmark spec fixes FP32 values,
+    vectors and accumulation for the V-cycle inside an FP64 outer iteration.  The Chebyshev
+    interval stays a pair of Python floats, rounded to `dtype` where it meets an array."""
+    cast = lambda M: M.astype(dtype)
+    return replace(H, A=[cast(A) for A in H.A], P=[cast(P) for P in H.P], dinv=[d.astype(dtype) for d in H.dinv],
+                   Lc=H.Lc.astype(dtype))
+
+
 @dataclass
 class PCGResult:
     x: np.ndarray
@@ -84,8 +96,16 @@ def _cond_from_cg(alphas, betas):
     return float(ev[-1] / ev[0])
 
 
-def pcg(A, b, precond, rtol=1e-8, maxit=500, x0=None):
-    """Preconditioned CG (Hestenes-Stiefel).  Stops when ||r||_2 <= rtol ||b||_2.
+def _threshold(rtol, bnorm, atol, reduction, r0norm):
+    """Stop threshold on ||r||_2: max(rtol ||b||, atol, reduction ||r_0||).  atol = reduction = 0
+    is the relative test of the workloads; rtol = 0, atol = 1e-9, reduction = 1e-6 is the rule
+    of Section 6 (absolute residual below 1e-9, or six orders of reduction)."""
+    return max(rtol * bnorm, atol, reduction * r0norm)
+
+
+def pcg(A, b, precond, rtol=1e-8, maxit=500, x0=None, atol=0.0, reduction=0.0):
+    """Preconditioned CG (Hestenes-Stiefel).  Stops when ||r||_2 <= max(rtol ||b||_2, atol,
+    reduction ||r_0||_2) (by default the relative test ||r|| <= rtol ||b||).
 
     Iterations = number of completed updates of x.  The condition estimate
     (the "Cond." column of the paper's tables) is the ratio of extreme
@@ -94,8 +114,10 @@ def pcg(A, b, precond, rtol=1e-8, maxit=500, x0=None):
     x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
     bnorm = float(np.linalg.norm(b))
     r = b - A @ x
-    hist = [float(np.linalg.norm(r)) / bnorm if bnorm > 0 else 0.0]
-    if bnorm == 0.0 or hist[0] <= rtol:
+    r0norm = float(np.linalg.norm(r))
+    thr = _threshold(rtol, bnorm, atol, reduction, r0norm)
+    hist = [r0norm / bnorm if bnorm > 0 else 0.0]
+    if bnorm == 0.0 or r0norm <= thr:
         return PCGResult(x, 0, hist[0], True, hist, 1.0)
     z = precond(r)
     p = z.copy()
@@ -110,9 +132,10 @@ def pcg(A, b, precond, rtol=1e-8, maxit=500, x0=None):
         x = x + alpha * p
         r = r - alpha * q
         alphas.append(alpha)
-        rel = float(np.linalg.norm(r)) / bnorm
+        rnorm = float(np.linalg.norm(r))
+        rel = rnorm / bnorm
         hist.append(rel)
-        if rel <= rtol:
+        if rnorm <= thr:
             return PCGResult(x, it, rel, True, hist, _cond_from_cg(alphas, betas))
         z = precond(r)
         rz_new = float(r @ z)
@@ -123,21 +146,28 @@ def pcg(A, b, precond, rtol=1e-8, maxit=500, x0=None):
     return PCGResult(x, maxit, hist[-1], False, hist, _cond_from_cg(alphas, betas))
 
 
-def fcg(A, b, precond, rtol=1e-8, maxit=500, x0=None):
+def fcg(A, b, precond, rtol=1e-8, maxit=500, x0=None, atol=0.0, reduction=0.0):
     """Flexible CG with one retained direction (Notay, SIAM J. Sci. Comput. 22, 2000).
 
     p_0 = z_0;  alpha_k = p_k^T r_k / p_k^T A p_k;  x += alpha p;  r -= alpha A p;
     z = M(r);  p_{k+1} = z - (z^T A p_k / p_k^T A p_k) p_k.
     With a fixed SPD preconditioner this equals PCG in exact arithmetic; it
     stays convergent when M varies slightly (a lower-precision V-cycle).
+    In exact arithmetic with a fixed SPD M, z_{k+1}^T A p_k = -r_{k+1}^T z_{k+1} / alpha_k and
+    p_k^T A p_k = r_k^T z_k / alpha_k, so the coefficient above is minus the PCG beta: the
+    condition estimate takes the alphas and the negated coefficients as PCG's.
+    Stop test as in ``pcg``.
     """
     x = np.zeros_like(b) if x0 is None else np.array(x0, np.float64)
     bnorm = float(np.linalg.norm(b))
     r = b - A @ x
-    hist = [float(np.linalg.norm(r)) / bnorm if bnorm > 0 else 0.0]
-    if bnorm == 0.0 or hist[0] <= rtol:
+    r0norm = float(np.linalg.norm(r))
+    thr = _threshold(rtol, bnorm, atol, reduction, r0norm)
+    hist = [r0norm / bnorm if bnorm > 0 else 0.0]
+    if bnorm == 0.0 or r0norm <= thr:
         return PCGResult(x, 0, hist[0], True, hist, 1.0)
     p = precond(r)
+    alphas, betas = [], []
     for it in range(1, maxit + 1):
         q = A @ p
         pq = float(p @ q)
@@ -146,11 +176,14 @@ def fcg(A, b, precond, rtol=1e-8, maxit=500, x0=None):
         alpha = float(p @ r) / pq
         x = x + alpha * p
         r = r - alpha * q
-        rel = float(np.linalg.norm(r)) / bnorm
+        alphas.append(alpha)
+        rnorm = float(np.linalg.norm(r))
+        rel = rnorm / bnorm
         hist.append(rel)
-        if rel <= rtol:
-            return PCGResult(x, it, rel, True, hist, float("nan"))
+        if rnorm <= thr:
+            return PCGResult(x, it, rel, True, hist, _cond_from_cg(alphas, betas))
         z = precond(r)
         beta = float(z @ q) / pq
+        betas.append(-beta)
         p = z - beta * p
-    return PCGResult(x, maxit, hist[-1], False, hist, float("nan"))
+    return PCGResult(x, maxit, hist[-1], False, hist, _cond_from_cg(alphas, betas))

@@ -130,3 +130,71 @@ def test_adjoint_against_finite_differences():
         Ap[rows[k], P.colidx[k]] += h; Am[rows[k], P.colidx[k]] -= h
         fd = (loss(np.linalg.solve(Ap, P.b)) - loss(np.linalg.solve(Am, P.b))) / (2 * h)
         assert abs(fd - gv[k]) <= 1e-6 * max(1, abs(gv[k]))
+
+
+def test_fcg_condition_estimate_is_pcg_estimate():
+    """With a fixed SPD preconditioner flexible CG is PCG: its alphas and negated betas give the
+    same Lanczos tridiagonal, so both estimates agree (and match the dense spectrum of M^{-1}A
+    as pinned above)."""
+    P, H = _small_hierarchy(3)
+    A = H.A[0]
+    rp = pcg(A, P.b, lambda r: vcycle(H, r), rtol=1e-12, maxit=200)
+    rf = fcg(A, P.b, lambda r: vcycle(H, r), rtol=1e-12, maxit=200)
+    assert rp.iterations == rf.iterations
+    assert abs(rf.cond_estimate - rp.cond_estimate) <= 1e-6 * rp.cond_estimate
+    M = np.stack([vcycle(H, e) for e in np.eye(P.n)], 1)
+    ev = np.sort(np.linalg.eigvals(M @ A.toarray()).real)
+    # Ritz values lie inside the spectrum: the estimate never exceeds the true condition number
+    assert rf.cond_estimate <= ev[-1] / ev[0] * (1 + 1e-9)
+    assert rf.cond_estimate > 0.95 * ev[-1] / ev[0]
+
+
+@pytest.mark.parametrize("solver", [pcg, fcg])
+def test_paper_stop_rule_stops_at_first_admissible_iterate(solver):
+    """Section 6's rule (absolute residual < atol or a `reduction` drop of the initial residual)
+    stops at the first iterate that meets either part; the iterates before it are those of a run
+    that never stops early (same arithmetic), so the stopping index is read off that run."""
+    P, H = _small_hierarchy(3)
+    A = H.A[0]
+    ref = solver(A, P.b, lambda r: vcycle(H, r), rtol=0.0, maxit=25)   # never stops early
+    bnorm = np.linalg.norm(P.b)
+    res = np.array(ref.history) * bnorm             # ||r_k||, k = 0, 1, ...
+    for atol, red in [(1e-9, 1e-6), (0.0, 1e-3), (res[4] * 1.0000001, 0.0), (1e-30, 1e-30)]:
+        thr = max(atol, red * res[0])
+        want = next((k for k in range(len(res)) if res[k] <= thr), None)
+        out = solver(A, P.b, lambda r: vcycle(H, r), rtol=0.0, maxit=25, atol=atol, reduction=red)
+        if want is None:
+            assert not out.converged and out.iterations == 25
+        else:
+            assert out.converged and out.iterations == want
+            assert np.array_equal(out.history, ref.history[:want + 1])
+
+
+def test_float32_vcycle_rounds_every_step():
+    """as_precision(H, float32): every operator in single precision, so the V-cycle returns
+    float32, differs from the FP64 V-cycle at the single-precision level (relative 1e-7..1e-4,
+    never 0) and float64 gives the FP64 V-cycle bit for bit."""
+    from oracle.solve import as_precision
+    P, H = _small_hierarchy(3)
+    r = np.random.default_rng(4).standard_normal(P.n)
+    z64 = vcycle(H, r)
+    assert np.array_equal(vcycle(as_precision(H, np.float64), r), z64)
+    z32 = vcycle(as_precision(H, np.float32), r.astype(np.float32))
+    assert z32.dtype == np.float32
+    err = np.linalg.norm(z32 - z64) / np.linalg.norm(z64)
+    assert 1e-8 < err < 1e-4, err
+    assert as_precision(H, np.float32).A[0].dtype == np.float32 and H.A[0].dtype == np.float64
+
+
+def test_threaded_products_give_the_same_bits():
+    """The all-core evaluation (row blocks on a thread pool) forms every row sum as the serial
+    product does: V-cycle and PCG give identical bits."""
+    from oracle.parallel import threaded
+    P, H = _small_hierarchy(3)
+    A = H.A[0]
+    Hp, Ap = threaded(H, A, 3)
+    r = np.random.default_rng(8).standard_normal(P.n)
+    assert np.array_equal(vcycle(Hp, r), vcycle(H, r))
+    a = pcg(A, P.b, lambda v: vcycle(H, v), rtol=1e-10)
+    b = pcg(Ap, P.b, lambda v: vcycle(Hp, v), rtol=1e-10)
+    assert a.iterations == b.iterations and np.array_equal(a.x, b.x)
