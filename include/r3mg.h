@@ -264,6 +264,160 @@ r3mg_status r3mg_level_apply(r3mg_hierarchy* h, int level, const double* x_dev, 
  */
 r3mg_status r3mg_coarse_solve(r3mg_hierarchy* h, const double* r_dev, double* z_dev, void* stream);
 
+/*
+ * One level-operator product in a chosen precision: y = A_l x with the level kernel chosen for
+ * that precision (the kernel the V-cycle runs).  fp32 = 0 is r3mg_level_apply (FP64 values);
+ * fp32 = 1 uses the FP32 values of the FP32 V-cycle (Section 4's level operators stored in
+ * single precision): x is rounded to FP32 (round to nearest), the row sums run in FP32 with FP32
+ * accumulation, y is widened to FP64 exactly.  x_dev, y_dev: device, n_l doubles, level
+ * numbering as in r3mg_level_apply.  The level's V-cycle vectors serve as scratch, so this call
+ * must not overlap a V-cycle or solve on the same hierarchy.  Asynchronous.
+ * Errors: R3MG_E_ARG (fp32 = 1 on an FP64 hierarchy or on the coarsest level), R3MG_E_CUDA.
+ */
+r3mg_status r3mg_level_apply_prec(r3mg_hierarchy* h, int level, int fp32, const double* x_dev, double* y_dev,
+                                  void* stream);
+
+/*
+ * One fused Chebyshev-Jacobi step of the smoother (Section 5, Remark on the smoother; Section 6;
+ * Saad's Algorithm 12.1 with the Jacobi preconditioner D_l^{-1}) on a smoothed level l < L-1, in
+ * the hierarchy's V-cycle precision and with the kernel the V-cycle uses:
+ *   x' = x + d;   r' = r - A_l d;   d' = a d + c D_l^{-1} r'.
+ * x_dev, r_dev, d_dev (device, n_l doubles, level numbering; level 0 = caller numbering) are
+ * read, rounded to the V-cycle precision; x_out, r_out, d_out (device, n_l doubles) receive the
+ * results widened to FP64; a and c are rounded to the V-cycle precision.  Outputs may alias
+ * inputs.  Uses the level's V-cycle vectors as scratch (no overlap with a V-cycle or solve on
+ * the same hierarchy).  Asynchronous.  Errors: R3MG_E_ARG (coarsest level, batched hierarchy).
+ */
+r3mg_status r3mg_level_cheb_step(r3mg_hierarchy* h, int level, const double* x_dev, const double* r_dev,
+                                 const double* d_dev, double a, double c, double* x_out, double* r_out,
+                                 double* d_out, void* stream);
+
+/* The coarsest solve of r3mg_coarse_solve in a chosen precision: fp32 = 1 applies the FP32
+ * copy of the explicit inverse that the FP32 V-cycle uses (r rounded to FP32, FP32 GEMV with
+ * FP32 accumulation, z widened), fp32 = 0 is r3mg_coarse_solve.  Errors: R3MG_E_ARG (fp32 = 1
+ * on an FP64 or batched hierarchy).  Asynchronous. */
+r3mg_status r3mg_coarse_solve_prec(r3mg_hierarchy* h, int fp32, const double* r_dev, double* z_dev, void* stream);
+
+/*
+ * Stop test of r3mg_pcg, r3mg_pcg_host and r3mg_pcg_multi (per column):
+ *     ||r_k||_2 <= max(rtol ||b||_2, atol, reduction ||r_0||_2),   r_0 = b - A x_0,
+ * confirmed on the FP64 true residual.  The defaults atol = reduction = 0 leave the relative
+ * test; rtol = 0 with atol = 1e-9 and reduction = 1e-6 is the paper's rule (Section 6: stop when
+ * the absolute residual norm falls below 1e-9 or the residual has dropped by six orders).
+ * Kept on the hierarchy until changed.  Batched solves keep the relative test.
+ * Errors: R3MG_E_ARG (negative or non-finite value).
+ */
+r3mg_status r3mg_set_stop_rule(r3mg_hierarchy* h, double atol, double reduction);
+
+/*
+ * Condition-number estimate of the last solve (the "Cond." column of the paper's tables,
+ * Section 6: the condition number estimated by PCG).  The solve keeps its CG coefficients
+ * alpha_j, beta_j on the device (the first 1024 of each; a restart from the true residual
+ * begins a new sequence); this call builds the Lanczos tridiagonal T (T_jj = 1/alpha_j +
+ * beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j) on the host and returns its extreme
+ * eigenvalues (Sturm bisection), estimates of those of M^{-1} A.  For flexible CG (FP32
+ * V-cycle) beta is taken with the sign flipped, which is the PCG beta when the preconditioner is
+ * fixed, so the estimate then holds to the FP32 V-cycle's accuracy.
+ *   column < 0: the last r3mg_pcg / r3mg_pcg_host; column >= 0: that column of the last
+ *   r3mg_pcg_multi.  cond_out = lmax / lmin (1 when no iteration ran), lmin_out, lmax_out
+ *   (0 when none), steps_out = size of T.  Any output may be NULL.  Synchronises.
+ * Errors: R3MG_E_ARG (no such column, batched hierarchy), R3MG_E_CUDA.
+ */
+r3mg_status r3mg_cond_estimate(r3mg_hierarchy* h, int column, double* cond_out, double* lmin_out, double* lmax_out,
+                               int* steps_out);
+
+/*
+ * Mesh statistics of the paper's tables (Section 6, table legend): H_out = the largest diameter
+ * (Euclidean length of the MBR diagonal) of a coarsest-level box; h_out = the largest distance
+ * between two support points coupled by a stored entry of A, which is the largest element
+ * diameter over the elements whose vertices are unknowns (two points share a stored entry
+ * exactly when they share an element); ratio_out = H / h.  ritz_out (levels entries, may be
+ * NULL): the Lanczos Ritz value of D_l^{-1} A_l on every smoothed level (the upper Chebyshev
+ * interval end is eig_safety times it), 0 on the coarsest.  Batched hierarchies: maxima over
+ * the problems.  Host-only; never fails on a valid hierarchy.
+ */
+r3mg_status r3mg_stats(r3mg_hierarchy* h, double* H_out, double* h_out, double* ratio_out, double* ritz_out);
+
+/*
+ * Transfer operator between levels l and l+1 (0 <= l < L-1) as a CSR matrix of n_l rows and
+ * n_{l+1} columns (Section 4): l = 0 is P_0 (rows in the caller's numbering, row i has the b
+ * columns box(i)*b + q, q = 0..b-1, value phi_{box(i),q}(x_i)); l >= 1 is the injection P~_l
+ * (row (c, q') has the columns parent(c)*b + q, value phi_{parent(c),q}(xi_{c,q'})).  The
+ * pattern is structural: exactly b entries per row, columns ascending, zeros kept.
+ *   rowptr_host (n_l + 1, required), cols_host (n_l * b, may be NULL), vals_host (n_l * b, FP64,
+ *   may be NULL; reading values synchronises the stream).  n_l from r3mg_info.
+ * Errors: R3MG_E_ARG, R3MG_E_CUDA.
+ */
+r3mg_status r3mg_get_transfer_pattern(r3mg_hierarchy* h, int level, int64_t* rowptr_host, int32_t* cols_host,
+                                      double* vals_host);
+
+/*
+ * Galerkin operator A_l (1 <= l < L, Sections 1 and 4) as a CSR matrix in coarse numbering
+ * (row and column (B, q) = B*b + q): row (B, q') holds, for every neighbour box of B in
+ * ascending order (r3mg_get_level_pattern), the b columns of that box in ascending order; the
+ * dense b x b blocks are stored whole (structural zeros kept), FP64 values.
+ *   rowptr_host (n_l + 1, required); cols_host, vals_host (rowptr[n_l] entries each, may be
+ *   NULL: call once with both NULL to size them).  Reading values synchronises the stream.
+ * Errors: R3MG_E_ARG, R3MG_E_CUDA, R3MG_E_OOM.
+ */
+r3mg_status r3mg_get_level_matrix(r3mg_hierarchy* h, int level, int64_t* rowptr_host, int32_t* cols_host,
+                                  double* vals_host);
+
+/*
+ * Expiry report of the bounded device waits.  The copy-engine-streamed kernels (the TMA level
+ * kernel form and the streamed coarse block kernel) give every mbarrier wait an iteration limit;
+ * on expiry a kernel raises a flag on the hierarchy and returns.  r3mg_pcg, r3mg_pcg_host and
+ * r3mg_pcg_multi read the flag before returning; calls that return without synchronising
+ * (r3mg_vcycle, r3mg_level_apply, r3mg_level0_apply_noalloc, ...) leave it for the next of those
+ * or for this call, which synchronises, returns R3MG_E_TIMEOUT if the flag was raised since the
+ * last check (and clears it), else R3MG_OK.  Callers that replay captured graphs check here.
+ */
+r3mg_status r3mg_device_status(r3mg_hierarchy* h, void* stream);
+
+/*
+ * Form of the coarsest solve (the paper's direct coarse solve, Section 6, read as a dense
+ * Cholesky factorisation A_c = L L^T): mode 0 (default) applies the explicit inverse
+ * A_c^{-1} = L^{-T} L^{-1} formed at setup (one GEMV, every row in parallel); mode 1 runs forward
+ * and back substitution with L (the textbook solve; a chain of dependent 32-row blocks, one CTA
+ * per substitution, solution in shared memory).  Applies to the V-cycle (both precisions) and to
+ * r3mg_coarse_solve / r3mg_coarse_solve_prec.  Drops captured graphs; synchronises.
+ * Errors: R3MG_E_ARG (mode 1 on a batched hierarchy), R3MG_E_LIMIT (mode 1 when the coarsest
+ * level holds more than 26,880 rows, beyond one CTA's shared memory).
+ */
+r3mg_status r3mg_set_coarse_mode(r3mg_hierarchy* h, int mode);
+
+/*
+ * Limit of the bounded mbarrier waits of the copy-engine-streamed kernels on this hierarchy:
+ * cycles = clock64 cycles per wait (0 = the default, about one second at 2 GHz; at most 4e9).
+ * withhold_first_copy = 1 is the library's test of the expiry path: CTA 0 of the TMA level
+ * kernel announces its first descriptor copy on its mbarrier but never issues it, so that wait
+ * runs out; the kernel then raises the flag, waits (bounded) for the copies it did issue, and
+ * returns, and r3mg_device_status reports R3MG_E_TIMEOUT.  0 in normal use.  Drops captured
+ * graphs; synchronises.  Errors: R3MG_E_ARG.
+ */
+r3mg_status r3mg_set_wait_limit(r3mg_hierarchy* h, long long cycles, int withhold_first_copy);
+
+/*
+ * Self-test of the bounded-wait mechanism, on the current device: one CTA waits on an mbarrier
+ * phase whose arrival announces 16 bytes that no copy delivers, so the wait runs out after
+ * limit_cycles (1 .. 4e9) clock64 cycles; the kernel records the expiry, invalidates the
+ * barrier and returns with nothing in flight.  expired_out (may be NULL) = 1 when it ran out.
+ * Returns R3MG_E_TIMEOUT when the wait expired (the expected outcome; the context stays
+ * usable), R3MG_OK if it somehow completed, R3MG_E_ARG, R3MG_E_OOM or R3MG_E_CUDA otherwise.
+ * Allocates and frees one int of device memory; synchronises the stream.
+ */
+r3mg_status r3mg_wait_selftest(long long limit_cycles, int* expired_out, void* stream);
+
+/*
+ * As r3mg_setup with the CSR arrays in device memory (rowptr_dev n+1 int64, colidx_dev nnz
+ * int32, vals_dev nnz doubles; coords stay host).  The library reads the arrays back to the
+ * host on `stream` (the partition and the symbolic analysis are host work) and then proceeds as
+ * r3mg_setup.  Errors: as r3mg_setup.
+ */
+r3mg_status r3mg_setup_device(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_dev,
+                              const int32_t* colidx_dev, const double* vals_dev, const r3mg_params* params,
+                              void* stream, r3mg_hierarchy** out);
+
 /* Level sizes: n_out[l] rows, nnz_out[l] stored values (padding excluded),
  * nbox_out[l] boxes (level 0: number of level-1 boxes), lam_out[l] upper
  * Chebyshev interval end (0 on the coarsest level).  Arrays hold `levels`
@@ -323,11 +477,12 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
  *   x_dev, y_dev: device, n doubles, caller numbering (as r3mg_level_apply); no aliasing.
  * Scratch: a static 16 MiB device array inside the library (two vectors of 2^20 doubles),
  * loaded with the library on every GPU that uses it and kept until the process exits.
- * Limits: n <= 2^20 (1,048,576 DoFs), else R3MG_E_LIMIT and nothing is launched.
- * Set-up: the first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make this first call before any stream
- * capture.  Nothing in the scratch needs clearing: every call overwrites the n entries it
- * reads.  All calls share the one array, which keeps the last call's contents, so calls
+ * Limits: n <= 2^20 (1,048,576 DoFs), else R3MG_E_LIMIT and nothing is launched (y untouched).
+ * Set-up: r3mg_setup / r3mg_batch_setup look up the array's device address
+ * (cudaGetSymbolAddress) on the hierarchy's device and keep it on the hierarchy, so this call
+ * itself needs no set-up step.  Nothing in the scratch needs clearing: every call overwrites
+ * the n entries it reads.  A bounded-wait expiry of the TMA kernel form (if the fine level uses
+ * it) is reported by r3mg_device_status, not by this call.  All calls share the one array, which keeps the last call's contents, so calls
  * whose work overlaps on the GPU (other streams, other threads, other hierarchies on the
  * same device) race and must be serialised by the caller.  Asynchronous on `stream`.
  * Errors: R3MG_E_ARG, R3MG_E_LIMIT, R3MG_E_CUDA.
@@ -359,6 +514,17 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
 
 /* The unroll depth chosen for level l and precision (0 = default, 4). */
 r3mg_status r3mg_kernel_unroll(const r3mg_hierarchy* h, int level, int fp32, int* unroll);
+
+/*
+ * Device characterisation for the FP64 roofline: the sustained FP64 FMA rate and the FP64
+ * tensor-core (mma.sync m8n8k4) rate of the current GPU, in TFLOP/s (2 flops per FMA).  Each is
+ * timed with CUDA events over one launch of 8 independent FMA (or 4 independent mma) chains per
+ * thread on 8 CTAs of 256 threads per SM, after one warm-up launch.  The FP64 level kernels do
+ * one FMA per 8-10 bytes of matrix stream, so on a GPU whose FP64 rate is low next to its memory
+ * bandwidth these rates, not HBM, bound them.  Allocates and frees a small device buffer;
+ * synchronises the stream.  Errors: R3MG_E_CUDA, R3MG_E_OOM.
+ */
+r3mg_status r3mg_measure_fp64_rates(double* fma_tflops, double* mma_tflops, void* stream);
 
 /* Message of the last failure on h (or of the last failed r3mg_setup /
  * r3mg_partition in this thread when h is NULL).  Never NULL. */

@@ -15,7 +15,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("Hierarchy", "BatchHierarchy", "partition", "partition_cells", "default_params"):
+    if name in ("Hierarchy", "BatchHierarchy", "partition", "partition_cells", "default_params", "measure_fp64_rates",
+                "wait_selftest"):
         from . import solver
         return getattr(solver, name)
     if name in ("R3MGSolve", "solve"):

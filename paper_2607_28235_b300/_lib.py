@@ -107,6 +107,21 @@ def lib():
         "r3mg_batch_setup": (ip, [i32, i32, vp, vp, vp, vp, vp, P(_Params), vp, P(vp)]),
         "r3mg_batch_pcg": (ip, [vp, vp, vp, dbl, i32, vp, vp, vp]),
         "r3mg_batch_offsets": (ip, [vp, i32, P(ctypes.c_int), vp]),
+        "r3mg_measure_fp64_rates": (ip, [P(ctypes.c_double), P(ctypes.c_double), vp]),
+        "r3mg_level_apply_prec": (ip, [vp, i32, i32, vp, vp, vp]),
+        "r3mg_level_cheb_step": (ip, [vp, i32, vp, vp, vp, dbl, dbl, vp, vp, vp, vp]),
+        "r3mg_coarse_solve_prec": (ip, [vp, i32, vp, vp, vp]),
+        "r3mg_set_stop_rule": (ip, [vp, dbl, dbl]),
+        "r3mg_cond_estimate": (ip, [vp, i32, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                                    P(ctypes.c_int)]),
+        "r3mg_stats": (ip, [vp, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), vp]),
+        "r3mg_get_transfer_pattern": (ip, [vp, i32, vp, vp, vp]),
+        "r3mg_get_level_matrix": (ip, [vp, i32, vp, vp, vp]),
+        "r3mg_device_status": (ip, [vp, vp]),
+        "r3mg_set_wait_limit": (ip, [vp, ctypes.c_longlong, i32]),
+        "r3mg_set_coarse_mode": (ip, [vp, i32]),
+        "r3mg_wait_selftest": (ip, [ctypes.c_longlong, P(ctypes.c_int), vp]),
+        "r3mg_setup_device": (ip, [i64, i32, vp, vp, vp, vp, P(_Params), vp, P(vp)]),
         "r3mg_last_error": (ctypes.c_char_p, [vp]),
         "r3mg_destroy": (None, [vp]),
     }

@@ -411,7 +411,31 @@ void gll_nodes01(int p, double* z) {
 }
 
 // Largest eigenvalue of a symmetric tridiagonal matrix by Sturm-sequence bisection.
+// Largest distance between two support points coupled by a stored entry of A.  Two points
+// share a stored entry exactly when they share an element, so this is the largest element
+// diameter over the elements whose vertices are all unknowns of the system.
+double max_coupled_distance(int64_t n, int dim, const double* coords, const int64_t* rowptr, const int32_t* colidx) {
+  double m2 = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : m2)
+  for (int64_t i = 0; i < n; ++i) {
+    const double* xi = coords + i * dim;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const double* xj = coords + (int64_t)colidx[k] * dim;
+      double s = 0.0;
+      for (int a = 0; a < dim; ++a) s += (xi[a] - xj[a]) * (xi[a] - xj[a]);
+      m2 = std::max(m2, s);
+    }
+  }
+  return std::sqrt(m2);
+}
+
 double tridiag_max_eig(const std::vector<double>& d, const std::vector<double>& e) {
+  return tridiag_kth_eig(d, e, (int)d.size() - 1);
+}
+
+// The j-th smallest eigenvalue (j = 0 .. k-1) of the symmetric tridiagonal matrix with diagonal
+// d and off-diagonal e, by Sturm-sequence bisection on the Gershgorin interval.
+double tridiag_kth_eig(const std::vector<double>& d, const std::vector<double>& e, int j) {
   const int k = (int)d.size();
   if (k == 0) return 0.0;
   double lo = d[0], hi = d[0];
@@ -432,7 +456,7 @@ double tridiag_max_eig(const std::vector<double>& d, const std::vector<double>& 
   for (int it = 0; it < 200 && hi - lo > 1e-16 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
     const double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (count_below(mid) >= k) hi = mid; else lo = mid;
+    if (count_below(mid) >= j + 1) hi = mid; else lo = mid;
   }
   return 0.5 * (lo + hi);
 }

@@ -58,5 +58,7 @@ bool fine_layout(const HostPartition& P, const HostPattern& pat, const int64_t* 
 bool validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colidx, Error& err);
 void gll_nodes01(int p, double* z);
 double tridiag_max_eig(const std::vector<double>& diag, const std::vector<double>& off);
+double tridiag_kth_eig(const std::vector<double>& diag, const std::vector<double>& off, int j);
+double max_coupled_distance(int64_t n, int dim, const double* coords, const int64_t* rowptr, const int32_t* colidx);
 
 }  // namespace r3mg

@@ -188,4 +188,83 @@ __global__ void __launch_bounds__(256) k_lauum(const double* Linv, double* Ainv,
     }
 }
 
+
+// ---------------------------------------------------------------- triangular solves
+// The coarsest solve by forward and back substitution with the Cholesky factor (L y = r,
+// L^T x = y), the textbook alternative to the explicit inverse.  A substitution is a chain of
+// dependent 32-row blocks, so it runs in ONE CTA (1024 threads) with the solution vector in
+// shared memory (n * sizeof(T) bytes of dynamic shared memory): per block, the warps form the
+// rows' dot products with the solved part (coalesced along rows of L), then warp 0 solves the
+// 32 x 32 diagonal block.  L: row-major, leading dimension ld, lower triangle.
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_trsv_lower(const T* __restrict__ L, int64_t ld, const T* __restrict__ r,
+                                                     int n, T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char trsv_smem[];
+  T* ys = reinterpret_cast<T*>(trsv_smem);
+  __shared__ T blk[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int nb = min(32, n - k0);
+    for (int i = warp; i < nb; i += NW) {          // s_i = r_i - L[i, 0:k0] y[0:k0]
+      const T* Lr = L + (int64_t)(k0 + i) * ld;
+      T s = T(0);
+      for (int j = lane; j < k0; j += 32) s += Lr[j] * ys[j];
+      s = warp_allsum(s);
+      if (lane == 0) blk[i] = r[k0 + i] - s;
+    }
+    __syncthreads();
+    if (warp == 0) {                               // the diagonal block, column by column
+      T v = lane < nb ? blk[lane] : T(0);
+      for (int i = 0; i < nb; ++i) {
+        const T yi = __shfl_sync(0xffffffffu, v, i) / L[(int64_t)(k0 + i) * ld + k0 + i];
+        if (lane == i) v = yi;
+        else if (lane > i && lane < nb) v -= L[(int64_t)(k0 + lane) * ld + k0 + i] * yi;
+      }
+      if (lane < nb) ys[k0 + lane] = v;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = ys[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_trsv_lower_t(const T* __restrict__ L, int64_t ld, const T* __restrict__ y,
+                                                       int n, T* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char trsv_smem[];
+  T* xs = reinterpret_cast<T*>(trsv_smem);
+  __shared__ T part[32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
+  const int nblk = (n + 31) / 32;
+  for (int kb = nblk - 1; kb >= 0; --kb) {
+    const int k0 = kb * 32, nb = min(32, n - k0), k1 = k0 + nb;
+    // t_c = y_c - sum_{j >= k1} L[j, c] x_j for the block's columns c = k0 + lane:
+    // rows j split over the warps, each warp reads 32 consecutive entries of a row
+    T s = T(0);
+    if (lane < nb)
+      for (int j = k1 + warp; j < n; j += NW) s += L[(int64_t)j * ld + k0 + lane] * xs[j];
+    if (warp < 32) part[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+      T t = T(0);
+      for (int w = 0; w < min(NW, 32); ++w) t += part[w][lane];
+      T v = lane < nb ? y[k0 + lane] - t : T(0);
+      for (int i = nb - 1; i >= 0; --i) {       // the diagonal block, bottom row first
+        const T xi = __shfl_sync(0xffffffffu, v, i) / L[(int64_t)(k0 + i) * ld + k0 + i];
+        if (lane == i) v = xi;
+        else if (lane < i) v -= L[(int64_t)(k0 + i) * ld + k0 + lane] * xi;
+      }
+      if (lane < nb) xs[k0 + lane] = v;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xs[i];
+}
+
 }  // namespace r3mg

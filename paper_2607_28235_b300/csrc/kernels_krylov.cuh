@@ -7,8 +7,16 @@
 namespace r3mg {
 
 enum Scal : int {
-  S_PQ = 0, S_RR, S_RZ, S_RZNEW, S_ZQ, S_PR, S_ALPHA, S_BETA, S_BB, S_TMP, S_COUNT = 16
+  S_PQ = 0, S_RR, S_RZ, S_RZNEW, S_ZQ, S_PR, S_ALPHA, S_BETA, S_BB, S_TMP,
+  S_NA, S_NB,        // counts of recorded alphas / betas (condition estimate)
+  S_THR,             // block solves: per-column stop threshold on ||r||^2
+  S_COUNT = 16
 };
+// CG coefficients kept per solve for the condition estimate (the Lanczos tridiagonal of the
+// iteration, Section 6's "condition number estimated by PCG"): the first kHist alphas and betas.
+constexpr int kHist = 1024;
+// single-vector scalar array: S_COUNT slots, then the alpha history, then the beta history
+constexpr int kScalTotal = S_COUNT + 2 * kHist;
 enum Fin : int { FIN_NONE = 0, FIN_ALPHA_PCG, FIN_ALPHA_FCG, FIN_BETA_PCG, FIN_BETA_FCG };
 
 constexpr int kVecBlocks = 148 * 4;   // grid of the vector kernels (4 CTAs per SM)
@@ -17,13 +25,13 @@ constexpr int kVecThreads = 256;
 template <typename S, typename D>
 __global__ void k_gather_perm(const S* __restrict__ src, const int64_t* __restrict__ perm, D* __restrict__ dst, int64_t n) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    dst[k] = (D)src[perm[k]];
+    dst[k] = (D)src[perm ? perm[k] : k];   // null perm: identity (coarse-level numbering)
 }
 
 template <typename S, typename D>
 __global__ void k_scatter_perm(const S* __restrict__ src, const int64_t* __restrict__ perm, D* __restrict__ dst, int64_t n) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    dst[perm[k]] = (D)src[k];
+    dst[perm ? perm[k] : k] = (D)src[k];
 }
 
 __device__ __forceinline__ void store_partial(double v, double* part) {
@@ -123,15 +131,25 @@ __global__ void k_reduce(const double* __restrict__ part, int m, double* scal, i
     double t = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
     scal[slot] = t;
+    // alpha and beta of every iteration also go to the history (the flexible-CG beta with its
+    // sign flipped: with a fixed SPD preconditioner it is minus the PCG beta)
     if (fin == FIN_ALPHA_PCG || fin == FIN_ALPHA_FCG) {
       const double num = (fin == FIN_ALPHA_PCG) ? scal[S_RZ] : scal[S_PR];
       if (!(t > 0.0) || !isfinite(num)) { if (status) atomicExch(status, 1); scal[S_ALPHA] = 0.0; }
-      else scal[S_ALPHA] = num / t;
-    } else if (fin == FIN_BETA_PCG) {
-      scal[S_BETA] = t / scal[S_RZ];
-      scal[S_RZ] = t;
-    } else if (fin == FIN_BETA_FCG) {
-      scal[S_BETA] = t / scal[S_PQ];
+      else {
+        const double a = num / t;
+        scal[S_ALPHA] = a;
+        const int ia = (int)scal[S_NA];
+        if (ia < kHist) scal[S_COUNT + ia] = a;
+        scal[S_NA] = (double)(ia + 1);
+      }
+    } else if (fin == FIN_BETA_PCG || fin == FIN_BETA_FCG) {
+      const double be = (fin == FIN_BETA_PCG) ? t / scal[S_RZ] : t / scal[S_PQ];
+      scal[S_BETA] = be;
+      if (fin == FIN_BETA_PCG) scal[S_RZ] = t;
+      const int ib = (int)scal[S_NB];
+      if (ib < kHist) scal[S_COUNT + kHist + ib] = (fin == FIN_BETA_PCG) ? be : -be;
+      scal[S_NB] = (double)(ib + 1);
     }
   }
 }
@@ -168,11 +186,11 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
     y[k] += a * x[k];
 }
 
-// Loop state of the single-problem solve graph: lp[0] = rtol^2 ||b||^2, lp[1] = iteration budget.
+// Loop state of the single-problem solve graph: lp[0] = threshold on ||r||^2, lp[1] = iteration budget.
 __global__ void k_loop_init(double* __restrict__ lp, int* __restrict__ its, int* __restrict__ status,
-                            double rtol2bb, int budget) {
+                            double thr2, int budget) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    lp[0] = rtol2bb;
+    lp[0] = thr2;
     lp[1] = (double)budget;
     *its = 0;
     *status = 0;
@@ -180,7 +198,7 @@ __global__ void k_loop_init(double* __restrict__ lp, int* __restrict__ its, int*
 }
 
 // Device-side stop test after the x/r update of one iteration: count it, then continue the loop
-// (and run this iteration's V-cycle and direction update) only while ||r||^2 > rtol^2 ||b||^2,
+// (and run this iteration's V-cycle and direction update) only while ||r||^2 > the threshold,
 // the budget is not spent and no breakdown was flagged.
 __global__ void k_converge1(const double* __restrict__ scal, const double* __restrict__ lp, int* __restrict__ its,
                             const int* __restrict__ status, cudaGraphConditionalHandle loop,

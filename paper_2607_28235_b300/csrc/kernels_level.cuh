@@ -78,6 +78,9 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* base, int64_t begin
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <int G, typename T>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
@@ -212,7 +215,11 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
         k0 = L.row_ptr[row];
         k1 = L.row_ptr[row + 1];
       }
-      T s = T(0);
+      // FP64: two accumulators (even and odd steps), each a chain of fused multiply-adds, so one
+      // FP64-pipe instruction per stored entry (the FP64 pipe, not HBM, bounds the FP64 form; a
+      // product tree adds a multiply and an add per four entries).  FP32: a short product tree
+      // per step of four entries (shorter dependent chains; the FP32 pipes have room to spare).
+      T sacc[2] = {T(0), T(0)};
       // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
       for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G * U) {
         T v[U][4];
@@ -230,10 +237,18 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
           }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          s += v[u][0] * win[ii[u][0]] + v[u][1] * win[ii[u][1]] + v[u][2] * win[ii[u][2]] + v[u][3] * win[ii[u][3]];
+        for (int u = 0; u < U; ++u) {
+          T& a = sacc[u & 1];
+          if constexpr (sizeof(T) == 8) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a = fma_rn(v[u][j], win[ii[u][j]], a);
+          } else {
+            a += v[u][0] * win[ii[u][0]] + v[u][1] * win[ii[u][1]] + v[u][2] * win[ii[u][2]] +
+                 v[u][3] * win[ii[u][3]];
+          }
+        }
       }
-      s = group_sum<G>(s);
+      T s = group_sum<G>(sacc[0] + sacc[1]);
       if (ok && lane == 0) ep.post(row, (int)(row - r0), s, auxp, acc);
     }
   };

@@ -9,7 +9,8 @@
 // neighbour boxes) and of the item's own-row vector entries the epilogue needs.  The HBM
 // stream therefore never waits on register-held loads: the copy engine keeps a whole item
 // (tens of KB per SM) in flight.  Every mbarrier wait is bounded (about one second of
-// clock64 cycles); on expiry the kernel raises an error flag and returns.
+// clock64 cycles by default); on expiry the kernel raises an error flag, waits (bounded again)
+// for the bulk copies it still has in flight and for its cp.async copies, and returns.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -48,6 +49,9 @@ struct TmaView {
   int max_item_rows = 0;                // rows per item at most
   int desc_max = 0;                     // largest descriptor in bytes (multiple of 16)
   int* err = nullptr;                   // set to 1 when a bounded wait expires
+  long long wait_cycles = kWaitCycles;  // limit of every mbarrier wait
+  int withhold_first = 0;               // test of the expiry path: CTA 0 announces its first
+                                        // descriptor copy but never issues it, so that wait runs out
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -70,13 +74,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: true on completion, false (and err raised) after ~kWaitCycles
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+// bounded wait: true on completion, false (and err raised when err is given) after `limit` cycles
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
-      atomicExch(err, 1);
+    if (clock64() - t0 > limit) {
+      if (err) atomicExch(err, 1);
       return false;
     }
   }
@@ -128,12 +133,26 @@ __global__ void __launch_bounds__(1024, 1) level_kernel_tma(TmaView<T> V, const 
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
+  // thread 0 tracks the barriers (0-1 stages, 2-4 descriptor ring) with a phase in flight and
+  // the parity of that phase, so that an expired wait can drain every copy it issued
+  uint32_t pend = 0, par = 0;
+  auto issued = [&](int j) { pend |= 1u << j; };
+  auto completed = [&](int j) { pend &= ~(1u << j); par ^= 1u << j; };
+  auto drain = [&]() {   // after an expired wait: no CTA leaves with a copy into its shared memory in flight
+    if (tid == 0)
+      for (int j = 0; j < 5; ++j)
+        if ((pend >> j) & 1u) mbar_wait_bounded(&bar[j], (par >> j) & 1u, nullptr, kWaitCycles);
+    cp_async_wait_all();
+  };
 
+  bool withheld = false;
   auto fetch_desc = [&](int64_t it, int j) {   // thread 0 only
     const int64_t o = V.desc_off[it];
     const uint32_t bytes = (uint32_t)(V.desc_off[it + 1] - o);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_expect_tx(&dbar[j], bytes);
+    issued(2 + j);
+    if (V.withhold_first && blockIdx.x == 0 && !withheld) { withheld = true; return; }
     bulk_g2s(tsm + lay.dsc[j], V.desc + o, bytes, &dbar[j]);
   };
 
@@ -152,6 +171,7 @@ __global__ void __launch_bounds__(1024, 1) level_kernel_tma(TmaView<T> V, const 
         bi = (uint32_t)((((e1 - ia) * 2) + 15) & ~(int64_t)15);
       }
       mbar_expect_tx(&bar[st], bv + bi);
+      issued(st);
       bulk_g2s(tsm + lay.vals[st], L.vals + e0, bv, &bar[st]);
       if (FINE) bulk_g2s(tsm + lay.idx[st], L.idx + ia, bi, &bar[st]);
     }
@@ -182,8 +202,9 @@ __global__ void __launch_bounds__(1024, 1) level_kernel_tma(TmaView<T> V, const 
       fetch_desc(it0, 0);
       if (it0 + G0 < V.nitems) fetch_desc(it0 + G0, 1);
     }
-    alive = mbar_wait_bounded(&dbar[0], 0, V.err);
-    if (__syncthreads_or(!alive)) return;
+    alive = mbar_wait_bounded(&dbar[0], 0, V.err, V.wait_cycles);
+    if (__syncthreads_or(!alive)) { drain(); return; }
+    completed(2);
     issue(tsm + lay.dsc[0], 0);
   } else {
     cp_async_commit();
@@ -195,15 +216,17 @@ __global__ void __launch_bounds__(1024, 1) level_kernel_tma(TmaView<T> V, const 
     if (tid == 0 && nxt2 < V.nitems) fetch_desc(nxt2, (k + 2) % 3);
     if (nxt < V.nitems) {
       const int j = (k + 1) % 3;
-      alive = mbar_wait_bounded(&dbar[j], (uint32_t)(((k + 1) / 3) & 1), V.err);
-      if (__syncthreads_or(!alive)) return;
+      alive = mbar_wait_bounded(&dbar[j], (uint32_t)(((k + 1) / 3) & 1), V.err, V.wait_cycles);
+      if (__syncthreads_or(!alive)) { drain(); return; }
+      completed(2 + j);
       issue(tsm + lay.dsc[j], st ^ 1);
     } else {
       cp_async_commit();
     }
     cp_async_wait_1();
-    alive = mbar_wait_bounded(&bar[st], (uint32_t)((k >> 1) & 1), V.err);
-    if (__syncthreads_or(!alive)) return;   // error flag raised; nothing is consumed
+    alive = mbar_wait_bounded(&bar[st], (uint32_t)((k >> 1) & 1), V.err, V.wait_cycles);
+    if (__syncthreads_or(!alive)) { drain(); return; }   // error flag raised; nothing is consumed
+    completed(st);
     const unsigned char* dsc = tsm + lay.dsc[k % 3];
     const ItemDesc* hd = reinterpret_cast<const ItemDesc*>(dsc);
     const int64_t e0 = hd->e0, rb = hd->rb;
@@ -220,7 +243,7 @@ __global__ void __launch_bounds__(1024, 1) level_kernel_tma(TmaView<T> V, const 
       const bool ok = lr < nr;
       int k0 = 0, k1 = 0;
       if (ok) { k0 = roff[lr]; k1 = roff[lr + 1]; }
-      T s = T(0);
+      T s = T(0);   // FP64: one fused multiply-add per stored entry (see the register kernel)
       for (int kk = k0 + 4 * lane; kk < k1; kk += 4 * G) {
         T v[4];
         if constexpr (sizeof(T) == 4) {
@@ -231,13 +254,20 @@ __global__ void __launch_bounds__(1024, 1) level_kernel_tma(TmaView<T> V, const 
           const double2 c = *reinterpret_cast<const double2*>(vb + kk + 2);
           v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
         }
+        int wi[4];
         if constexpr (FINE) {
           const uint2 q = *reinterpret_cast<const uint2*>(ib + kk);
-          s += v[0] * win[q.x & 0xffff] + v[1] * win[q.x >> 16] + v[2] * win[q.y & 0xffff] + v[3] * win[q.y >> 16];
+          wi[0] = q.x & 0xffff; wi[1] = q.x >> 16; wi[2] = q.y & 0xffff; wi[3] = q.y >> 16;
         } else {
           // coarse rows: dense blocks laid out over the window in slot order
           const int t = kk - k0;
-          s += v[0] * win[t] + v[1] * win[t + 1] + v[2] * win[t + 2] + v[3] * win[t + 3];
+          wi[0] = t; wi[1] = t + 1; wi[2] = t + 2; wi[3] = t + 3;
+        }
+        if constexpr (sizeof(T) == 8) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) s = fma_rn(v[j], win[wi[j]], s);
+        } else {
+          s += v[0] * win[wi[0]] + v[1] * win[wi[1]] + v[2] * win[wi[2]] + v[3] * win[wi[3]];
         }
       }
       s = group_sum<G>(s);

@@ -300,7 +300,7 @@ inline size_t mr_coarse_smem(const LevelView<T>& L) {   // staged window, later 
 // of two shared-memory buffers (cp.async.bulk, mbarrier completion) while the previous chunk is
 // computed, and the box's window of X is staged once per box (16-byte cp.async).  Every operand
 // of the inner loop then comes from shared memory.  Every mbarrier wait is bounded: on expiry
-// the kernel raises *err and all threads leave.
+// the kernel raises *err, waits (bounded) for its copies still in flight, and all threads leave.
 struct MrStreamLayout {
   size_t xs = 0, vals0 = 0, vals1 = 0, red = 0, bar = 0, total = 0;
   int RC = 0;
@@ -376,8 +376,12 @@ __global__ void __launch_bounds__(256) k_mr_coarse_stream(LevelView<T> L, const 
     if (tid == 0 && k + 1 < nitems) issue(k + 1);
     const bool alive = mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), err);
     if (__syncthreads_or(!alive)) {
-      // leave only after the copy issued for the next item has landed (bounded as well)
-      if (tid == 0 && k + 1 < nitems) mbar_wait_bounded(&bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), err);
+      // leave only after the copies still in flight have landed (bounded as well): this item's,
+      // whose wait ran out, and the one issued for the next item
+      if (tid == 0) {
+        mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), nullptr);
+        if (k + 1 < nitems) mbar_wait_bounded(&bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), nullptr);
+      }
       return;
     }
     const T* vb = reinterpret_cast<const T*>(smem_raw + ((k & 1) ? lay.vals1 : lay.vals0));
@@ -884,22 +888,43 @@ __global__ void k_mr_reduce(const double* __restrict__ part, int nb, double* msc
   if (l != 0) return;
   mscal[slot * M + c] = s;
   const bool act = active == nullptr || active[c] != 0;
+  // per-column coefficient history after the S_COUNT x M slots: column c owns 2 x kHist
+  // doubles (alphas, then betas; flexible-CG betas sign-flipped to their PCG equivalent)
+  double* hist = mscal + S_COUNT * M + (int64_t)c * 2 * kHist;
   if (fin == FIN_ALPHA_PCG || fin == FIN_ALPHA_FCG) {
     const double num = (fin == FIN_ALPHA_PCG) ? mscal[S_RZ * M + c] : mscal[S_PR * M + c];
     if (!act) mscal[S_ALPHA * M + c] = 0.0;
     else if (!(s > 0.0) || !isfinite(num)) { if (status) atomicExch(status, 1); mscal[S_ALPHA * M + c] = 0.0; }
-    else mscal[S_ALPHA * M + c] = num / s;
-  } else if (fin == FIN_BETA_PCG) {
-    mscal[S_BETA * M + c] = act ? s / mscal[S_RZ * M + c] : 0.0;
-    if (act) mscal[S_RZ * M + c] = s;
-  } else if (fin == FIN_BETA_FCG) {
-    mscal[S_BETA * M + c] = act ? s / mscal[S_PQ * M + c] : 0.0;
+    else {
+      const double a = num / s;
+      mscal[S_ALPHA * M + c] = a;
+      const int ia = (int)mscal[S_NA * M + c];
+      if (ia < kHist) hist[ia] = a;
+      mscal[S_NA * M + c] = (double)(ia + 1);
+    }
+  } else if (fin == FIN_BETA_PCG || fin == FIN_BETA_FCG) {
+    const double be = act ? s / mscal[(fin == FIN_BETA_PCG ? S_RZ : S_PQ) * M + c] : 0.0;
+    mscal[S_BETA * M + c] = be;
+    if (act) {
+      if (fin == FIN_BETA_PCG) mscal[S_RZ * M + c] = s;
+      const int ib = (int)mscal[S_NB * M + c];
+      if (ib < kHist) hist[kHist + ib] = (fin == FIN_BETA_PCG) ? be : -be;
+      mscal[S_NB * M + c] = (double)(ib + 1);
+    }
   }
 }
 
+// Restart of the active columns' coefficient histories (a restarted column begins a new
+// Lanczos sequence).  One warp.
+template <int M>
+__global__ void k_mr_hist_reset(double* mscal, const int* __restrict__ active) {
+  const int c = threadIdx.x;
+  if (c < M && active[c]) { mscal[S_NA * M + c] = 0.0; mscal[S_NB * M + c] = 0.0; }
+}
+
 // Device-side stop test after the X/R update: count the update of every active column, retire
-// columns with ||r_c||^2 <= rtol^2 ||b_c||^2 or a spent budget, continue while any is active.
-// lp[0] = rtol^2, lp[1] = iteration budget per column.  One warp.  Inside the loop graph
+// columns with ||r_c||^2 <= their threshold or a spent budget, continue while any is active.
+// mscal[S_THR][c] = the column's threshold on ||r_c||^2, lp[1] = iteration budget per column.  One warp.  Inside the loop graph
 // (in_graph = 1) the decision sets the loop's conditions, else it goes to *go_out.
 template <int M>
 __global__ void k_mr_converge(const double* __restrict__ mscal, const double* __restrict__ lp, int* __restrict__ its,
@@ -912,7 +937,7 @@ __global__ void k_mr_converge(const double* __restrict__ mscal, const double* __
     its[c] = k;
     const double rr = mscal[S_RR * M + c];
     if (!isfinite(rr)) atomicExch(status, 1);
-    const bool done = !(rr > lp[0] * mscal[S_BB * M + c]) || (double)k >= lp[1];
+    const bool done = !(rr > mscal[S_THR * M + c]) || (double)k >= lp[1];
     if (done) active[c] = 0;
     go = !done;
   }

@@ -27,6 +27,12 @@ using namespace r3mg;
 namespace {
 
 thread_local std::string g_last_error = "no error";
+
+// Scratch of r3mg_level0_apply_noalloc: the caller-numbered input and output permuted into
+// tree order.  It lives in the library image, so every GPU that loads the library holds it
+// (16 MiB) until the process exits; no call ever allocates it.
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 20;
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxN];
 constexpr size_t kMaxSmem = 226 * 1024;   // opt-in shared memory per CTA on sm_103a, minus static use
 
 struct Level {
@@ -168,6 +174,22 @@ struct r3mg_hierarchy {
   int nsm = 148;
   int tma_ctas = 1;                   // TMA kernel CTAs per SM
   int64_t graph_kernels = 0;          // kernels in one replay of the V-cycle graph
+  // stop test: ||r|| <= max(rtol ||b||, stop_atol, stop_red ||r_0||)  (r3mg_set_stop_rule)
+  double stop_atol = 0.0, stop_red = 0.0;
+  // mesh statistics of the paper's tables: h = largest distance between two coupled support
+  // points, H = largest diameter of a coarsest-level box
+  double h_fine = 0.0, H_coarse = 0.0;
+  std::vector<double> ritz;           // per smoothed level: the Lanczos Ritz value (before the safety factor)
+  int mr_last_m = 0;                  // columns of the last block solve (condition estimates)
+  double* noalloc_scratch = nullptr;  // device address of the allocation-free product's static scratch
+  // coarsest solve: 0 = explicit inverse (one GEMV), 1 = forward and back substitution with the
+  // Cholesky factor (r3mg_set_coarse_mode); the factor is kept for single hierarchies
+  int coarse_mode = 0;
+  double* L64 = nullptr;
+  float* L32 = nullptr;
+  double* ctmp = nullptr;             // the forward substitution's result (nc values, either precision)
+  long long wait_cycles = 0;          // limit of the streamed kernels' mbarrier waits (0 = about 1 s)
+  int withhold_first = 0;             // expiry-path test: withhold CTA 0's first descriptor copy
 };
 
 namespace {
@@ -345,12 +367,20 @@ void prof_harvest(r3mg_hierarchy* h) {
   h->pending.clear();
 }
 
+// Bounded-wait control of the copy-engine-streamed kernels: the expiry flag, the wait limit and
+// the expiry-path test switch (r3mg_set_wait_limit).
+struct TmaCtl {
+  int* err;
+  long long wait;
+  int withhold;
+};
+
 template <typename T, int G, bool FINE, class Ep>
-void launch_tma_g(const Level& A, const Level::Items& it, const T* xin, Ep ep, double* part, cudaStream_t s, int* err) {
+void launch_tma_g(const Level& A, const Level::Items& it, const T* xin, Ep ep, double* part, cudaStream_t s, TmaCtl ctl) {
   TmaView<T> v;
   v.L = view<T>(A);
   v.desc = it.desc; v.desc_off = it.desc_off; v.nitems = it.nitems; v.stage_entries = it.SE; v.max_item_rows = it.rmax;
-  v.desc_max = it.dmax; v.err = err;
+  v.desc_max = it.dmax; v.err = ctl.err; v.wait_cycles = ctl.wait; v.withhold_first = ctl.withhold;
   auto kern = level_kernel_tma<T, G, FINE, Ep>;
   ensure_smem((const void*)kern, it.smem);
   kern<<<it.grid, A.conf[sizeof(T) == 4 ? 1 : 0].nt, it.smem, s>>>(v, xin, ep, part);
@@ -358,7 +388,7 @@ void launch_tma_g(const Level& A, const Level::Items& it, const T* xin, Ep ep, d
 }
 
 template <typename T, class Ep>
-void launch_tma(const Level& A, const T* xin, Ep ep, double* part, cudaStream_t s, int* err) {
+void launch_tma(const Level& A, const T* xin, Ep ep, double* part, cudaStream_t s, TmaCtl err) {
   const Level::Items& it = A.tma[sizeof(T) == 4 ? 1 : 0];
   const bool fine = (A.b == 0);
   switch (A.conf[sizeof(T) == 4 ? 1 : 0].G) {
@@ -367,6 +397,10 @@ void launch_tma(const Level& A, const T* xin, Ep ep, double* part, cudaStream_t 
     case 16: fine ? launch_tma_g<T, 16, true>(A, it, xin, ep, part, s, err) : launch_tma_g<T, 16, false>(A, it, xin, ep, part, s, err); break;
     default: fine ? launch_tma_g<T, 32, true>(A, it, xin, ep, part, s, err) : launch_tma_g<T, 32, false>(A, it, xin, ep, part, s, err); break;
   }
+}
+
+TmaCtl tma_ctl(const r3mg_hierarchy* h) {
+  return TmaCtl{h->tma_err, h->wait_cycles > 0 ? h->wait_cycles : kWaitCycles, h->withhold_first};
 }
 
 // Product y = A x (+ partial w . y) on either kernel form; partial count = grid of the kernel.
@@ -379,7 +413,7 @@ bool tma_on(const Level& A) {
 template <typename T>
 int level_apply_dot(r3mg_hierarchy* h, const Level& A, const T* x, T* y, const T* w, double* part) {
   if (tma_on<T>(A)) {
-    launch_tma<T>(A, x, TEpApplyDot<T>{y, w}, part, h->stream, h->tma_err);
+    launch_tma<T>(A, x, TEpApplyDot<T>{y, w}, part, h->stream, tma_ctl(h));
     return A.tma[sizeof(T) == 4 ? 1 : 0].grid;
   }
   return launch_level<T>(A, x, TEpApplyDot<T>{y, w}, part, h->stream);
@@ -393,7 +427,7 @@ void level_cheb(r3mg_hierarchy* h, const Level& A, T* x, T* r, T* d, T* dn, cons
       return;
     }
   }
-  if (tma_on<T>(A)) launch_tma<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream, h->tma_err);
+  if (tma_on<T>(A)) launch_tma<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream, tma_ctl(h));
   else launch_level<T>(A, d, TEpCheb<T>{x, r, d, dn, dinv, a, c}, nullptr, h->stream);
 }
 
@@ -587,6 +621,28 @@ const T* Ainv(r3mg_hierarchy* h) {
   if constexpr (sizeof(T) == 8) return (const T*)h->Ainv64; else return (const T*)h->Ainv32;
 }
 template <typename T>
+const T* Lfac(r3mg_hierarchy* h) {
+  if constexpr (sizeof(T) == 8) return (const T*)h->L64; else return (const T*)h->L32;
+}
+
+// The coarsest solve x = A_c^{-1} r in the configured form: one GEMV with the explicit inverse,
+// or forward and back substitution with the Cholesky factor (one CTA each).  Returns launches.
+template <typename T>
+int coarsest_apply(r3mg_hierarchy* h, const T* r, T* x) {
+  cudaStream_t s = h->stream;
+  if (h->coarse_mode == 1) {
+    const size_t sm = sizeof(T) * (size_t)h->nc;
+    k_trsv_lower<T><<<1, 1024, sm, s>>>(Lfac<T>(h), h->ncp, r, (int)h->nc, (T*)h->ctmp);
+    k_trsv_lower_t<T><<<1, 1024, sm, s>>>(Lfac<T>(h), h->ncp, (const T*)h->ctmp, (int)h->nc, x);
+    CK(cudaGetLastError());
+    return 2;
+  }
+  k_dense_gemv<T><<<grid_for(h->nc * 32), 256, 0, s>>>(Ainv<T>(h), h->ncp, r, h->nc, x);
+  CK(cudaGetLastError());
+  return 1;
+}
+
+template <typename T>
 const T* Dinv(const Level& L) {
   if constexpr (sizeof(T) == 8) return (const T*)L.dinv64; else return (const T*)L.dinv32;
 }
@@ -628,9 +684,7 @@ T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
   }
   {
     Level& C = h->lv[L - 1];
-    k_dense_gemv<T><<<grid_for(h->nc * 32), 256, 0, s>>>(Ainv<T>(h), h->ncp, (const T*)C.r, h->nc, (T*)C.x);
-    CK(cudaGetLastError());
-    ++nk;
+    nk += coarsest_apply<T>(h, (const T*)C.r, (T*)C.x);
   }
   for (int l = L - 2; l >= 0; --l) {
     Level& A = h->lv[l];
@@ -745,6 +799,8 @@ void lanczos(r3mg_hierarchy* h, int l) {
   }
   const double lmax = tridiag_max_eig(dg, off);
   if (!(lmax > 0.0) || !std::isfinite(lmax)) throw Fail{R3MG_E_NOT_SPD, "Lanczos estimate non-positive on level " + std::to_string(l)};
+  if ((int)h->ritz.size() < h->L) h->ritz.resize(h->L, 0.0);
+  h->ritz[l] = lmax;
   A.lam_hi = h->prm.eig_safety * lmax;
   A.lam_lo = A.lam_hi / h->prm.eig_ratio;
   make_schedule(A, h->prm.cheb_degree, h->prm.sweeps);
@@ -752,7 +808,8 @@ void lanczos(r3mg_hierarchy* h, int l) {
 
 // Dense Cholesky, triangular inverse and symmetric inverse of the boxes [B0, B0 + nbox) of the
 // coarsest block level, written to out (ncp x ncp, leading dimension ncp, identity padding).
-void dense_block(r3mg_hierarchy* h, Level& C, int64_t B0, int64_t nbox, double* out, int64_t ncp) {
+void dense_block(r3mg_hierarchy* h, Level& C, int64_t B0, int64_t nbox, double* out, int64_t ncp,
+                 double* keep_factor = nullptr) {
   cudaStream_t s = h->stream;
   const int64_t nc = nbox * h->b;
   const int nb = (int)(ncp / kTile);
@@ -783,6 +840,8 @@ void dense_block(r3mg_hierarchy* h, Level& C, int64_t B0, int64_t nbox, double* 
   }
   k_lauum<<<nb * (nb + 1) / 2, 256, 0, s>>>(Li, out, ncp, nb);
   CK(cudaGetLastError());
+  // the factor itself (lower triangle of D) for the substitution form of the coarsest solve
+  if (keep_factor) CK(cudaMemcpyAsync(keep_factor, D, sizeof(double) * ncp * ncp, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaFree(D)); CK(cudaFree(Li));
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)D), h->allocs.end());
@@ -792,7 +851,8 @@ void dense_block(r3mg_hierarchy* h, Level& C, int64_t B0, int64_t nbox, double* 
 void dense_coarsest(r3mg_hierarchy* h) {
   Level& C = h->lv[h->L - 1];
   if (!h->Ainv64) h->Ainv64 = dalloc<double>(h, h->ncp * h->ncp);
-  dense_block(h, C, 0, C.nbox, h->Ainv64, h->ncp);
+  if (!h->L64) h->L64 = dalloc<double>(h, h->ncp * h->ncp);
+  dense_block(h, C, 0, C.nbox, h->Ainv64, h->ncp, h->L64);
 }
 
 // Autotuner: times one fused level step (or the FP64 product for the fine level of the mixed
@@ -932,6 +992,11 @@ void numeric(r3mg_hierarchy* h, const double* vals_dev) {
     const int64_t na = !h->bl.empty() ? h->batch_ainv_size : h->ncp * h->ncp;
     k_convert<double, float><<<grid_for(na), 256, 0, s>>>(h->Ainv64, h->Ainv32, na);
     CK(cudaGetLastError());
+    if (h->L64) {
+      if (!h->L32) h->L32 = dalloc<float>(h, h->ncp * h->ncp);
+      k_convert<double, float><<<grid_for(h->ncp * h->ncp), 256, 0, s>>>(h->L64, h->L32, h->ncp * h->ncp);
+      CK(cudaGetLastError());
+    }
   }
   CK(cudaStreamSynchronize(s));
 }
@@ -942,6 +1007,7 @@ struct ProbHost {
   HostPartition P;
   std::vector<HostPattern> pats;
   HostFineLayout lay;
+  double hmax = 0.0;   // largest distance between two coupled support points (the mesh size h)
 };
 
 // Cells of a problem for cell-based agglomeration (null: point-based).
@@ -981,6 +1047,7 @@ void analyse_problem(const r3mg_params& prm, int dim, int b, int fan, int64_t n,
   fine_pattern(P, rowptr, colidx, out.pats[1]);
   for (int l = 2; l < L; ++l) coarse_pattern(out.pats[l - 1], fan, P.nbox(l), out.pats[l]);
   if (!fine_layout(P, out.pats[1], rowptr, colidx, out.lay, err)) throw Fail{err.status, err.msg};
+  out.hmax = max_coupled_distance(n, dim, coords, rowptr, colidx);
 }
 
 void batch_levels_upload(r3mg_hierarchy* h);
@@ -1000,6 +1067,16 @@ void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLay
   const int L = prm.levels;
   h->L = L;
   h->lv.assign(L, Level());
+  // H: the largest diameter (MBR diagonal) of a coarsest-level box
+  h->H_coarse = 0.0;
+  for (int64_t B = 0; B < P.nbox(L - 1); ++B) {
+    double s2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      const double e = P.hi[L - 1][B * dim + a] - P.lo[L - 1][B * dim + a];
+      s2 += e * e;
+    }
+    h->H_coarse = std::max(h->H_coarse, std::sqrt(s2));
+  }
   h->nnz_csr = 0;
   for (auto& pc : vals) h->nnz_csr += pc.second;
   // ---- fine level
@@ -1138,8 +1215,8 @@ void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLay
   h->npart = np;
   h->part_a = dalloc<double>(h, np);
   h->part_b = dalloc<double>(h, np);
-  h->scal = dalloc<double>(h, S_COUNT);
-  CK(cudaMemsetAsync(h->scal, 0, sizeof(double) * S_COUNT, s));
+  h->scal = dalloc<double>(h, kScalTotal);
+  CK(cudaMemsetAsync(h->scal, 0, sizeof(double) * kScalTotal, s));
   int64_t nmax = h->n;
   for (int l = 1; l < L; ++l) nmax = std::max(nmax, h->lv[l].n);
   h->cx = dalloc<double>(h, nmax); h->cr = dalloc<double>(h, nmax); h->cp = dalloc<double>(h, nmax);
@@ -1216,6 +1293,7 @@ void build(r3mg_hierarchy* h, const double* coords, const int64_t* rowptr, const
   ProbHost ph;
   analyse_problem(prm, h->dim, h->b, h->fan, h->n, coords, rowptr, colidx, vals, ph, cells);
   h->part = std::move(ph.P);
+  h->h_fine = ph.hmax;
   build_device(h, ph.pats, ph.lay, coords, rowptr, colidx, {{vals, rowptr[h->n]}});
 }
 
@@ -1357,7 +1435,9 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
     if (bb) *bb = reduce_read(h, h->part_b, gv, S_BB);
   };
   auto precondition_restart = [&]() {
-    // z = M r; p = z; (PCG) rz = r.z ; (FCG) pr = p.r
+    // z = M r; p = z; (PCG) rz = r.z ; (FCG) pr = p.r.  A restart begins a new Lanczos
+    // sequence: the coefficient history of the condition estimate starts over.
+    CK(cudaMemsetAsync(h->scal + S_NA, 0, 2 * sizeof(double), s));
     k_vc_init<T><<<gv, 256, 0, s>>>(h->cr, n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), (T)F.c0);
     CK(cudaGetLastError());
     T* d = run_vcycle<T>(h);
@@ -1367,6 +1447,7 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
     CK(cudaMemcpyAsync(h->cp, h->cz, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   };
   double rr = 0.0, bb = 0.0;
+  CK(cudaMemsetAsync(h->scal + S_NA, 0, 2 * sizeof(double), s));   // no coefficients recorded yet
   true_residual(rr, &bb, all_zero(h, h->cx, n));
   const double bnorm = std::sqrt(bb);
   *iters = 0;
@@ -1377,7 +1458,11 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
   }
   double rel = std::sqrt(rr) / bnorm;
   *relres = rel;
-  if (rel <= rtol) return R3MG_OK;
+  // stop when ||r|| <= max(rtol ||b||, atol, reduction ||r_0||); with atol = reduction = 0 (the
+  // default) this is the relative test, with rtol = 0, atol = 1e-9, reduction = 1e-6 Section 6's
+  const double thr = std::max(rtol * bnorm, std::max(h->stop_atol, h->stop_red * std::sqrt(rr)));
+  const double thr2 = thr * thr;
+  if (rr <= thr2) return R3MG_OK;
   precondition_restart();
   if (!h->prof_on && h->lgraph_state >= 0) {
     // The whole iteration loop as one graph launch.  A conditional WHILE node repeats one
@@ -1389,7 +1474,7 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
     if (h->lgraph_state == 1) {
       int done_its = 0;
       while (done_its < maxit) {
-        k_loop_init<<<1, 32, 0, s>>>(h->d_loop, h->d_its, h->status, rtol * rtol * bb, maxit - done_its);
+        k_loop_init<<<1, 32, 0, s>>>(h->d_loop, h->d_its, h->status, thr2, maxit - done_its);
         CK(cudaGetLastError());
         CK(cudaGraphLaunch(h->lgraph, s));
         int its = 0, st = 0;
@@ -1410,7 +1495,7 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
         true_residual(rt, nullptr);
         *relres = std::sqrt(rt) / bnorm;
         if (!std::isfinite(*relres)) throw Fail{R3MG_E_BREAKDOWN, "CG breakdown: non-finite residual"};
-        if (*relres <= rtol) return R3MG_OK;
+        if (rt <= thr2) return R3MG_OK;
         if (done_its >= maxit) break;
         precondition_restart();   // recursive residual drifted: restart from the true residual
       }
@@ -1447,11 +1532,11 @@ r3mg_status krylov(r3mg_hierarchy* h, double rtol, int maxit, int* iters, double
     rel = std::sqrt(rr) / bnorm;
     *relres = rel;
     if (!std::isfinite(rel)) throw Fail{R3MG_E_BREAKDOWN, "CG breakdown: non-finite residual"};
-    if (rel <= rtol) {
+    if (rr <= thr2) {
       double rt = 0.0;
       true_residual(rt, nullptr);
       *relres = std::sqrt(rt) / bnorm;
-      if (*relres <= rtol) return R3MG_OK;
+      if (rt <= thr2) return R3MG_OK;
       precondition_restart();   // recursive residual drifted: restart from the true residual
       continue;
     }
@@ -1651,12 +1736,15 @@ T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing) {
   const int L = h->L;
   std::vector<int> cur(L, 0);
   int64_t nk = 0;
+  h->slot_next = 0;
   for (int l = 0; l < L - 1; ++l) {
     Level& A = h->lv[l];
     T* x = (T*)A.x; T* r = (T*)A.r;
     for (int st = 0; st < h->bl[l].npre; ++st) {
       T* d = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      const int ps = prof_begin(h, 1 + l, capturing);
       level_cheb_b<T>(h, A, l, x, r, d, dn, false, st);
+      prof_end(h, ps, capturing);
       cur[l] ^= 1;
       ++nk;
     }
@@ -1694,12 +1782,14 @@ T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing) {
     T* x = (T*)A.x; T* r = (T*)A.r;
     for (int st = 0; st < h->bl[l].npost; ++st) {
       T* dd = (T*)A.d[cur[l]]; T* dn = (T*)A.d[cur[l] ^ 1];
+      const int ps = prof_begin(h, 1 + l, capturing);
       level_cheb_b<T>(h, A, l, x, r, dd, dn, true, st);
+      prof_end(h, ps, capturing);
       cur[l] ^= 1;
       ++nk;
     }
   }
-  if (!capturing) h->launches += nk;
+  if (capturing) h->graph_kernels = nk; else h->launches += nk;
   return (T*)h->lv[0].d[cur[0]];
 }
 
@@ -1857,6 +1947,7 @@ void build_batch(r3mg_hierarchy* h, int np, const int64_t* n, const double* cons
   }
   const int64_t N = row0[np];
   h->n = N;
+  for (int k = 0; k < np; ++k) h->h_fine = std::max(h->h_fine, ph[k].hmax);
   // combined partition: every problem's boxes, in problem order
   HostPartition& P = h->part;
   P.n = N; P.dim = dim; P.levels = L; P.depth = 0;
@@ -1970,15 +2061,15 @@ void mr_alloc(r3mg_hierarchy* h, int M) {
   const int64_t nm = h->n * M;
   h->mr_b = dalloc<double>(h, nm); h->mr_xc = dalloc<double>(h, nm); h->mr_rc = dalloc<double>(h, nm);
   h->mr_p = dalloc<double>(h, nm); h->mr_q = dalloc<double>(h, nm); h->mr_z = dalloc<double>(h, nm);
-  h->mr_scal = dalloc<double>(h, (int64_t)S_COUNT * M);
-  CK(cudaMemsetAsync(h->mr_scal, 0, sizeof(double) * S_COUNT * M, h->stream));
+  h->mr_scal = dalloc<double>(h, (int64_t)(S_COUNT + 2 * kHist) * M);   // slots, then per-column histories
+  CK(cudaMemsetAsync(h->mr_scal, 0, sizeof(double) * (S_COUNT + 2 * kHist) * M, h->stream));
   h->mr_npart = std::max<int64_t>(grid_for(nm), (int64_t)h->nsm * 8);
   h->mr_pa = dalloc<double>(h, h->mr_npart * M);
   h->mr_pb = dalloc<double>(h, h->mr_npart * M);
   h->mr_lp = dalloc<double>(h, 2);
   h->mr_its = dalloc<int>(h, M + 1);   // + the host-driven loop's continue flag
   h->mr_active = dalloc<int>(h, M);
-  if (!h->mr_host) CK(cudaMallocHost(&h->mr_host, sizeof(double) * 64));
+  if (!h->mr_host) CK(cudaMallocHost(&h->mr_host, sizeof(double) * 128));
   h->mr_M = M;
 }
 
@@ -2426,21 +2517,30 @@ r3mg_status mr_krylov(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its
     h->launches += with_bb ? 4 : 3;
   };
   auto restart = [&]() {   // z = M r; p = z; per column rz (PCG) or pr (FCG)
+    k_mr_hist_reset<M><<<1, 32, 0, s>>>(h->mr_scal, h->mr_active);   // new Lanczos sequences
     mr_vcycle_apply<T, M>(h, h->mr_rc, h->mr_z);
     mr_reduce<M>(h, h->mr_pa, gv, fcg ? S_PR : S_RZ, FIN_NONE);
     CK(cudaMemcpyAsync(h->mr_p, h->mr_z, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
     h->launches += 3;
   };
+  h->mr_last_m = m;
+  CK(cudaMemsetAsync(h->mr_scal + S_NA * M, 0, 2 * M * sizeof(double), s));   // no coefficients yet
   true_residual(true, all_zero(h, h->mr_xc, nm));
-  std::vector<double> bb(M), rel(M, 0.0);
+  std::vector<double> bb(M), rel(M, 0.0), thr2(M, 0.0);
   std::vector<int> its(M, 0), act(M, 0);
   unsigned zero_mask = 0;
+  double* hthr = hs + 64;   // pinned: the per-column thresholds uploaded to mscal[S_THR]
   for (int c = 0; c < M; ++c) {
     bb[c] = hs[16 + c];
     if (c < m && bb[c] == 0.0) zero_mask |= 1u << c;
     rel[c] = (bb[c] > 0.0) ? std::sqrt(hs[c] / bb[c]) : 0.0;
-    act[c] = (c < m && bb[c] > 0.0 && !(rel[c] <= rtol) && maxit > 0) ? 1 : 0;
+    // ||r_c|| <= max(rtol ||b_c||, atol, reduction ||r_c,0||), as in the single-vector solve
+    const double t = std::max(rtol * std::sqrt(bb[c]), std::max(h->stop_atol, h->stop_red * std::sqrt(hs[c])));
+    thr2[c] = t * t;
+    hthr[c] = thr2[c];
+    act[c] = (c < m && bb[c] > 0.0 && !(hs[c] <= thr2[c]) && maxit > 0) ? 1 : 0;
   }
+  CK(cudaMemcpyAsync(h->mr_scal + S_THR * M, hthr, sizeof(double) * M, cudaMemcpyHostToDevice, s));
   if (zero_mask) {
     k_mr_zero_cols<<<gv, 256, 0, s>>>(h->mr_xc, nm, M, zero_mask);
     CK(cudaGetLastError());
@@ -2451,7 +2551,8 @@ r3mg_status mr_krylov(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its
     CK(cudaMemcpyAsync(h->mr_active, hi + 16, sizeof(int) * M, cudaMemcpyHostToDevice, s));
   };
   bool any = false;
-  for (int c = 0; c < M; ++c) any = any || act[c];
+  std::vector<char> conv_c(M, 0);
+  for (int c = 0; c < M; ++c) { any = any || act[c]; conv_c[c] = (c < m && !act[c] && hs[c] <= thr2[c]); }
   if (any) {
     upload_active();
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
@@ -2516,7 +2617,8 @@ r3mg_status mr_krylov(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its
         if (c >= m || bb[c] == 0.0) { act[c] = 0; continue; }
         rel[c] = std::sqrt(hs[c] / bb[c]);
         if (!std::isfinite(rel[c])) throw Fail{R3MG_E_BREAKDOWN, "pcg_multi: non-finite residual"};
-        act[c] = (rel[c] > rtol && its[c] < maxit) ? 1 : 0;
+        act[c] = (hs[c] > thr2[c] && its[c] < maxit) ? 1 : 0;
+        conv_c[c] = hs[c] <= thr2[c];
         again = again || act[c];
       }
       if (!again) break;
@@ -2528,7 +2630,7 @@ r3mg_status mr_krylov(r3mg_hierarchy* h, int m, double rtol, int maxit, int* its
   for (int c = 0; c < m; ++c) {
     its_out[c] = its[c];
     rel_out[c] = rel[c];
-    conv = conv && rel[c] <= rtol;
+    conv = conv && (bb[c] == 0.0 || conv_c[c]);
   }
   return conv ? R3MG_OK : R3MG_E_NOCONV;
 }
@@ -2673,6 +2775,8 @@ static r3mg_status setup_common(int64_t n, int dim, const double* coords_host, c
     CK(cudaMallocHost(&h->host_scal, sizeof(double) * 16));
     h->status = dalloc<int>(h, 1);
     h->tma_err = dalloc<int>(h, 1);
+    // the allocation-free product's static scratch: its device address on this device
+    CK(cudaGetSymbolAddress((void**)&h->noalloc_scratch, g_noalloc_scratch));
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
     int dev = 0;
@@ -2728,6 +2832,8 @@ r3mg_status r3mg_batch_setup(int nprob, int dim, const int64_t* n, const double*
     CK(cudaMallocHost(&h->host_scal, sizeof(double) * 16));
     h->status = dalloc<int>(h, 1);
     h->tma_err = dalloc<int>(h, 1);
+    // the allocation-free product's static scratch: its device address on this device
+    CK(cudaGetSymbolAddress((void**)&h->noalloc_scratch, g_noalloc_scratch));
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     CK(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
     int dev = 0;
@@ -2989,8 +3095,7 @@ r3mg_status r3mg_coarse_solve(r3mg_hierarchy* h, const double* r_dev, double* z_
   if (!h->bl.empty()) { h->err = "coarse_solve: batched hierarchy"; return R3MG_E_ARG; }
   return guarded(h, [&] {
     StreamJoin j(h, stream);
-    k_dense_gemv<double><<<grid_for(h->nc * 32), 256, 0, h->stream>>>(h->Ainv64, h->ncp, r_dev, h->nc, z_dev);
-    CK(cudaGetLastError());
+    coarsest_apply<double>(h, r_dev, z_dev);
   });
 }
 
@@ -3191,15 +3296,307 @@ void r3mg_destroy(r3mg_hierarchy* h) {
   delete h;
 }
 
-// ---------------------------------------------------------------- allocation-free product
-// Scratch of r3mg_level0_apply_noalloc: the caller-numbered input and output permuted into
-// tree order.  It lives in the library image, so every GPU that loads the library holds it
-// (16 MiB) until the process exits; no call ever allocates it.
-constexpr int64_t kNoAllocMaxN = (int64_t)1 << 20;
-static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxN];
-static std::mutex g_noalloc_mutex;
-static double* g_noalloc_addr[256] = {};   // device address of the scratch, per device ordinal
+// ---------------------------------------------------------------- single steps, statistics, exports
+r3mg_status r3mg_level_apply_prec(r3mg_hierarchy* h, int level, int fp32, const double* x_dev, double* y_dev,
+                                  void* stream) {
+  if (!h || level < 0 || level >= h->L || !x_dev || !y_dev || (fp32 != 0 && fp32 != 1)) return R3MG_E_ARG;
+  if (!fp32) return r3mg_level_apply(h, level, x_dev, y_dev, stream);
+  if (h->prm.precision != 1 || level == h->L - 1) {
+    h->err = "level_apply_prec: FP32 values exist only on the smoothed levels of an FP32 V-cycle hierarchy";
+    return R3MG_E_ARG;
+  }
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    Level& A = h->lv[level];
+    float* xs = (float*)A.x;   // the level's V-cycle vectors serve as FP32 scratch
+    float* ys = (float*)A.r;
+    const int gv = grid_for(A.n);
+    k_gather_perm<double, float><<<gv, 256, 0, h->stream>>>(x_dev, level == 0 ? h->perm : nullptr, xs, A.n);
+    CK(cudaGetLastError());
+    level_apply_dot<float>(h, A, xs, ys, nullptr, nullptr);
+    k_scatter_perm<float, double><<<gv, 256, 0, h->stream>>>(ys, level == 0 ? h->perm : nullptr, y_dev, A.n);
+    CK(cudaGetLastError());
+  });
+}
 
+r3mg_status r3mg_level_cheb_step(r3mg_hierarchy* h, int level, const double* x_dev, const double* r_dev,
+                                 const double* d_dev, double a, double c, double* x_out, double* r_out,
+                                 double* d_out, void* stream) {
+  if (!h || level < 0 || level + 1 >= h->L || !x_dev || !r_dev || !d_dev || !x_out || !r_out || !d_out)
+    return R3MG_E_ARG;
+  if (!h->bl.empty()) { h->err = "level_cheb_step: batched hierarchy"; return R3MG_E_ARG; }
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    Level& A = h->lv[level];
+    const int64_t* perm = level == 0 ? h->perm : nullptr;
+    const int gv = grid_for(A.n);
+    auto run = [&](auto zero) {
+      using T = decltype(zero);
+      T *x = (T*)A.x, *r = (T*)A.r, *d = (T*)A.d[0], *dn = (T*)A.d[1];
+      k_gather_perm<double, T><<<gv, 256, 0, h->stream>>>(x_dev, perm, x, A.n);
+      k_gather_perm<double, T><<<gv, 256, 0, h->stream>>>(r_dev, perm, r, A.n);
+      k_gather_perm<double, T><<<gv, 256, 0, h->stream>>>(d_dev, perm, d, A.n);
+      CK(cudaGetLastError());
+      level_cheb<T>(h, A, x, r, d, dn, Dinv<T>(A), (T)a, (T)c);
+      k_scatter_perm<T, double><<<gv, 256, 0, h->stream>>>(x, perm, x_out, A.n);
+      k_scatter_perm<T, double><<<gv, 256, 0, h->stream>>>(r, perm, r_out, A.n);
+      k_scatter_perm<T, double><<<gv, 256, 0, h->stream>>>(dn, perm, d_out, A.n);
+      CK(cudaGetLastError());
+    };
+    if (h->prm.precision == 1) run(0.0f); else run(0.0);
+  });
+}
+
+r3mg_status r3mg_coarse_solve_prec(r3mg_hierarchy* h, int fp32, const double* r_dev, double* z_dev, void* stream) {
+  if (!h || !r_dev || !z_dev || (fp32 != 0 && fp32 != 1)) return R3MG_E_ARG;
+  if (!fp32) return r3mg_coarse_solve(h, r_dev, z_dev, stream);
+  if (!h->bl.empty() || h->prm.precision != 1) {
+    h->err = "coarse_solve_prec: the FP32 inverse exists only on single FP32 V-cycle hierarchies";
+    return R3MG_E_ARG;
+  }
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    Level& C = h->lv[h->L - 1];
+    float* rs = (float*)C.r;
+    float* zs = (float*)C.x;
+    k_convert<double, float><<<grid_for(h->nc), 256, 0, h->stream>>>(r_dev, rs, h->nc);
+    coarsest_apply<float>(h, rs, zs);
+    k_convert<float, double><<<grid_for(h->nc), 256, 0, h->stream>>>(zs, z_dev, h->nc);
+    CK(cudaGetLastError());
+  });
+}
+
+r3mg_status r3mg_set_stop_rule(r3mg_hierarchy* h, double atol, double reduction) {
+  if (!h) return R3MG_E_ARG;
+  if (!(atol >= 0.0) || !(reduction >= 0.0) || !std::isfinite(atol) || !std::isfinite(reduction)) {
+    h->err = "set_stop_rule: atol and reduction must be finite and >= 0";
+    return R3MG_E_ARG;
+  }
+  h->stop_atol = atol;
+  h->stop_red = reduction;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_cond_estimate(r3mg_hierarchy* h, int column, double* cond_out, double* lmin_out, double* lmax_out,
+                               int* steps_out) {
+  if (!h) return R3MG_E_ARG;
+  if (column >= 0 && (column >= h->mr_last_m || !h->mr_scal)) {
+    h->err = "cond_estimate: no such column in the last block solve";
+    return R3MG_E_ARG;
+  }
+  if (!h->bl.empty()) { h->err = "cond_estimate: not kept for batched solves"; return R3MG_E_ARG; }
+  return guarded(h, [&] {
+    double* hs = h->host_scal;   // pinned, 16 doubles
+    const double* hist;
+    double* cnt_a;
+    double* cnt_b;
+    if (column < 0) {
+      cnt_a = h->scal + S_NA; cnt_b = h->scal + S_NB; hist = h->scal + S_COUNT;
+    } else {
+      const int M = h->mr_M;
+      cnt_a = h->mr_scal + S_NA * M + column; cnt_b = h->mr_scal + S_NB * M + column;
+      hist = h->mr_scal + S_COUNT * M + (int64_t)column * 2 * kHist;
+    }
+    CK(cudaMemcpyAsync(&hs[10], cnt_a, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&hs[11], cnt_b, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const int na = std::min((int)hs[10], kHist), nb = std::min((int)hs[11], kHist);
+    const int k = std::min(na, nb + 1);
+    std::vector<double> al(kHist), be(kHist);
+    if (k > 0) {
+      CK(cudaMemcpy(al.data(), hist, sizeof(double) * k, cudaMemcpyDeviceToHost));
+      if (k > 1) CK(cudaMemcpy(be.data(), hist + kHist, sizeof(double) * (k - 1), cudaMemcpyDeviceToHost));
+    }
+    // Lanczos tridiagonal of the CG iteration: T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+    // T_{j,j+1} = sqrt(beta_j)/alpha_j; its extreme eigenvalues estimate those of M^{-1} A
+    double lmin = 0.0, lmax = 0.0, cond = 1.0;
+    if (k > 0) {
+      std::vector<double> dg(k), off(k > 1 ? k - 1 : 0);
+      for (int i = 0; i < k; ++i) {
+        dg[i] = 1.0 / al[i] + (i > 0 ? be[i - 1] / al[i - 1] : 0.0);
+        if (i + 1 < k) off[i] = std::sqrt(std::max(be[i], 0.0)) / al[i];
+      }
+      lmin = tridiag_kth_eig(dg, off, 0);
+      lmax = tridiag_kth_eig(dg, off, k - 1);
+      cond = lmax / lmin;
+    }
+    if (cond_out) *cond_out = cond;
+    if (lmin_out) *lmin_out = lmin;
+    if (lmax_out) *lmax_out = lmax;
+    if (steps_out) *steps_out = k;
+  });
+}
+
+r3mg_status r3mg_stats(r3mg_hierarchy* h, double* H_out, double* h_out, double* ratio_out, double* ritz_out) {
+  if (!h) return R3MG_E_ARG;
+  if (H_out) *H_out = h->H_coarse;
+  if (h_out) *h_out = h->h_fine;
+  if (ratio_out) *ratio_out = h->h_fine > 0.0 ? h->H_coarse / h->h_fine : 0.0;
+  if (ritz_out) {
+    for (int l = 0; l < h->L; ++l) {
+      double v = 0.0;
+      if (l + 1 < h->L) {
+        if (h->bl.empty()) v = l < (int)h->ritz.size() ? h->ritz[l] : 0.0;
+        else for (double lam : h->bl[l].lam) v = std::max(v, lam / h->prm.eig_safety);
+      }
+      ritz_out[l] = v;
+    }
+  }
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_get_transfer_pattern(r3mg_hierarchy* h, int level, int64_t* rowptr_host, int32_t* cols_host,
+                                      double* vals_host) {
+  if (!h || level < 0 || level + 1 >= h->L || !rowptr_host) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    const int b = h->b;
+    const int64_t nl = h->lv[level].n;
+    for (int64_t i = 0; i <= nl; ++i) rowptr_host[i] = i * b;
+    std::vector<int64_t> box;   // level 0: level-1 box of every tree position
+    if (level == 0) {
+      box.resize(h->n);
+      const auto& off = h->part.box_off[1];
+      for (int64_t B = 0; B + 1 < (int64_t)off.size(); ++B)
+        for (int64_t k = off[B]; k < off[B + 1]; ++k) box[k] = B;
+    }
+    if (cols_host) {
+      for (int64_t i = 0; i < nl; ++i) {
+        const int64_t parent = (level == 0) ? box[h->part.iperm[i]] : (i / b) / h->fan;
+        for (int q = 0; q < b; ++q) cols_host[i * b + q] = (int32_t)(parent * b + q);
+      }
+    }
+    if (vals_host) {
+      const int64_t cnt = nl * b;
+      std::vector<double> t(cnt);
+      CK(cudaMemcpyAsync(t.data(), h->P64[level], sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (level == 0) {
+        for (int64_t k = 0; k < h->n; ++k) std::memcpy(vals_host + h->part.perm[k] * b, t.data() + k * b, sizeof(double) * b);
+      } else {
+        std::memcpy(vals_host, t.data(), sizeof(double) * cnt);   // rows (c, q') already in level order
+      }
+    }
+  });
+}
+
+r3mg_status r3mg_get_level_matrix(r3mg_hierarchy* h, int level, int64_t* rowptr_host, int32_t* cols_host,
+                                  double* vals_host) {
+  if (!h || level < 1 || level >= h->L || !rowptr_host) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    const int b = h->b;
+    const Level& C = h->lv[level];
+    const HostPattern& pt = C.pat;
+    rowptr_host[0] = 0;
+    for (int64_t B = 0; B < C.nbox; ++B) {
+      const int64_t len = (pt.ptr[B + 1] - pt.ptr[B]) * b;
+      for (int q = 0; q < b; ++q) rowptr_host[B * b + q + 1] = rowptr_host[B * b + q] + len;
+    }
+    if (cols_host) {
+      for (int64_t B = 0; B < C.nbox; ++B)
+        for (int q1 = 0; q1 < b; ++q1) {
+          int64_t o = rowptr_host[B * b + q1];
+          for (int64_t e = pt.ptr[B]; e < pt.ptr[B + 1]; ++e)
+            for (int q = 0; q < b; ++q) cols_host[o++] = (int32_t)(pt.nbr[e] * b + q);
+        }
+    }
+    if (vals_host) {
+      std::vector<double> blk((size_t)C.npairs * b * b);
+      CK(cudaStreamSynchronize(h->stream));
+      r3mg_status st = r3mg_get_level_blocks(h, level, blk.data());
+      if (st != R3MG_OK) throw Fail{st, h->err};
+      for (int64_t B = 0; B < C.nbox; ++B)
+        for (int q1 = 0; q1 < b; ++q1) {
+          int64_t o = rowptr_host[B * b + q1];
+          for (int64_t e = pt.ptr[B]; e < pt.ptr[B + 1]; ++e)
+            for (int q = 0; q < b; ++q) vals_host[o++] = blk[(size_t)e * b * b + q1 * b + q];
+        }
+    }
+  });
+}
+
+r3mg_status r3mg_device_status(r3mg_hierarchy* h, void* stream) {
+  if (!h) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    StreamJoin j(h, stream);
+    int terr = 0;
+    CK(cudaMemcpyAsync(&h->host_scal[15], h->tma_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(&terr, &h->host_scal[15], sizeof(int));
+    if (terr) {
+      CK(cudaMemsetAsync(h->tma_err, 0, sizeof(int), h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      throw Fail{R3MG_E_TIMEOUT, "a bounded wait of a copy-engine-streamed kernel expired since the last check"};
+    }
+  });
+}
+
+r3mg_status r3mg_set_coarse_mode(r3mg_hierarchy* h, int mode) {
+  if (!h || (mode != 0 && mode != 1)) return R3MG_E_ARG;
+  if (mode == 1 && (!h->bl.empty() || !h->L64)) {
+    h->err = "set_coarse_mode: the substitution form needs a single (not batched) hierarchy";
+    return R3MG_E_ARG;
+  }
+  const size_t sm = sizeof(double) * (size_t)h->nc;
+  if (mode == 1 && sm + 16 * 1024 > kMaxSmem) {   // dynamic solution vector + the kernels' static arrays
+    h->err = "set_coarse_mode: the coarsest level (" + std::to_string(h->nc) + " rows) does not fit one CTA's shared memory";
+    return R3MG_E_LIMIT;
+  }
+  return guarded(h, [&] {
+    CK(cudaStreamSynchronize(h->stream));
+    if (mode == 1) {
+      if (!h->ctmp) h->ctmp = dalloc<double>(h, h->nc);
+      ensure_smem((const void*)k_trsv_lower<double>, sm);
+      ensure_smem((const void*)k_trsv_lower_t<double>, sm);
+      ensure_smem((const void*)k_trsv_lower<float>, sm / 2);
+      ensure_smem((const void*)k_trsv_lower_t<float>, sm / 2);
+    }
+    h->coarse_mode = mode;
+    drop_graphs(h);   // captured V-cycles hold the old form
+  });
+}
+
+r3mg_status r3mg_set_wait_limit(r3mg_hierarchy* h, long long cycles, int withhold_first_copy) {
+  if (!h || cycles < 0 || cycles > 4000000000LL || (withhold_first_copy != 0 && withhold_first_copy != 1)) return R3MG_E_ARG;
+  return guarded(h, [&] {
+    CK(cudaStreamSynchronize(h->stream));
+    h->wait_cycles = cycles;
+    h->withhold_first = withhold_first_copy;
+    drop_graphs(h);   // captured graphs hold the old setting as launch arguments
+  });
+}
+
+r3mg_status r3mg_setup_device(int64_t n, int dim, const double* coords_host, const int64_t* rowptr_dev,
+                              const int32_t* colidx_dev, const double* vals_dev, const r3mg_params* params,
+                              void* stream, r3mg_hierarchy** out) {
+  if (!out) { g_last_error = "setup_device: null output"; return R3MG_E_ARG; }
+  *out = nullptr;
+  if (n < 1 || !rowptr_dev || !colidx_dev || !vals_dev) { g_last_error = "setup_device: null pointer or n < 1"; return R3MG_E_ARG; }
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> va;
+  cudaStream_t us = (cudaStream_t)stream;
+  try {
+    rp.resize(n + 1);
+    if (cudaMemcpyAsync(rp.data(), rowptr_dev, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, us) != cudaSuccess ||
+        cudaStreamSynchronize(us) != cudaSuccess) {
+      g_last_error = "setup_device: reading the row pointers failed";
+      return R3MG_E_CUDA;
+    }
+    const int64_t nnz = rp[n];
+    if (nnz < 0 || rp[0] != 0) { g_last_error = "setup_device: malformed row pointers"; return R3MG_E_ARG; }
+    ci.resize(nnz);
+    va.resize(nnz);
+    if (cudaMemcpyAsync(ci.data(), colidx_dev, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, us) != cudaSuccess ||
+        cudaMemcpyAsync(va.data(), vals_dev, sizeof(double) * nnz, cudaMemcpyDeviceToHost, us) != cudaSuccess ||
+        cudaStreamSynchronize(us) != cudaSuccess) {
+      g_last_error = "setup_device: reading the CSR arrays failed";
+      return R3MG_E_CUDA;
+    }
+  } catch (std::bad_alloc&) { g_last_error = "host allocation failed"; return R3MG_E_OOM; }
+  return setup_common(n, dim, coords_host, rp.data(), ci.data(), va.data(), nullptr, params, stream, out);
+}
+
+// ---------------------------------------------------------------- allocation-free product
 r3mg_status r3mg_level0_apply_noalloc(r3mg_hierarchy* h, const double* x_dev, double* y_dev, void* stream) {
   if (!h || !x_dev || !y_dev) return R3MG_E_ARG;
   if (h->n > kNoAllocMaxN) {
@@ -3207,18 +3604,11 @@ r3mg_status r3mg_level0_apply_noalloc(r3mg_hierarchy* h, const double* x_dev, do
              std::to_string(kNoAllocMaxN) + " DoFs";
     return R3MG_E_LIMIT;
   }
+  if (!h->noalloc_scratch) { h->err = "level0_apply_noalloc: no scratch address"; return R3MG_E_CUDA; }
   return guarded(h, [&] {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) throw Fail{R3MG_E_ARG, "level0_apply_noalloc: device ordinal out of range"};
-    double* scratch = nullptr;
-    {
-      // first call on a device: look up the device address of the static array (host code
-      // may not use the symbol itself as a device pointer)
-      std::lock_guard<std::mutex> lk(g_noalloc_mutex);
-      if (!g_noalloc_addr[dev]) CK(cudaGetSymbolAddress((void**)&g_noalloc_addr[dev], g_noalloc_scratch));
-      scratch = g_noalloc_addr[dev];
-    }
+    // the device address of the static array was looked up by the setup call, on the
+    // hierarchy's device (host code may not use the symbol itself as a device pointer)
+    double* scratch = h->noalloc_scratch;
     double* xt = scratch;                  // x in tree order
     double* yt = scratch + kNoAllocMaxN;   // y in tree order
     StreamJoin j(h, stream);

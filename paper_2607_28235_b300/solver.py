@@ -68,6 +68,21 @@ def partition_cells(coords: np.ndarray, cell_ptr: np.ndarray, cell_pts: np.ndarr
     return perm, off[:nb + 1].copy(), lo[:nb * d].reshape(nb, d).copy(), hi[:nb * d].reshape(nb, d).copy(), depth.value
 
 
+def wait_selftest(limit_cycles: int) -> tuple:
+    """(status, expired): a one-CTA kernel whose mbarrier wait can only run out (status 10 = E_TIMEOUT)."""
+    e = ctypes.c_int(0)
+    rc = lib().r3mg_wait_selftest(int(limit_cycles), ctypes.byref(e), _stream())
+    return rc, e.value
+
+
+def measure_fp64_rates() -> dict:
+    """Sustained FP64 FMA and FP64 tensor-core (mma.sync) rates of the current GPU, TFLOP/s."""
+    f = ctypes.c_double(0)
+    m = ctypes.c_double(0)
+    _check(lib().r3mg_measure_fp64_rates(ctypes.byref(f), ctypes.byref(m), _stream()))
+    return {"fma_tflops": f.value, "mma_tflops": m.value}
+
+
 class Hierarchy:
     """R-tree multilevel hierarchy on the current CUDA device."""
 
@@ -83,12 +98,27 @@ class Hierarchy:
         self.params = {f: getattr(p, f) for f, _ in _Params._fields_}
         x = np.ascontiguousarray(coords, dtype=np.float64)
         self.n, self.dim = x.shape
-        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
-        ci = np.ascontiguousarray(colidx, dtype=np.int32)
-        va = np.ascontiguousarray(vals, dtype=np.float64)
-        self.nnz = int(rp[-1])
+        on_device = isinstance(rowptr, torch.Tensor) and rowptr.is_cuda
+        rp = None if on_device else np.ascontiguousarray(rowptr, dtype=np.int64)
+        ci = None if on_device else np.ascontiguousarray(colidx, dtype=np.int32)
+        va = None if on_device else np.ascontiguousarray(vals, dtype=np.float64)
+        self.nnz = 0 if on_device else int(rp[-1])
         self.b = (p.pprime + 1) ** self.dim
         h = ctypes.c_void_p()
+        if isinstance(rowptr, torch.Tensor) and rowptr.is_cuda:
+            # CSR arrays in device memory (r3mg_setup_device reads them back for the host analysis)
+            assert cells is None, "cell-based setup takes host arrays"
+            drp = rowptr.contiguous().to(torch.int64)
+            dci = colidx.contiguous().to(torch.int32)
+            dva = vals.contiguous().to(torch.float64)
+            self.nnz = int(drp[-1].item())
+            self.b = (p.pprime + 1) ** self.dim
+            rc = lib().r3mg_setup_device(self.n, self.dim, _p(x), _p(drp), _p(dci), _p(dva), ctypes.byref(p),
+                                         _stream(), ctypes.byref(h))
+            _check(rc)
+            self._h = h
+            self.levels = self.info()["levels"]
+            return
         if cells is None:
             rc = lib().r3mg_setup(self.n, self.dim, _p(x), _p(rp), _p(ci), _p(va), ctypes.byref(p), _stream(),
                                   ctypes.byref(h))
@@ -201,19 +231,78 @@ class Hierarchy:
         assert vals.is_cuda and vals.dtype == torch.float64 and vals.numel() == self.nnz
         _check(lib().r3mg_update_values(self._h, _p(vals), _stream()), self._h)
 
-    def coarse_solve(self, r: torch.Tensor) -> torch.Tensor:
-        """z = A_{L-1}^{-1} r on the coarsest level (FP64, coarsest-level numbering)."""
+    def coarse_solve(self, r: torch.Tensor, fp32: bool = False) -> torch.Tensor:
+        """z = A_{L-1}^{-1} r on the coarsest level (coarsest-level numbering); fp32: the FP32 inverse."""
         r = r.contiguous()
         assert r.is_cuda and r.dtype == torch.float64
         z = torch.empty_like(r)
-        _check(lib().r3mg_coarse_solve(self._h, _p(r), _p(z), _stream()), self._h)
+        _check(lib().r3mg_coarse_solve_prec(self._h, 1 if fp32 else 0, _p(r), _p(z), _stream()), self._h)
         return z
 
-    def level_apply(self, level: int, x: torch.Tensor) -> torch.Tensor:
+    def level_apply(self, level: int, x: torch.Tensor, fp32: bool = False) -> torch.Tensor:
+        """y = A_l x with the V-cycle's kernel; fp32 uses the FP32 values (FP32 V-cycle hierarchies)."""
         x = x.contiguous()
         y = torch.empty_like(x)
-        _check(lib().r3mg_level_apply(self._h, int(level), _p(x), _p(y), _stream()), self._h)
+        _check(lib().r3mg_level_apply_prec(self._h, int(level), 1 if fp32 else 0, _p(x), _p(y), _stream()), self._h)
         return y
+
+    def cheb_step(self, level: int, x: torch.Tensor, r: torch.Tensor, d: torch.Tensor, a: float, c: float):
+        """One fused Chebyshev-Jacobi step in the V-cycle precision: (x + d, r - A d, a d + c D^-1 (r - A d))."""
+        x = x.contiguous(); r = r.contiguous(); d = d.contiguous()
+        xo = torch.empty_like(x); ro = torch.empty_like(r); do = torch.empty_like(d)
+        _check(lib().r3mg_level_cheb_step(self._h, int(level), _p(x), _p(r), _p(d), float(a), float(c), _p(xo), _p(ro),
+                                          _p(do), _stream()), self._h)
+        return xo, ro, do
+
+    def set_stop_rule(self, atol: float = 0.0, reduction: float = 0.0):
+        """Stop when ||r|| <= max(rtol ||b||, atol, reduction ||r_0||) (rtol = 0, 1e-9, 1e-6: the paper's rule)."""
+        _check(lib().r3mg_set_stop_rule(self._h, float(atol), float(reduction)), self._h)
+
+    def cond_estimate(self, column: int = -1) -> dict:
+        """Condition estimate of the last solve (column >= 0: that column of the last block solve)."""
+        c = ctypes.c_double(0); lo = ctypes.c_double(0); hi = ctypes.c_double(0); k = ctypes.c_int(0)
+        _check(lib().r3mg_cond_estimate(self._h, int(column), ctypes.byref(c), ctypes.byref(lo), ctypes.byref(hi),
+                                        ctypes.byref(k)), self._h)
+        return {"cond": c.value, "lmin": lo.value, "lmax": hi.value, "steps": k.value}
+
+    def stats(self) -> dict:
+        """H (largest coarsest-box diameter), h (largest coupled-point distance), H/h, Ritz values per level."""
+        H = ctypes.c_double(0); hh = ctypes.c_double(0); q = ctypes.c_double(0)
+        ritz = np.zeros(self.levels, np.float64)
+        _check(lib().r3mg_stats(self._h, ctypes.byref(H), ctypes.byref(hh), ctypes.byref(q), _p(ritz)), self._h)
+        return {"H": H.value, "h": hh.value, "H_over_h": q.value, "ritz": ritz}
+
+    def transfer_pattern(self, level: int, values: bool = True):
+        """CSR (rowptr, cols, vals) of the transfer from level l+1 to level l (vals None unless values)."""
+        nl = int(self.info()["n"][level])
+        rp = np.empty(nl + 1, np.int64)
+        cols = np.empty(nl * self.b, np.int32)
+        vals = np.empty(nl * self.b, np.float64) if values else None
+        _check(lib().r3mg_get_transfer_pattern(self._h, int(level), _p(rp), _p(cols), _p(vals) if values else None),
+               self._h)
+        return rp, cols, vals
+
+    def level_matrix(self, level: int):
+        """CSR (rowptr, cols, vals) of the Galerkin operator A_l, l >= 1, in coarse numbering."""
+        nl = int(self.info()["n"][level])
+        rp = np.empty(nl + 1, np.int64)
+        _check(lib().r3mg_get_level_matrix(self._h, int(level), _p(rp), None, None), self._h)
+        cols = np.empty(int(rp[-1]), np.int32)
+        vals = np.empty(int(rp[-1]), np.float64)
+        _check(lib().r3mg_get_level_matrix(self._h, int(level), _p(rp), _p(cols), _p(vals)), self._h)
+        return rp, cols, vals
+
+    def set_coarse_mode(self, mode: int):
+        """Coarsest solve: 0 = explicit inverse (GEMV), 1 = forward and back substitution with L."""
+        _check(lib().r3mg_set_coarse_mode(self._h, int(mode)), self._h)
+
+    def set_wait_limit(self, cycles: int = 0, withhold_first_copy: bool = False):
+        """Limit of the streamed kernels' bounded waits (0 = default); withhold_first_copy tests the expiry path."""
+        _check(lib().r3mg_set_wait_limit(self._h, int(cycles), 1 if withhold_first_copy else 0), self._h)
+
+    def device_status(self) -> int:
+        """Status code of the bounded device waits since the last check (0, or 10 = E_TIMEOUT)."""
+        return lib().r3mg_device_status(self._h, _stream())
 
     def sampled_outer(self, lam: torch.Tensor, u: torch.Tensor, alpha: float = -1.0) -> torch.Tensor:
         """out[k] = alpha * lam[i] * u[j] on every stored entry (i, j), in the setup CSR order."""

@@ -265,3 +265,33 @@ def test_update_values_recaptures(pair):
     assert abs(it - refs.iterations) <= 1
     assert np.linalg.norm(P.b - A2 @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(P.b)
     Hu.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coarse_substitution_form(pair, precision):
+    """The coarsest solve by forward and back substitution with the Cholesky factor (the
+    oracle's own method) against the oracle, and the V-cycle with it against the V-cycle with
+    the explicit inverse: the two forms of A_c^{-1} differ by kappa(A_c) eps at most."""
+    P, params, H, Ho = pair
+    Hc = _hier(P, params, precision=precision)
+    Ac = Ho.A[-1].toarray()
+    kappa = np.linalg.cond(Ac)
+    r = np.random.default_rng(19).standard_normal(Ac.shape[0])
+    z0 = Hc.coarse_solve(torch.tensor(r, device="cuda"), fp32=bool(precision)).cpu().numpy()
+    rv = np.random.default_rng(20).standard_normal(P.n)
+    v0 = Hc.vcycle(torch.tensor(rv, device="cuda")).cpu().numpy()
+    Hc.set_coarse_mode(1)
+    z1 = Hc.coarse_solve(torch.tensor(r, device="cuda"), fp32=bool(precision)).cpu().numpy()
+    v1 = Hc.vcycle(torch.tensor(rv, device="cuda")).cpu().numpy()
+    ref = O.cholesky_solve(Ho.Lc, r)
+    eps = 2.0 ** -53 if precision == 0 else 2.0 ** -24
+    tol = 64 * eps * kappa
+    assert np.linalg.norm(z1 - ref) <= tol * np.linalg.norm(ref), (np.linalg.norm(z1 - ref) / np.linalg.norm(ref), tol)
+    assert np.linalg.norm(z0 - z1) <= tol * np.linalg.norm(ref)
+    assert np.linalg.norm(v1 - v0) <= tol * np.linalg.norm(v0)
+    if precision == 0:
+        assert np.linalg.norm(v1 - O.vcycle(Ho, rv)) <= 1e-12 * np.linalg.norm(v1)
+    x, it, rel = Hc.pcg(torch.tensor(P.b, device="cuda"), rtol=1e-10)
+    assert rel <= 1e-10
+    Hc.set_coarse_mode(0)
+    Hc.close()
