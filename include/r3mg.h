@@ -463,7 +463,9 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
  * form 0 = register-streamed, 1 = TMA-streamed, 2 = register-streamed persistent with a
  * double-buffered window, 3 = register-streamed with a bulk L2 prefetch of each box's matrix
  * slice, 4 = symmetric block form (coarse FP32 levels: only the upper blocks are streamed, each
- * used for both of its products); lanes per matrix row; threads per CTA;
+ * used for both of its products), 5 = register-streamed with a software-pipelined row loop
+ * (the next chunk of matrix entries is in flight while the current one is consumed), 6 = form 5
+ * with the L2 prefetch; lanes per matrix row; threads per CTA;
  * the autotuner's measured time of one launch (0 when not tuned).  Any output may be NULL. */
 r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
                                float* tuned_ms);
@@ -503,7 +505,7 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
                                double* out_dev, void* stream);
 
 /* Pin the level-operator kernel of level l and precision (fp32 = 1 needs an FP32 V-cycle):
- * form 0..4 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads per CTA in
+ * form 0..6 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads per CTA in
  * {128, 256} for the register forms and {256, 512, 1024} for the TMA form.  Replays a configuration chosen earlier (reproducible timing
  * and profiling).  Errors: R3MG_E_ARG for an unsupported combination.  Synchronises. */
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads);

@@ -141,7 +141,67 @@ struct TEpCheb {
   }
 };
 
-template <typename T, int G, bool FINE, class Ep, int U, bool PIPE, bool PF>
+// Shared-memory carve-up of one stage of the register kernels (byte offsets): the window,
+// the epilogue's own-row vectors, the box's row offsets (absolute entry positions, int64) and
+// (fine level) its row order, so that no row waits on a dependent global load for its bounds.
+struct LevelSmem {
+  size_t aux = 0, rp = 0, ord = 0, total = 0;
+  static __host__ __device__ size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
+  __host__ __device__ LevelSmem(size_t elem, int win_max, int max_box_rows) {
+    aux = up16(elem * (size_t)win_max);
+    rp = aux + up16(elem * (size_t)kAuxMax * max_box_rows);
+    ord = rp + up16(sizeof(int64_t) * ((size_t)max_box_rows + 1));
+    total = ord + up16(sizeof(int32_t) * (size_t)max_box_rows);
+  }
+};
+
+// One chunk of a row: U steps of 4 consecutive entries per lane (values, and the fine level's
+// packed 16-bit window indices; coarse rows index the window by position).
+template <typename T, int U, bool FINE>
+struct Chunk {
+  T v[U][4];
+  uint2 q[U];   // fine: packed indices; coarse: q[u].x = window position of the step's first entry
+  __device__ __forceinline__ void load(const T* vals, const uint16_t* idx, int64_t k, int64_t k0, int64_t k1, int G) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * 4 * G;
+      if (kk < k1) {
+        Vec4<T>::load(vals + kk, v[u]);
+        if constexpr (FINE) q[u] = __ldcs(reinterpret_cast<const uint2*>(idx + kk));
+        else q[u] = make_uint2((unsigned)(kk - k0), 0u);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[u][j] = T(0);
+        q[u] = make_uint2(0u, 0u);
+      }
+    }
+  }
+  // FP64: two fused multiply-add chains (one FP64-pipe instruction per stored entry: the FP64
+  // pipe, not HBM, bounds the FP64 form; a product tree adds a multiply and an add per four
+  // entries).  FP32: a short product tree per step (shorter dependent chains).
+  __device__ __forceinline__ void consume(const T* win, T (&acc)[2]) const {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int ii[4];
+      if constexpr (FINE) { ii[0] = q[u].x & 0xffff; ii[1] = q[u].x >> 16; ii[2] = q[u].y & 0xffff; ii[3] = q[u].y >> 16; }
+      else { const int t = (int)q[u].x; ii[0] = t; ii[1] = t + 1; ii[2] = t + 2; ii[3] = t + 3; }
+      T& a = acc[u & 1];
+      if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a = fma_rn(v[u][j], win[ii[j]], a);
+      } else {
+        a += v[u][0] * win[ii[0]] + v[u][1] * win[ii[1]] + v[u][2] * win[ii[2]] + v[u][3] * win[ii[3]];
+      }
+    }
+  }
+};
+
+// PIPE: persistent CTAs with two stages (the next box staged while the current one computes).
+// PF: an L2 bulk prefetch of each box's matrix slice.  SP: software-pipelined row loop (the
+// next chunk -- of the same row, or the group's next row -- is loaded into registers before the
+// current chunk is consumed, so loads stay in flight through the arithmetic, the group
+// reduction and the epilogue).
+template <typename T, int G, bool FINE, class Ep, int U, bool PIPE, bool PF, bool SP>
 __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __restrict__ xin, Ep ep,
                                                     double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -149,21 +209,26 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
   const int NG = blockDim.x / G, NW = blockDim.x >> 5;   // 128 or 256 threads
   const int g = threadIdx.x / G, lane = threadIdx.x % G;
   const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  const LevelSmem lay(sizeof(T), L.win_max, L.max_box_rows);
   double acc = 0.0;
-  // window staging: one warp per neighbour slot, asynchronous global->shared copies
-  // (cp.async) so every element of the window is in flight at once
+  auto box_rows = [&](int64_t B, int64_t& r0, int64_t& r1) {
+    if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
+    else { r0 = B * L.b; r1 = r0 + L.b; }
+  };
   // the box's matrix slice is contiguous: one thread asks the copy engine to pull it into L2
   auto prefetch = [&](int64_t B) {
     if (threadIdx.x == 0) {
       int64_t r0, r1;
-      if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
-      else { r0 = B * L.b; r1 = r0 + L.b; }
+      box_rows(B, r0, r1);
       const int64_t k0 = L.row_ptr[r0], k1 = L.row_ptr[r1];
       bulk_prefetch_l2(L.vals, k0 * (int64_t)sizeof(T), k1 * (int64_t)sizeof(T));
       if constexpr (FINE) bulk_prefetch_l2(L.idx, k0 * 2, k1 * 2);
     }
   };
-  auto stage = [&](int64_t B, T* win) {
+  // window staging: one warp per neighbour slot, asynchronous global->shared copies
+  // (cp.async) so every element of the window is in flight at once
+  auto stage = [&](int64_t B, unsigned char* base) {
+    T* win = reinterpret_cast<T*>(base);
     const int64_t e0 = L.nbr_ptr[B];
     const int nn = (int)(L.nbr_ptr[B + 1] - e0);
     int W;
@@ -185,96 +250,117 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
     }
     const int Wp = (W + 3) & ~3;
     for (int k = W + threadIdx.x; k < Wp; k += blockDim.x) win[k] = T(0);
-    // the epilogue's own-row vectors, so no row waits on a dependent global load
+    // the epilogue's own-row vectors and the rows' bounds, so no row waits on a dependent
+    // global load
     int64_t r0, r1;
-    if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
-    else { r0 = B * L.b; r1 = r0 + L.b; }
-    T* aux = win + L.win_max;
+    box_rows(B, r0, r1);
+    T* aux = reinterpret_cast<T*>(base + lay.aux);
     const int nr = (int)(r1 - r0);
     for (int j = 0; j < Ep::kStage; ++j) {
       if (!ep.stage(j)) continue;
       const T* sp = ep.src(j);
       for (int t = threadIdx.x; t < nr; t += blockDim.x) cp_async_elem(aux + j * L.max_box_rows + t, sp + r0 + t);
     }
+    int64_t* rp = reinterpret_cast<int64_t*>(base + lay.rp);
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) cp_async_elem(rp + t, L.row_ptr + r0 + t);
+    if (FINE && L.row_order) {
+      int32_t* od = reinterpret_cast<int32_t*>(base + lay.ord);
+      for (int t = threadIdx.x; t < nr; t += blockDim.x) cp_async_elem(od + t, L.row_order + r0 + t);
+    }
   };
-  auto compute = [&](int64_t B, const T* win) {
+  auto compute = [&](int64_t B, unsigned char* base) {
+    const T* win = reinterpret_cast<const T*>(base);
     int64_t r0, r1;
-    if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
-    else { r0 = B * L.b; r1 = r0 + L.b; }
+    box_rows(B, r0, r1);
+    const int nr = (int)(r1 - r0);
     T* auxp[kAuxMax];
-    for (int j = 0; j < kAuxMax; ++j) auxp[j] = const_cast<T*>(win) + L.win_max + j * L.max_box_rows;
+    for (int j = 0; j < kAuxMax; ++j) auxp[j] = reinterpret_cast<T*>(base + lay.aux) + j * L.max_box_rows;
+    const int64_t* rp = reinterpret_cast<const int64_t*>(base + lay.rp);
+    const int32_t* od = reinterpret_cast<const int32_t*>(base + lay.ord);
+    // local row of this group at row-loop iteration `it` (-1 past the box's end); rows are
+    // taken longest first on the fine level (host-built order) so the groups finish together
+    auto row_at = [&](int it) -> int {
+      const int i = it * NG + g;
+      if (i >= nr) return -1;
+      return (FINE && L.row_order) ? od[i] : i;
+    };
     // warp-uniform trip count: every lane of a warp runs the same iterations so the
     // group shuffles always see the full warp; rows past the box end are masked.
     const int g_first = (threadIdx.x >> 5) * (32 / G);
-    for (int64_t base = r0; base + g_first < r1; base += NG) {
-      const bool ok = base + g < r1;
-      // rows are taken longest first (host-built order) so the groups finish together
-      const int64_t row = (FINE && L.row_order && ok) ? r0 + L.row_order[base + g] : base + g;
+    const int nit = (nr > g_first) ? (nr - g_first + NG - 1) / NG : 0;
+    if constexpr (!SP) {
+      for (int it = 0; it < nit; ++it) {
+        const int lr = row_at(it);
+        int64_t k0 = 0, k1 = 0;
+        if (lr >= 0) { k0 = rp[lr]; k1 = rp[lr + 1]; }
+        T a[2] = {T(0), T(0)};
+        // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
+        for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G * U) {
+          Chunk<T, U, FINE> c;
+          c.load(L.vals, L.idx, k, k0, k1, G);
+          c.consume(win, a);
+        }
+        const T s = group_sum<G>(a[0] + a[1]);
+        if (lr >= 0 && lane == 0) ep.post(r0 + lr, lr, s, auxp, acc);
+      }
+    } else {
+      int lr = row_at(0);
       int64_t k0 = 0, k1 = 0;
-      if (ok) {
-        k0 = L.row_ptr[row];
-        k1 = L.row_ptr[row + 1];
-      }
-      // FP64: two accumulators (even and odd steps), each a chain of fused multiply-adds, so one
-      // FP64-pipe instruction per stored entry (the FP64 pipe, not HBM, bounds the FP64 form; a
-      // product tree adds a multiply and an add per four entries).  FP32: a short product tree
-      // per step of four entries (shorter dependent chains; the FP32 pipes have room to spare).
-      T sacc[2] = {T(0), T(0)};
-      // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
-      for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G * U) {
-        T v[U][4];
-        int ii[U][4];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int64_t kk = k + (int64_t)u * 4 * G;
-          if (kk < k1) {
-            Vec4<T>::load(L.vals + kk, v[u]);
-            if constexpr (FINE) load_idx4(L.idx + kk, ii[u]);
-            else { const int t = (int)(kk - k0); ii[u][0] = t; ii[u][1] = t + 1; ii[u][2] = t + 2; ii[u][3] = t + 3; }
+      if (lr >= 0) { k0 = rp[lr]; k1 = rp[lr + 1]; }
+      int64_t k = k0 + 4 * lane;
+      Chunk<T, U, FINE> cur;
+      if (nit > 0) cur.load(L.vals, L.idx, k, k0, k1, G);
+      for (int it = 0; it < nit; ++it) {
+        T a[2] = {T(0), T(0)};
+        const int lr_now = lr;
+        while (true) {
+          // the next chunk: further along this row, or the first of the group's next row
+          const bool same = k + 4 * G * U < k1;
+          int64_t nk, nk0 = k0, nk1 = k1;
+          int nlr = lr;
+          if (same) {
+            nk = k + 4 * G * U;
           } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) { v[u][j] = T(0); ii[u][j] = 0; }
+            nlr = (it + 1 < nit) ? row_at(it + 1) : -1;
+            nk0 = 0; nk1 = 0;
+            if (nlr >= 0) { nk0 = rp[nlr]; nk1 = rp[nlr + 1]; }
+            nk = nk0 + 4 * lane;
           }
+          Chunk<T, U, FINE> nxt;
+          nxt.load(L.vals, L.idx, nk, nk0, nk1, G);   // loads nothing past the row's end
+          cur.consume(win, a);
+          cur = nxt;
+          k = nk;
+          if (!same) { lr = nlr; k0 = nk0; k1 = nk1; break; }
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          T& a = sacc[u & 1];
-          if constexpr (sizeof(T) == 8) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) a = fma_rn(v[u][j], win[ii[u][j]], a);
-          } else {
-            a += v[u][0] * win[ii[u][0]] + v[u][1] * win[ii[u][1]] + v[u][2] * win[ii[u][2]] +
-                 v[u][3] * win[ii[u][3]];
-          }
-        }
+        const T s = group_sum<G>(a[0] + a[1]);
+        if (lr_now >= 0 && lane == 0) ep.post(r0 + lr_now, lr_now, s, auxp, acc);
       }
-      T s = group_sum<G>(sacc[0] + sacc[1]);
-      if (ok && lane == 0) ep.post(row, (int)(row - r0), s, auxp, acc);
     }
   };
-  T* win0 = reinterpret_cast<T*>(smem_raw);
+  unsigned char* base0 = smem_raw;
   if constexpr (!PIPE) {
     for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
       if (PF) prefetch(B);
-      stage(B, win0);
+      stage(B, base0);
       cp_async_wait_all();
       __syncthreads();
-      compute(B, win0);
+      compute(B, base0);
       __syncthreads();
     }
   } else {
     // persistent CTAs: the next box's window is staged while the current box computes
-    T* win1 = win0 + L.win_max + kAuxMax * L.max_box_rows;
+    unsigned char* base1 = smem_raw + lay.total;
     int64_t B = blockIdx.x;
-    if (B < L.nbox) { if (PF) prefetch(B); stage(B, win0); }
+    if (B < L.nbox) { if (PF) prefetch(B); stage(B, base0); }
     cp_async_commit_group();
     for (int k = 0; B < L.nbox; B += gridDim.x, ++k) {
       const int64_t nxt = B + gridDim.x;
-      if (nxt < L.nbox) { if (PF) prefetch(nxt); stage(nxt, (k & 1) ? win0 : win1); }
+      if (nxt < L.nbox) { if (PF) prefetch(nxt); stage(nxt, (k & 1) ? base0 : base1); }
       cp_async_commit_group();
       cp_async_wait_group1();
       __syncthreads();
-      compute(B, (k & 1) ? win1 : win0);
+      compute(B, (k & 1) ? base1 : base0);
       __syncthreads();
     }
   }
@@ -287,8 +373,8 @@ __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __r
 }
 
 template <typename T>
-inline size_t level_smem_bytes(const LevelView<T>& L) {   // one window + staged own-row vectors
-  return sizeof(T) * ((size_t)L.win_max + (size_t)kAuxMax * L.max_box_rows);
+inline size_t level_smem_bytes(const LevelView<T>& L) {   // one stage: window, own-row vectors, row bounds
+  return LevelSmem(sizeof(T), L.win_max, L.max_box_rows).total;
 }
 
 }  // namespace r3mg

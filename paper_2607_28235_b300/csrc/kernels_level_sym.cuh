@@ -5,8 +5,8 @@
 // over a stored block serves both products it takes part in:
 //   y_B  += A_BB' x_B'             (row-wise, reduced across the CTA)
 //   t_BB' = A_BB'^T x_B            (column-wise, one b-vector per off-diagonal upper pair)
-// k_sym_block streams every stored block once (half the bytes of the full operator) with one
-// thread per 4 columns and all b rows in flight; k_sym_finish adds to each row the transposed
+// k_sym_block streams every stored block once (half the bytes of the full operator), one CTA
+// per box with one thread per 4 columns; k_sym_finish adds to each row the transposed
 // contributions of its lower neighbours, in increasing box order, and applies the fused
 // Chebyshev-Jacobi update.  Both passes are deterministic.
 #pragma once
@@ -34,71 +34,88 @@ struct SymView {
 
 constexpr int kSymMaxB = 32;
 
-// One warp per box (8 boxes per CTA, no CTA-wide barrier).  A pass gives each lane two 16-byte
-// column chunks of the box's upper rows and walks all b rows: the row partials of y stay in
-// the lane's registers (reduced across the warp at the end), the transposed sums t of the
-// lane's columns are complete after the pass and are written at once.
-__global__ void __launch_bounds__(256) k_sym_block(SymView V, const float* __restrict__ xin, float* __restrict__ ybuf,
-                                                   float* __restrict__ tbuf) {
-  extern __shared__ __align__(16) float swin_all[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* swin = swin_all + warp * V.win_max;
+// One CTA (128 threads) per box.  The box's upper window (x over the diagonal and upper
+// neighbour slots) is staged in shared memory; each thread owns 4 consecutive columns of the
+// box's upper rows (one 16-byte load per row, coalesced along the row), walks all b rows in
+// groups of 8 loads in flight, and keeps
+//   * the row partials y_q += A[q, cols] . x_win[cols] for every row q (registers), and
+//   * the column sums t_cols = sum_q A[q, cols] x_B[q] (A_BB'^T x_B for its upper slots).
+// The row partials are reduced across each warp by a halving exchange (31 shuffles leave lane q
+// with row q's warp sum) and across the 4 warps in a fixed order, so the result is deterministic.
+constexpr int kSymThreads = 128;
+static_assert(kSymMaxB == 32, "the halving exchange maps lane q to row q of up to 32 rows");
+
+__global__ void __launch_bounds__(kSymThreads) k_sym_block(SymView V, const float* __restrict__ xin,
+                                                          float* __restrict__ ybuf, float* __restrict__ tbuf) {
+  extern __shared__ __align__(16) float swin[];
+  __shared__ float ysum[kSymThreads / 32][32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = kSymThreads / 32;
   const int b = V.b;
-  for (int64_t B = (int64_t)blockIdx.x * 8 + warp; B < V.nbox; B += (int64_t)gridDim.x * 8) {
+  for (int64_t B = blockIdx.x; B < V.nbox; B += gridDim.x) {
     const int64_t q0 = V.nbr_ptr[B];
     const int nn = (int)(V.nbr_ptr[B + 1] - q0), d = V.dslot[B], nup = nn - d;
     const int W = nup * b, Wp = V.up_len[B];
-    for (int sI = 0; sI < nup; ++sI) {
+    for (int sI = warp; sI < nup; sI += NW) {
       const int64_t src = V.nbr[q0 + d + sI] * b;
       for (int t = lane; t < b; t += 32) cp_async_elem(swin + sI * b + t, xin + src + t);
     }
-    for (int t = W + lane; t < Wp; t += 32) swin[t] = 0.f;
+    for (int t = W + tid; t < Wp; t += kSymThreads) swin[t] = 0.f;
     cp_async_wait_all();
-    __syncwarp();
-    float yacc[kSymMaxB];
+    __syncthreads();
+    float yp[kSymMaxB];
 #pragma unroll
-    for (int q = 0; q < kSymMaxB; ++q) yacc[q] = 0.f;
+    for (int q = 0; q < kSymMaxB; ++q) yp[q] = 0.f;
     const float* base = V.vals + V.up_base[B];
-    const int nch = Wp >> 2;
-    for (int p0 = 0; p0 < nch; p0 += 64) {
-      const int c0 = p0 + lane, c1 = p0 + 32 + lane;
-      const bool v0 = c0 < nch, v1 = c1 < nch;
-      const float4 x0 = v0 ? *reinterpret_cast<const float4*>(swin + 4 * c0) : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 x1 = v1 ? *reinterpret_cast<const float4*>(swin + 4 * c1) : make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
+    const int64_t tp = V.tp_off[B];
+    for (int c4 = tid; 4 * c4 < Wp; c4 += kSymThreads) {
+      const float4 xw = *reinterpret_cast<const float4*>(swin + 4 * c4);
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < kSymMaxB; ++q) {
-        if (q < b) {
-          const float* row = base + (int64_t)q * Wp;
-          const float4 a0 = v0 ? __ldcs(reinterpret_cast<const float4*>(row + 4 * c0)) : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float4 a1 = v1 ? __ldcs(reinterpret_cast<const float4*>(row + 4 * c1)) : make_float4(0.f, 0.f, 0.f, 0.f);
-          yacc[q] += a0.x * x0.x + a0.y * x0.y + a0.z * x0.z + a0.w * x0.w + a1.x * x1.x + a1.y * x1.y + a1.z * x1.z +
-                     a1.w * x1.w;
-          const float xq = swin[q];   // x_B: the diagonal slot is the window's first segment
-          t0.x += a0.x * xq; t0.y += a0.y * xq; t0.z += a0.z * xq; t0.w += a0.w * xq;
-          t1.x += a1.x * xq; t1.y += a1.y * xq; t1.z += a1.z * xq; t1.w += a1.w * xq;
+      for (int q0r = 0; q0r < kSymMaxB; q0r += 8) {
+        if (q0r >= b) break;
+        float4 a[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          a[j] = (q0r + j < b) ? __ldcs(reinterpret_cast<const float4*>(base + (int64_t)(q0r + j) * Wp + 4 * c4))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int q = q0r + j;
+          yp[q] += a[j].x * xw.x + a[j].y * xw.y + a[j].z * xw.z + a[j].w * xw.w;
+          const float xq = (q < b) ? swin[q] : 0.f;   // x_B: the diagonal slot opens the window
+          t.x += a[j].x * xq; t.y += a[j].y * xq; t.z += a[j].z * xq; t.w += a[j].w * xq;
         }
       }
-      const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+      const float tv[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int c = 4 * (j < 4 ? c0 : c1) + (j & 3);
-        if (c >= b && c < W) {   // off-diagonal upper block: keep A_BB'^T x_B
+      for (int j = 0; j < 4; ++j) {
+        const int c = 4 * c4 + j;
+        if (c >= b && c < W) {   // an off-diagonal upper block: keep A_BB'^T x_B
           const int sI = c / b;
-          tbuf[(V.tp_off[B] + sI - 1) * b + (c - sI * b)] = tv[j];
+          tbuf[(tp + sI - 1) * b + (c - sI * b)] = tv[j];
         }
       }
     }
-    // y_B: reduce the lanes' row partials (fixed butterfly order)
+    // halving exchange: at each step a lane keeps the half of its values its lane bit selects
+    // and adds the partner's copy of that half; lane q ends with the warp's sum of row q
 #pragma unroll
-    for (int q = 0; q < kSymMaxB; ++q) {
-      if (q < b) {
-        float v = yacc[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) ybuf[B * b + q] = v;
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool hi = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < o; ++i) {
+        const float send = hi ? yp[i] : yp[i + o];
+        const float keep = hi ? yp[i + o] : yp[i];
+        yp[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
       }
     }
-    __syncwarp();
+    ysum[warp][lane] = yp[0];
+    __syncthreads();
+    if (tid < b) {
+      float y = 0.f;
+      for (int w = 0; w < NW; ++w) y += ysum[w][tid];
+      ybuf[B * b + tid] = y;
+    }
+    __syncthreads();   // the window and ysum are free for the next box
   }
 }
 

@@ -69,6 +69,7 @@ struct Level {
   // symmetric block form (coarse levels, FP32): upper blocks only
   SymView sym;
   bool sym_ok = false;
+  int64_t sym_nnz = 0, sym_tvals = 0;   // stored upper values (padding excluded); transposed-pair values
   float* sym_vals = nullptr;
   float* sym_y = nullptr;
   float* sym_t = nullptr;
@@ -264,22 +265,32 @@ constexpr int unroll_for() { return sizeof(T) == 4 ? 4 : 2; }
 
 template <typename T, int G, bool FINE, class Ep, int U>
 void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
-                     int pf, int nt);
+                     int pf, int nt, int sp);
 
 // FP64 rows may use 2 or 4 steps of 32 bytes in flight per lane (autotuned); FP32 uses 4 x 16 bytes
 template <typename T, int G, bool FINE, class Ep>
 void launch_level_g(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
-                    int pf, int nt, int u) {
-  if (sizeof(T) == 8 && u == 4) launch_level_gu<T, G, FINE, Ep, 4>(v, xin, ep, part, s, pipe, nsm, pf, nt);
-  else launch_level_gu<T, G, FINE, Ep, unroll_for<T, FINE>()>(v, xin, ep, part, s, pipe, nsm, pf, nt);
+                    int pf, int nt, int u, int sp) {
+  if (sizeof(T) == 8 && u == 4 && !sp) launch_level_gu<T, G, FINE, Ep, 4>(v, xin, ep, part, s, pipe, nsm, pf, nt, 0);
+  else launch_level_gu<T, G, FINE, Ep, unroll_for<T, FINE>()>(v, xin, ep, part, s, pipe, nsm, pf, nt, sp);
 }
 
 template <typename T, int G, bool FINE, class Ep, int U>
 void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, cudaStream_t s, int pipe, int nsm,
-                     int pf, int nt) {
+                     int pf, int nt, int sp) {
+  if constexpr (U == unroll_for<T, FINE>()) {
+    if (sp) {   // software-pipelined row loop, with or without the L2 prefetch
+      const size_t sm = level_smem_bytes(v);
+      auto kern = pf ? level_kernel<T, G, FINE, Ep, U, false, true, true> : level_kernel<T, G, FINE, Ep, U, false, false, true>;
+      ensure_smem((const void*)kern, sm);
+      kern<<<(int)std::max<int64_t>(1, v.nbox), nt, sm, s>>>(v, xin, ep, part);
+      CK(cudaGetLastError());
+      return;
+    }
+  }
   if (pf) {
     const size_t sm = level_smem_bytes(v);
-    auto kern = level_kernel<T, G, FINE, Ep, U, false, true>;
+    auto kern = level_kernel<T, G, FINE, Ep, U, false, true, false>;
     ensure_smem((const void*)kern, sm);
     kern<<<(int)std::max<int64_t>(1, v.nbox), nt, sm, s>>>(v, xin, ep, part);
     CK(cudaGetLastError());
@@ -288,7 +299,7 @@ void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, c
   if (pipe) {
     // persistent form: two windows per CTA, grid sized to the CTAs that fit the SMs
     const size_t sm = 2 * level_smem_bytes(v);
-    auto kern = level_kernel<T, G, FINE, Ep, U, true, false>;
+    auto kern = level_kernel<T, G, FINE, Ep, U, true, false, false>;
     ensure_smem((const void*)kern, sm);
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / nt, (kMaxSmem + 1024) / (sm + 1024)));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(v.nbox, (int64_t)nsm * per_sm));
@@ -297,7 +308,7 @@ void launch_level_gu(const LevelView<T>& v, const T* xin, Ep ep, double* part, c
     return;
   }
   const size_t sm = level_smem_bytes(v);
-  auto kern = level_kernel<T, G, FINE, Ep, U, false, false>;
+  auto kern = level_kernel<T, G, FINE, Ep, U, false, false, false>;
   // opt in to more than 48 KB of dynamic shared memory per instantiation (the setup's warm-up
   // V-cycle does this before any graph capture)
   ensure_smem((const void*)kern, sm);
@@ -311,12 +322,14 @@ int launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t
   const LevelView<T> v = view<T>(L);
   const bool fine = (L.b == 0);
   const Level::KConf& c = L.conf[sizeof(T) == 4 ? 1 : 0];
-  const int pipe = (c.form == 2), pf = (c.form == 3), nsm = L.nsm, nt = (c.nt == 128) ? 128 : 256, u = c.u;
+  // forms: 0 register, 2 persistent, 3 L2 prefetch, 5 software-pipelined, 6 pipelined + L2 prefetch
+  const int pipe = (c.form == 2), pf = (c.form == 3 || c.form == 6), sp = (c.form == 5 || c.form == 6);
+  const int nsm = L.nsm, nt = (c.nt == 128) ? 128 : 256, u = c.u;
   switch (c.G) {
-    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
-    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
-    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
-    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u) : launch_level_g<T, 32, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u); break;
+    case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
+    case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
+    case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
+    default: fine ? launch_level_g<T, 32, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 32, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
   }
   if (!pipe) return (int)std::max<int64_t>(1, v.nbox);
   const size_t sm = 2 * level_smem_bytes(v);
@@ -546,14 +559,16 @@ void build_sym(r3mg_hierarchy* h, Level& A) {
   V.vals = A.sym_vals;
   A.sym_y = dalloc<float>(h, A.n);
   A.sym_t = dalloc<float>(h, std::max<int64_t>(1, tp_off[nb] * b));
+  A.sym_nnz = 0;
+  for (int64_t B = 0; B < nb; ++B) A.sym_nnz += (int64_t)(A.pat.ptr[B + 1] - A.pat.ptr[B] - dslot[B]) * b * b;
+  A.sym_tvals = tp_off[nb] * b;
   A.sym_ok = true;
 }
 
 void sym_step(r3mg_hierarchy* h, const Level& A, const float* d, SymCheb ep) {
-  const size_t sm = sizeof(float) * 8 * (size_t)A.sym.win_max;
+  const size_t sm = sizeof(float) * (size_t)A.sym.win_max;
   ensure_smem((const void*)k_sym_block, sm);
-  k_sym_block<<<(int)std::max<int64_t>(1, (A.nbox + 7) / 8), 256, sizeof(float) * 8 * (size_t)A.sym.win_max,
-                h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
+  k_sym_block<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
   k_sym_finish<<<grid_for(A.n), 256, 0, h->stream>>>(A.sym, A.sym_y, A.sym_t, ep);
   CK(cudaGetLastError());
 }
@@ -881,6 +896,7 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
         cand.push_back({0, G, nt, 0.f, u});
         if (2 * level_smem_bytes(view<T>(A)) <= kMaxSmem) cand.push_back({2, G, nt, 0.f, u});
         cand.push_back({3, G, nt, 0.f, u});
+        if (u == 0) { cand.push_back({5, G, nt, 0.f, 0}); cand.push_back({6, G, nt, 0.f, 0}); }
       }
     if (A.tma[pi].nitems > 0)
       for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f, 0});
@@ -3212,8 +3228,15 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
         const Level& A = h->lv[kind - 1];
         const double es = f32 ? 4.0 : 8.0;
         const double ib = (A.b == 0) ? 2.0 : 0.0;
-        *bytes_per_launch = (double)A.nnz * (es + ib) + 8.0 * (A.n + 1) + (6.0 * cols + 1.0) * es * A.n +
-                            (A.b == 0 ? 0.0 : 8.0 * (double)A.npairs);
+        if (f32 && cols == 1.0 && A.conf[1].form == 4 && A.sym_ok) {
+          // symmetric block form: the upper blocks once, the transposed-pair values and the row
+          // sums written and read back, and the step's vectors
+          *bytes_per_launch = (double)A.sym_nnz * es + 2.0 * es * (double)A.sym_tvals + 2.0 * es * A.n +
+                              7.0 * es * A.n + 8.0 * (double)A.npairs;
+        } else {
+          *bytes_per_launch = (double)A.nnz * (es + ib) + 8.0 * (A.n + 1) + (6.0 * cols + 1.0) * es * A.n +
+                              (A.b == 0 ? 0.0 : 8.0 * (double)A.npairs);
+        }
       }
     }
   });
@@ -3240,9 +3263,9 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
     if (h) h->err = "set_kernel_config: unroll 4 is an FP64 option (0 = default)";
     return R3MG_E_ARG;
   }
-  if (!h || level < 0 || level >= h->L || form < 0 || form > 4 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
+  if (!h || level < 0 || level >= h->L || form < 0 || form > 6 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
       (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || (form == 1 && threads == 128)) {
-    if (h) h->err = "set_kernel_config: invalid level, form (0..3), lanes (4,8,16,32) or threads (128 register forms only, 256, 512, 1024)";
+    if (h) h->err = "set_kernel_config: invalid level, form (0..6), lanes (4,8,16,32) or threads (128 register forms only, 256, 512, 1024)";
     return R3MG_E_ARG;
   }
   Level& A = h->lv[level];
@@ -3263,7 +3286,8 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
   const Level::KConf& c = h->lv[level].conf[fp32 ? 1 : 0];
   const bool tma = c.form == 1 && h->lv[level].tma[fp32 ? 1 : 0].nitems > 0;
-  if (form) *form = tma ? 1 : (c.form == 2 || c.form == 3 || (c.form == 4 && h->lv[level].sym_ok) ? c.form : 0);
+  if (form)
+    *form = tma ? 1 : (c.form == 2 || c.form == 3 || c.form == 5 || c.form == 6 || (c.form == 4 && h->lv[level].sym_ok) ? c.form : 0);
   if (lanes) *lanes = c.G;
   if (threads) *threads = tma ? c.nt : (c.nt == 128 ? 128 : 256);
   if (tuned_ms) *tuned_ms = c.ms;

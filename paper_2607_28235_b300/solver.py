@@ -14,6 +14,11 @@ import torch
 from ._lib import R3MGError, _Params, lib
 
 
+# level-operator kernel forms, in the order of r3mg_kernel_config's codes
+FORMS = ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block", "register_pipelined",
+         "register_pipelined_l2_prefetch"]
+
+
 def _p(a) -> ctypes.c_void_p:
     if isinstance(a, torch.Tensor):
         return ctypes.c_void_p(a.data_ptr())
@@ -349,7 +354,7 @@ class Hierarchy:
                                                 ctypes.byref(ms)), self._h)
                 un = ctypes.c_int(0)
                 _check(lib().r3mg_kernel_unroll(self._h, lev, fp32, ctypes.byref(un)), self._h)
-                row[key] = {"form": ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block"][f.value], "lanes": g.value,
+                row[key] = {"form": FORMS[f.value], "lanes": g.value,
                             "threads": t.value, "unroll": un.value,
                             "tuned_ms": round(ms.value, 5)}
             out.append(row)
@@ -357,7 +362,7 @@ class Hierarchy:
 
     def set_kernel_config(self, config: list):
         """Replay a configuration returned by kernel_config() (same hierarchy shape)."""
-        forms = {"register": 0, "tma": 1, "register_persistent": 2, "register_l2_prefetch": 3, "symmetric_block": 4}
+        forms = {name: i for i, name in enumerate(FORMS)}
         for lev, row in enumerate(config):
             for fp32, key in ((0, "f64"), (1, "f32")):
                 if key not in row or (fp32 and self.params["precision"] != 1):

@@ -43,7 +43,8 @@ from tests.gpu_cases import CASES, make
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-FORMS = ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block"]
+FORMS = ["register", "tma", "register_persistent", "register_l2_prefetch", "register_pipelined",
+         "register_pipelined_l2_prefetch", "symmetric_block"]
 
 
 def _hier(P, params, precision=1, **kw):
@@ -82,7 +83,7 @@ def _row_len(A):
     return np.diff(sp.csr_matrix(A).indptr)
 
 
-@pytest.mark.parametrize("form", FORMS[:4])
+@pytest.mark.parametrize("form", FORMS[:-1])
 def test_fp32_level_product_rowwise_bound(case, form):
     P, params, Ho = case
     H = _hier(P, params)

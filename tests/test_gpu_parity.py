@@ -173,7 +173,8 @@ def test_kernel_forms_match_oracle(pair, form):
     Hf.close()
 
 
-@pytest.mark.parametrize("form", ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block"])
+@pytest.mark.parametrize("form", ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block",
+                                  "register_pipelined", "register_pipelined_l2_prefetch"])
 def test_set_kernel_config_each_form(pair, form):
     """Every kernel form, pinned through r3mg_set_kernel_config, gives a converged mixed-precision
     PCG (the symmetric block form exists on coarse FP32 levels only)."""
