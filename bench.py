@@ -272,16 +272,31 @@ def run_batch(args):
                          precision=1)
     t_setup = time.perf_counter() - t0
     b = torch.tensor(np.concatenate(rhs), device="cuda")
-    for _ in range(args.warmup):
-        H.pcg(b, rtol=w["rtol"])
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        x, its, rel = H.pcg(b, rtol=w["rtol"])
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+
+    def timed_mode(mode):
+        H.set_batch_mode(mode)
+        for _ in range(args.warmup):
+            H.pcg(b, rtol=w["rtol"])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            out = H.pcg(b, rtol=w["rtol"])
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, out
+
+    # the loop as a graph of per-step kernels (mode 0) and as one persistent kernel (mode 1);
+    # the faster is the one the line reports
+    mode_ms = {}
+    outs = {}
+    for mode in (0, 1):
+        mode_ms[mode], outs[mode] = timed_mode(mode)
+    best = min(mode_ms, key=mode_ms.get)
+    H.set_batch_mode(best)
+    ms = mode_ms[best]
+    x, its, rel = outs[best]
+    same_bits = bool(torch.equal(outs[0][0], outs[1][0]))
     xs = x.cpu().numpy()
     off = H.level_offsets(0)
     chk = max(float(np.linalg.norm(rhs[k] - probs[k].scipy() @ xs[off[k]:off[k + 1]]) / np.linalg.norm(rhs[k]))
@@ -320,9 +335,13 @@ def run_batch(args):
                        "dofs_min": int(min(P.n for P in probs)), "dofs_max": int(max(P.n for P in probs)),
                        "nnz_total": int(sum(P.nnz for P in probs)), "leaf_size": w["leaf_size"], "pprime": w["pprime"],
                        "levels": w["levels"], "precision": "FP32 V-cycle in FP64 flexible CG",
-                       "loop": "one CUDA graph launch (conditional WHILE node)"},
+                       "loop": "one graph launch: conditional WHILE over per-step kernels, or one persistent "
+                               "cooperative kernel (the faster of the two, loop_mode)"},
             "iterations": {"min": int(its.min()), "max": int(its.max()), "mean": float(its.mean())},
             "max_true_relres": chk, "dofs_per_s": H.n / (ms * 1e-3),
+            "loop_modes_ms": {"graph_of_kernels": mode_ms[0], "persistent_kernel": mode_ms[1]},
+            "loop_mode": ["graph_of_kernels", "persistent_kernel"][best],
+            "modes_same_solution_bits": same_bits,
             "setup_s": t_setup, "assembly_s": t_asm,
             "roofline": {"bound": "hbm", "kernel": f"batched_{top}_f32", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
@@ -662,18 +681,20 @@ def run_ours(args):
         cfg = json.load(open(args.kernel_config))
         Hm.set_kernel_config(cfg["mixed"])
         Hd.set_kernel_config(cfg["fp64"])
-    for pin in args.pin_form or []:
-        # level:form[:lanes[:threads]] pins the FP32 kernel of one level of the mixed hierarchy
-        parts = pin.split(":")
-        lev = int(parts[0])
-        cfg = Hm.kernel_config()
-        row = cfg[lev]["f32"]
-        row["form"] = parts[1]
-        if len(parts) > 2:
-            row["lanes"] = int(parts[2])
-        if len(parts) > 3:
-            row["threads"] = int(parts[3])
-        Hm.set_kernel_config(cfg[:-1])
+    for pins, H, key in ((args.pin_form, Hm, "f32"), (args.pin_form64, Hd, "f64")):
+        for pin in pins or []:
+            # level:form[:lanes[:threads]] pins the level kernel of one level (FP32 of the mixed
+            # hierarchy, or FP64 of the FP64 hierarchy)
+            parts = pin.split(":")
+            lev = int(parts[0])
+            cfg = H.kernel_config()
+            row = cfg[lev][key]
+            row["form"] = parts[1]
+            if len(parts) > 2:
+                row["lanes"] = int(parts[2])
+            if len(parts) > 3:
+                row["threads"] = int(parts[3])
+            H.set_kernel_config(cfg[:-1])
     if args.save_config:
         os.makedirs(os.path.dirname(os.path.abspath(args.save_config)), exist_ok=True)
         json.dump({"mixed": Hm.kernel_config(), "fp64": Hd.kernel_config()}, open(args.save_config, "w"))
@@ -777,7 +798,9 @@ def run_ours(args):
         "iterations": its_m[-1], "relres_check": chk_m,
         "fp64": {"ms": ms_fp64, "iterations": its_d[-1], "relres_check": chk_d,
                  "top_kernel": top_d, "top_kernel_avg_ms": avg_d,
-                 "top_kernel_achieved_gbs": td["bytes_per_launch"] / (avg_d * 1e-3) / 1e9},
+                 "top_kernel_achieved_gbs": td["bytes_per_launch"] / (avg_d * 1e-3) / 1e9,
+                 "kernel_config": [row["f64"] for row in Hd.kernel_config()],
+                 "kernel_ms": {k: v["ms"] / max(v["launches"], 1) for k, v in kinds_d.items()}},
         "mixed_vs_fp64_speedup": ms_fp64 / ms_mixed, "mixed_vs_fp64_solution_reldiff": diff_md,
         "paper_diagnostics": diag,
         "setup_s": {"mixed": setup_mixed_s, "fp64": setup_fp64_s},
@@ -811,6 +834,8 @@ def main():
     ap.add_argument("--kernel-config", default=None, help="replay a saved kernel configuration (JSON)")
     ap.add_argument("--pin-form", action="append", default=None,
                     help="level:form[:lanes[:threads]]: pin the FP32 level kernel of one level (repeatable)")
+    ap.add_argument("--pin-form64", action="append", default=None,
+                    help="level:form[:lanes[:threads]]: pin the FP64 level kernel of one level (repeatable)")
     ap.add_argument("--ncu-region", default="mixed", choices=["mixed", "fp64"],
                     help="which profiled pass lies between cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--workload", default="full", choices=["full", "small", "cells", "batch256", "rhs16",

@@ -387,13 +387,30 @@ r3mg_status r3mg_device_status(r3mg_hierarchy* h, void* stream);
 r3mg_status r3mg_set_coarse_mode(r3mg_hierarchy* h, int mode);
 
 /*
+ * Execution of r3mg_batch_pcg's iteration loop on a batched hierarchy.  mode 0 (default): one
+ * CUDA graph launch whose conditional WHILE node repeats a batched iteration, each V-cycle step,
+ * transfer, dot and update of all problems being one kernel.  mode 1: one persistent cooperative
+ * kernel (captured in a CUDA graph when the driver allows it) runs the whole loop: its CTAs, all
+ * resident at once, walk the same phases in the same order of rounding, separated by a grid
+ * barrier whose waits are bounded (r3mg_set_wait_limit; on expiry the kernel returns and the
+ * solve reports R3MG_E_TIMEOUT), and skip the work of problems that have stopped.  Every
+ * problem's iterates are the same in both modes.  Level kernels run in the register form with the
+ * lanes per row tuned for each level.  Errors: R3MG_E_ARG (not a batched hierarchy),
+ * R3MG_E_LIMIT (more than 8 levels).
+ */
+r3mg_status r3mg_set_batch_mode(r3mg_hierarchy* h, int mode);
+
+/*
  * Limit of the bounded mbarrier waits of the copy-engine-streamed kernels on this hierarchy:
  * cycles = clock64 cycles per wait (0 = the default, about one second at 2 GHz; at most 4e9).
+ * The same limit bounds the grid-barrier waits of the persistent batched solve.
  * withhold_first_copy = 1 is the library's test of the expiry path: CTA 0 of the TMA level
  * kernel announces its first descriptor copy on its mbarrier but never issues it, so that wait
  * runs out; the kernel then raises the flag, waits (bounded) for the copies it did issue, and
- * returns, and r3mg_device_status reports R3MG_E_TIMEOUT.  0 in normal use.  Drops captured
- * graphs; synchronises.  Errors: R3MG_E_ARG.
+ * returns, and r3mg_device_status reports R3MG_E_TIMEOUT.  In the persistent batched solve CTA 0
+ * withholds its arrival at the first grid barrier, so every CTA's wait runs out and the solve
+ * returns R3MG_E_TIMEOUT.  0 in normal use.  Drops captured graphs; synchronises.
+ * Errors: R3MG_E_ARG.
  */
 r3mg_status r3mg_set_wait_limit(r3mg_hierarchy* h, long long cycles, int withhold_first_copy);
 

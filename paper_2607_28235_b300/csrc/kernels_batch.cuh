@@ -39,17 +39,19 @@ struct NextInitB {
   }
 };
 
-// Block-diagonal coarsest solve: row r of problem p uses its own dense inverse.
+// Block-diagonal coarsest solve: row r of problem p uses its own dense inverse (rows of stopped
+// problems skipped when `act` is given).
 template <typename T>
-__global__ void __launch_bounds__(256) k_block_gemv(const T* __restrict__ M, const int64_t* __restrict__ moff,
-                                                    const int64_t* __restrict__ mld, const int64_t* __restrict__ cof,
-                                                    const int32_t* __restrict__ rprob, const T* __restrict__ r,
-                                                    int64_t nrows, T* __restrict__ x) {
+__device__ __forceinline__ void block_gemv_body(const T* __restrict__ M, const int64_t* __restrict__ moff,
+                                                const int64_t* __restrict__ mld, const int64_t* __restrict__ cof,
+                                                const int32_t* __restrict__ rprob, const T* __restrict__ r,
+                                                int64_t nrows, T* __restrict__ x, const int* act) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = w; row < nrows; row += nw) {
     const int p = rprob[row];
+    if (act && !act[p]) continue;   // uniform across the warp (one row per warp)
     const int64_t c0 = cof[p], nc = cof[p + 1] - c0, ld = mld[p];
     const T* a = M + moff[p] + (row - c0) * ld;
     T s = T(0);
@@ -57,6 +59,14 @@ __global__ void __launch_bounds__(256) k_block_gemv(const T* __restrict__ M, con
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) x[row] = s;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_block_gemv(const T* __restrict__ M, const int64_t* __restrict__ moff,
+                                                    const int64_t* __restrict__ mld, const int64_t* __restrict__ cof,
+                                                    const int32_t* __restrict__ rprob, const T* __restrict__ r,
+                                                    int64_t nrows, T* __restrict__ x) {
+  block_gemv_body<T>(M, moff, mld, cof, rprob, r, nrows, x, nullptr);
 }
 
 // Segmented dot products: segment s covers rows [sb[s], se[s]) of one problem.

@@ -196,171 +196,187 @@ struct Chunk {
   }
 };
 
+// ---- one box of a level step, as device functions shared by the level kernels and the
+// persistent batched solve.  A box is staged (window, own-row vectors, row bounds) into one
+// shared-memory stage, then its rows are computed from it.
+template <typename T, bool FINE>
+__device__ __forceinline__ void level_box_rows(const LevelView<T>& L, int64_t B, int64_t& r0, int64_t& r1) {
+  if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
+  else { r0 = B * L.b; r1 = r0 + L.b; }
+}
+
+// the box's matrix slice is contiguous: one thread asks the copy engine to pull it into L2
+template <typename T, bool FINE>
+__device__ __forceinline__ void level_prefetch(const LevelView<T>& L, int64_t B) {
+  if (threadIdx.x == 0) {
+    int64_t r0, r1;
+    level_box_rows<T, FINE>(L, B, r0, r1);
+    const int64_t k0 = L.row_ptr[r0], k1 = L.row_ptr[r1];
+    bulk_prefetch_l2(L.vals, k0 * (int64_t)sizeof(T), k1 * (int64_t)sizeof(T));
+    if constexpr (FINE) bulk_prefetch_l2(L.idx, k0 * 2, k1 * 2);
+  }
+}
+
+// window staging: one warp per neighbour slot, asynchronous global->shared copies (cp.async)
+// so every element of the window is in flight at once; then the epilogue's own-row vectors and
+// the rows' bounds, so no row waits on a dependent global load.  Completed by cp_async_wait_*.
+template <typename T, bool FINE, class Ep>
+__device__ __forceinline__ void level_stage(const LevelView<T>& L, const T* __restrict__ xin, const Ep& ep,
+                                            const LevelSmem& lay, int64_t B, unsigned char* base) {
+  const int NW = blockDim.x >> 5, warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+  T* win = reinterpret_cast<T*>(base);
+  const int64_t e0 = L.nbr_ptr[B];
+  const int nn = (int)(L.nbr_ptr[B + 1] - e0);
+  int W;
+  if constexpr (FINE) {
+    W = L.win_size[B];
+    for (int s = warp; s < nn; s += NW) {
+      const int wo = L.win_off[e0 + s];
+      const int64_t src = L.slot_src[e0 + s];
+      const int len = (s + 1 < nn ? L.win_off[e0 + s + 1] : W) - wo;
+      for (int t = wl; t < len; t += 32) cp_async_elem(win + wo + t, xin + src + t);
+    }
+  } else {
+    const int b = L.b;
+    W = nn * b;
+    for (int s = warp; s < nn; s += NW) {
+      const int64_t src = L.nbr[e0 + s] * b;
+      for (int t = wl; t < b; t += 32) cp_async_elem(win + s * b + t, xin + src + t);
+    }
+  }
+  const int Wp = (W + 3) & ~3;
+  for (int k = W + threadIdx.x; k < Wp; k += blockDim.x) win[k] = T(0);
+  int64_t r0, r1;
+  level_box_rows<T, FINE>(L, B, r0, r1);
+  T* aux = reinterpret_cast<T*>(base + lay.aux);
+  const int nr = (int)(r1 - r0);
+  for (int j = 0; j < Ep::kStage; ++j) {
+    if (!ep.stage(j)) continue;
+    const T* sp = ep.src(j);
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) cp_async_elem(aux + j * L.max_box_rows + t, sp + r0 + t);
+  }
+  int64_t* rp = reinterpret_cast<int64_t*>(base + lay.rp);
+  for (int t = threadIdx.x; t <= nr; t += blockDim.x) cp_async_elem(rp + t, L.row_ptr + r0 + t);
+  if (FINE && L.row_order) {
+    int32_t* od = reinterpret_cast<int32_t*>(base + lay.ord);
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) cp_async_elem(od + t, L.row_order + r0 + t);
+  }
+}
+
+// The rows of a staged box: groups of G lanes per row, U steps of 4 entries per lane in flight;
+// SP: software-pipelined row loop (the next chunk -- of the same row, or the group's next row --
+// is loaded into registers before the current chunk is consumed, so loads stay in flight through
+// the arithmetic, the group reduction and the epilogue).
+template <typename T, int G, bool FINE, class Ep, int U, bool SP>
+__device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& ep, const LevelSmem& lay, int64_t B,
+                                              unsigned char* base, double& acc) {
+  const int NG = blockDim.x / G;
+  const int g = threadIdx.x / G, lane = threadIdx.x % G;
+  const T* win = reinterpret_cast<const T*>(base);
+  int64_t r0, r1;
+  level_box_rows<T, FINE>(L, B, r0, r1);
+  const int nr = (int)(r1 - r0);
+  T* auxp[kAuxMax];
+  for (int j = 0; j < kAuxMax; ++j) auxp[j] = reinterpret_cast<T*>(base + lay.aux) + j * L.max_box_rows;
+  const int64_t* rp = reinterpret_cast<const int64_t*>(base + lay.rp);
+  const int32_t* od = reinterpret_cast<const int32_t*>(base + lay.ord);
+  // local row of this group at row-loop iteration `it` (-1 past the box's end); rows are
+  // taken longest first on the fine level (host-built order) so the groups finish together
+  auto row_at = [&](int it) -> int {
+    const int i = it * NG + g;
+    if (i >= nr) return -1;
+    return (FINE && L.row_order) ? od[i] : i;
+  };
+  // warp-uniform trip count: every lane of a warp runs the same iterations so the
+  // group shuffles always see the full warp; rows past the box end are masked.
+  const int g_first = (threadIdx.x >> 5) * (32 / G);
+  const int nit = (nr > g_first) ? (nr - g_first + NG - 1) / NG : 0;
+  if constexpr (!SP) {
+    for (int it = 0; it < nit; ++it) {
+      const int lr = row_at(it);
+      int64_t k0 = 0, k1 = 0;
+      if (lr >= 0) { k0 = rp[lr]; k1 = rp[lr + 1]; }
+      T a[2] = {T(0), T(0)};
+      // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
+      for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G * U) {
+        Chunk<T, U, FINE> c;
+        c.load(L.vals, L.idx, k, k0, k1, G);
+        c.consume(win, a);
+      }
+      const T s = group_sum<G>(a[0] + a[1]);
+      if (lr >= 0 && lane == 0) ep.post(r0 + lr, lr, s, auxp, acc);
+    }
+  } else {
+    int lr = row_at(0);
+    int64_t k0 = 0, k1 = 0;
+    if (lr >= 0) { k0 = rp[lr]; k1 = rp[lr + 1]; }
+    int64_t k = k0 + 4 * lane;
+    Chunk<T, U, FINE> cur;
+    if (nit > 0) cur.load(L.vals, L.idx, k, k0, k1, G);
+    for (int it = 0; it < nit; ++it) {
+      T a[2] = {T(0), T(0)};
+      const int lr_now = lr;
+      while (true) {
+        // the next chunk: further along this row, or the first of the group's next row
+        const bool same = k + 4 * G * U < k1;
+        int64_t nk, nk0 = k0, nk1 = k1;
+        int nlr = lr;
+        if (same) {
+          nk = k + 4 * G * U;
+        } else {
+          nlr = (it + 1 < nit) ? row_at(it + 1) : -1;
+          nk0 = 0; nk1 = 0;
+          if (nlr >= 0) { nk0 = rp[nlr]; nk1 = rp[nlr + 1]; }
+          nk = nk0 + 4 * lane;
+        }
+        Chunk<T, U, FINE> nxt;
+        nxt.load(L.vals, L.idx, nk, nk0, nk1, G);   // loads nothing past the row's end
+        cur.consume(win, a);
+        cur = nxt;
+        k = nk;
+        if (!same) { lr = nlr; k0 = nk0; k1 = nk1; break; }
+      }
+      const T s = group_sum<G>(a[0] + a[1]);
+      if (lr_now >= 0 && lane == 0) ep.post(r0 + lr_now, lr_now, s, auxp, acc);
+    }
+  }
+}
+
 // PIPE: persistent CTAs with two stages (the next box staged while the current one computes).
-// PF: an L2 bulk prefetch of each box's matrix slice.  SP: software-pipelined row loop (the
-// next chunk -- of the same row, or the group's next row -- is loaded into registers before the
-// current chunk is consumed, so loads stay in flight through the arithmetic, the group
-// reduction and the epilogue).
+// PF: an L2 bulk prefetch of each box's matrix slice.  SP: software-pipelined row loop.
 template <typename T, int G, bool FINE, class Ep, int U, bool PIPE, bool PF, bool SP>
 __global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __restrict__ xin, Ep ep,
                                                     double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8];
-  const int NG = blockDim.x / G, NW = blockDim.x >> 5;   // 128 or 256 threads
-  const int g = threadIdx.x / G, lane = threadIdx.x % G;
-  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
   const LevelSmem lay(sizeof(T), L.win_max, L.max_box_rows);
   double acc = 0.0;
-  auto box_rows = [&](int64_t B, int64_t& r0, int64_t& r1) {
-    if constexpr (FINE) { r0 = L.box_row[B]; r1 = L.box_row[B + 1]; }
-    else { r0 = B * L.b; r1 = r0 + L.b; }
-  };
-  // the box's matrix slice is contiguous: one thread asks the copy engine to pull it into L2
-  auto prefetch = [&](int64_t B) {
-    if (threadIdx.x == 0) {
-      int64_t r0, r1;
-      box_rows(B, r0, r1);
-      const int64_t k0 = L.row_ptr[r0], k1 = L.row_ptr[r1];
-      bulk_prefetch_l2(L.vals, k0 * (int64_t)sizeof(T), k1 * (int64_t)sizeof(T));
-      if constexpr (FINE) bulk_prefetch_l2(L.idx, k0 * 2, k1 * 2);
-    }
-  };
-  // window staging: one warp per neighbour slot, asynchronous global->shared copies
-  // (cp.async) so every element of the window is in flight at once
-  auto stage = [&](int64_t B, unsigned char* base) {
-    T* win = reinterpret_cast<T*>(base);
-    const int64_t e0 = L.nbr_ptr[B];
-    const int nn = (int)(L.nbr_ptr[B + 1] - e0);
-    int W;
-    if constexpr (FINE) {
-      W = L.win_size[B];
-      for (int s = warp; s < nn; s += NW) {
-        const int wo = L.win_off[e0 + s];
-        const int64_t src = L.slot_src[e0 + s];
-        const int len = (s + 1 < nn ? L.win_off[e0 + s + 1] : W) - wo;
-        for (int t = wl; t < len; t += 32) cp_async_elem(win + wo + t, xin + src + t);
-      }
-    } else {
-      const int b = L.b;
-      W = nn * b;
-      for (int s = warp; s < nn; s += NW) {
-        const int64_t src = L.nbr[e0 + s] * b;
-        for (int t = wl; t < b; t += 32) cp_async_elem(win + s * b + t, xin + src + t);
-      }
-    }
-    const int Wp = (W + 3) & ~3;
-    for (int k = W + threadIdx.x; k < Wp; k += blockDim.x) win[k] = T(0);
-    // the epilogue's own-row vectors and the rows' bounds, so no row waits on a dependent
-    // global load
-    int64_t r0, r1;
-    box_rows(B, r0, r1);
-    T* aux = reinterpret_cast<T*>(base + lay.aux);
-    const int nr = (int)(r1 - r0);
-    for (int j = 0; j < Ep::kStage; ++j) {
-      if (!ep.stage(j)) continue;
-      const T* sp = ep.src(j);
-      for (int t = threadIdx.x; t < nr; t += blockDim.x) cp_async_elem(aux + j * L.max_box_rows + t, sp + r0 + t);
-    }
-    int64_t* rp = reinterpret_cast<int64_t*>(base + lay.rp);
-    for (int t = threadIdx.x; t <= nr; t += blockDim.x) cp_async_elem(rp + t, L.row_ptr + r0 + t);
-    if (FINE && L.row_order) {
-      int32_t* od = reinterpret_cast<int32_t*>(base + lay.ord);
-      for (int t = threadIdx.x; t < nr; t += blockDim.x) cp_async_elem(od + t, L.row_order + r0 + t);
-    }
-  };
-  auto compute = [&](int64_t B, unsigned char* base) {
-    const T* win = reinterpret_cast<const T*>(base);
-    int64_t r0, r1;
-    box_rows(B, r0, r1);
-    const int nr = (int)(r1 - r0);
-    T* auxp[kAuxMax];
-    for (int j = 0; j < kAuxMax; ++j) auxp[j] = reinterpret_cast<T*>(base + lay.aux) + j * L.max_box_rows;
-    const int64_t* rp = reinterpret_cast<const int64_t*>(base + lay.rp);
-    const int32_t* od = reinterpret_cast<const int32_t*>(base + lay.ord);
-    // local row of this group at row-loop iteration `it` (-1 past the box's end); rows are
-    // taken longest first on the fine level (host-built order) so the groups finish together
-    auto row_at = [&](int it) -> int {
-      const int i = it * NG + g;
-      if (i >= nr) return -1;
-      return (FINE && L.row_order) ? od[i] : i;
-    };
-    // warp-uniform trip count: every lane of a warp runs the same iterations so the
-    // group shuffles always see the full warp; rows past the box end are masked.
-    const int g_first = (threadIdx.x >> 5) * (32 / G);
-    const int nit = (nr > g_first) ? (nr - g_first + NG - 1) / NG : 0;
-    if constexpr (!SP) {
-      for (int it = 0; it < nit; ++it) {
-        const int lr = row_at(it);
-        int64_t k0 = 0, k1 = 0;
-        if (lr >= 0) { k0 = rp[lr]; k1 = rp[lr + 1]; }
-        T a[2] = {T(0), T(0)};
-        // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
-        for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G * U) {
-          Chunk<T, U, FINE> c;
-          c.load(L.vals, L.idx, k, k0, k1, G);
-          c.consume(win, a);
-        }
-        const T s = group_sum<G>(a[0] + a[1]);
-        if (lr >= 0 && lane == 0) ep.post(r0 + lr, lr, s, auxp, acc);
-      }
-    } else {
-      int lr = row_at(0);
-      int64_t k0 = 0, k1 = 0;
-      if (lr >= 0) { k0 = rp[lr]; k1 = rp[lr + 1]; }
-      int64_t k = k0 + 4 * lane;
-      Chunk<T, U, FINE> cur;
-      if (nit > 0) cur.load(L.vals, L.idx, k, k0, k1, G);
-      for (int it = 0; it < nit; ++it) {
-        T a[2] = {T(0), T(0)};
-        const int lr_now = lr;
-        while (true) {
-          // the next chunk: further along this row, or the first of the group's next row
-          const bool same = k + 4 * G * U < k1;
-          int64_t nk, nk0 = k0, nk1 = k1;
-          int nlr = lr;
-          if (same) {
-            nk = k + 4 * G * U;
-          } else {
-            nlr = (it + 1 < nit) ? row_at(it + 1) : -1;
-            nk0 = 0; nk1 = 0;
-            if (nlr >= 0) { nk0 = rp[nlr]; nk1 = rp[nlr + 1]; }
-            nk = nk0 + 4 * lane;
-          }
-          Chunk<T, U, FINE> nxt;
-          nxt.load(L.vals, L.idx, nk, nk0, nk1, G);   // loads nothing past the row's end
-          cur.consume(win, a);
-          cur = nxt;
-          k = nk;
-          if (!same) { lr = nlr; k0 = nk0; k1 = nk1; break; }
-        }
-        const T s = group_sum<G>(a[0] + a[1]);
-        if (lr_now >= 0 && lane == 0) ep.post(r0 + lr_now, lr_now, s, auxp, acc);
-      }
-    }
-  };
   unsigned char* base0 = smem_raw;
   if constexpr (!PIPE) {
     for (int64_t B = blockIdx.x; B < L.nbox; B += gridDim.x) {
-      if (PF) prefetch(B);
-      stage(B, base0);
+      if (PF) level_prefetch<T, FINE>(L, B);
+      level_stage<T, FINE, Ep>(L, xin, ep, lay, B, base0);
       cp_async_wait_all();
       __syncthreads();
-      compute(B, base0);
+      level_compute<T, G, FINE, Ep, U, SP>(L, ep, lay, B, base0, acc);
       __syncthreads();
     }
   } else {
     // persistent CTAs: the next box's window is staged while the current box computes
     unsigned char* base1 = smem_raw + lay.total;
     int64_t B = blockIdx.x;
-    if (B < L.nbox) { if (PF) prefetch(B); stage(B, base0); }
+    if (B < L.nbox) { if (PF) level_prefetch<T, FINE>(L, B); level_stage<T, FINE, Ep>(L, xin, ep, lay, B, base0); }
     cp_async_commit_group();
     for (int k = 0; B < L.nbox; B += gridDim.x, ++k) {
       const int64_t nxt = B + gridDim.x;
-      if (nxt < L.nbox) { if (PF) prefetch(nxt); stage(nxt, (k & 1) ? base0 : base1); }
+      if (nxt < L.nbox) {
+        if (PF) level_prefetch<T, FINE>(L, nxt);
+        level_stage<T, FINE, Ep>(L, xin, ep, lay, nxt, (k & 1) ? base0 : base1);
+      }
       cp_async_commit_group();
       cp_async_wait_group1();
       __syncthreads();
-      compute(B, (k & 1) ? base1 : base0);
+      level_compute<T, G, FINE, Ep, U, SP>(L, ep, lay, B, (k & 1) ? base1 : base0, acc);
       __syncthreads();
     }
   }

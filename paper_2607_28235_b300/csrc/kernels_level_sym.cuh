@@ -140,7 +140,15 @@ __global__ void k_sym_finish(SymView V, const float* __restrict__ ybuf, const fl
     const int64_t B = i / V.b;
     const int q = (int)(i - B * V.b);
     float y = ybuf[i];
-    for (int64_t k = V.low_ptr[B]; k < V.low_ptr[B + 1]; ++k) y += tbuf[V.low_pair[k] * V.b + q];
+    const int64_t k0 = V.low_ptr[B], k1 = V.low_ptr[B + 1];
+    int64_t k = k0;
+    // four independent loads in flight, added in increasing pair order (deterministic)
+    for (; k + 4 <= k1; k += 4) {
+      const float t0 = tbuf[V.low_pair[k] * V.b + q], t1 = tbuf[V.low_pair[k + 1] * V.b + q];
+      const float t2 = tbuf[V.low_pair[k + 2] * V.b + q], t3 = tbuf[V.low_pair[k + 3] * V.b + q];
+      y += t0; y += t1; y += t2; y += t3;
+    }
+    for (; k < k1; ++k) y += tbuf[V.low_pair[k] * V.b + q];
     ep(i, y);
   }
 }

@@ -18,15 +18,23 @@ struct NextInit {
   }
 };
 
+// The transfer kernels' bodies are device functions so that the persistent batched solve runs
+// the same code; `rprob`/`act` (both null in the plain kernels) skip the rows of problems that
+// have stopped.
+__device__ __forceinline__ bool skip_row(const int32_t* rprob, const int* act, int64_t row) {
+  return act != nullptr && !act[rprob[row]];
+}
+
 // Fine -> level 1: b1[B*b + q] = sum_{i in B} P0[i][q] r[i].  One CTA per box.
 template <typename T, class NX>
-__global__ void __launch_bounds__(256) k_restrict_fine(const T* __restrict__ P0, const T* __restrict__ r,
-                                                       const int64_t* __restrict__ box_row, int64_t nbox, int b,
-                                                       NX nx) {
+__device__ __forceinline__ void restrict_fine_body(const T* __restrict__ P0, const T* __restrict__ r,
+                                                   const int64_t* __restrict__ box_row, int64_t nbox, int b, NX nx,
+                                                   const int32_t* rprob1, const int* act) {
   __shared__ T part[256];
   const int per = blockDim.x / b;   // row lanes per coefficient (b <= 256)
   const int q = threadIdx.x % b, j = threadIdx.x / b;
   for (int64_t B = blockIdx.x; B < nbox; B += gridDim.x) {
+    if (skip_row(rprob1, act, B * b)) continue;   // uniform across the CTA
     T s = T(0);
     if (j < per)
       for (int64_t i = box_row[B] + j; i < box_row[B + 1]; i += per) s += P0[i * b + q] * r[i];
@@ -41,12 +49,21 @@ __global__ void __launch_bounds__(256) k_restrict_fine(const T* __restrict__ P0,
   }
 }
 
+template <typename T, class NX>
+__global__ void __launch_bounds__(256) k_restrict_fine(const T* __restrict__ P0, const T* __restrict__ r,
+                                                       const int64_t* __restrict__ box_row, int64_t nbox, int b,
+                                                       NX nx) {
+  restrict_fine_body<T, NX>(P0, r, box_row, nbox, b, nx, nullptr, nullptr);
+}
+
 // Level l -> l+1 (l >= 1): b_{l+1}[B][q] = sum_{children c} sum_{q'} Pt[c][q'][q] r_l[c][q'].
 template <typename T, class NX>
-__global__ void k_restrict_coarse(const T* __restrict__ Pt, const T* __restrict__ r, int64_t nparent, int b, int fan,
-                                  NX nx) {
+__device__ __forceinline__ void restrict_coarse_body(const T* __restrict__ Pt, const T* __restrict__ r,
+                                                     int64_t nparent, int b, int fan, NX nx, int64_t t0, int64_t ts,
+                                                     const int32_t* rprob1, const int* act) {
   const int64_t tot = nparent * b;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = t0; t < tot; t += ts) {
+    if (skip_row(rprob1, act, t)) continue;
     const int64_t B = t / b;
     const int q = (int)(t - B * b);
     T s = T(0);
@@ -56,11 +73,21 @@ __global__ void k_restrict_coarse(const T* __restrict__ Pt, const T* __restrict_
   }
 }
 
+template <typename T, class NX>
+__global__ void k_restrict_coarse(const T* __restrict__ Pt, const T* __restrict__ r, int64_t nparent, int b, int fan,
+                                  NX nx) {
+  restrict_coarse_body<T, NX>(Pt, r, nparent, b, fan, nx, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                              (int64_t)gridDim.x * blockDim.x, nullptr, nullptr);
+}
+
 // Level 1 -> fine: d0[k] = sum_q P0[k][q] (x1 + d1)[box(k)*b + q]   (d1 may be null).
 template <typename T>
-__global__ void k_prolong_fine(const T* __restrict__ P0, const int32_t* __restrict__ box_of, const T* __restrict__ x1,
-                               const T* __restrict__ d1, int64_t n, int b, T* __restrict__ d0) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void prolong_fine_body(const T* __restrict__ P0, const int32_t* __restrict__ box_of,
+                                                  const T* __restrict__ x1, const T* __restrict__ d1, int64_t n, int b,
+                                                  T* __restrict__ d0, int64_t k0, int64_t ks, const int32_t* rprob,
+                                                  const int* act) {
+  for (int64_t k = k0; k < n; k += ks) {
+    if (skip_row(rprob, act, k)) continue;
     const int64_t B = box_of[k];
     T s = T(0);
     for (int q = 0; q < b; ++q) {
@@ -71,11 +98,21 @@ __global__ void k_prolong_fine(const T* __restrict__ P0, const int32_t* __restri
   }
 }
 
+template <typename T>
+__global__ void k_prolong_fine(const T* __restrict__ P0, const int32_t* __restrict__ box_of, const T* __restrict__ x1,
+                               const T* __restrict__ d1, int64_t n, int b, T* __restrict__ d0) {
+  prolong_fine_body<T>(P0, box_of, x1, d1, n, b, d0, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                       (int64_t)gridDim.x * blockDim.x, nullptr, nullptr);
+}
+
 // Level l+1 -> l: d_l[c][q'] = sum_q Pt[c][q'][q] (x + d)_{l+1}[parent(c)][q].
 template <typename T>
-__global__ void k_prolong_coarse(const T* __restrict__ Pt, const T* __restrict__ x1, const T* __restrict__ d1,
-                                 int64_t nchild, int b, int fan, T* __restrict__ d0) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nchild * b; t += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void prolong_coarse_body(const T* __restrict__ Pt, const T* __restrict__ x1,
+                                                    const T* __restrict__ d1, int64_t nchild, int b, int fan,
+                                                    T* __restrict__ d0, int64_t t0, int64_t ts, const int32_t* rprob,
+                                                    const int* act) {
+  for (int64_t t = t0; t < nchild * b; t += ts) {
+    if (skip_row(rprob, act, t)) continue;
     const int64_t c = t / b;
     const int qp = (int)(t - c * b);
     const int64_t B = c / fan;
@@ -83,6 +120,13 @@ __global__ void k_prolong_coarse(const T* __restrict__ Pt, const T* __restrict__
     for (int q = 0; q < b; ++q) s += Pt[(c * b + qp) * b + q] * (x1[B * b + q] + (d1 ? d1[B * b + q] : T(0)));
     d0[t] = s;
   }
+}
+
+template <typename T>
+__global__ void k_prolong_coarse(const T* __restrict__ Pt, const T* __restrict__ x1, const T* __restrict__ d1,
+                                 int64_t nchild, int b, int fan, T* __restrict__ d0) {
+  prolong_coarse_body<T>(Pt, x1, d1, nchild, b, fan, d0, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                         (int64_t)gridDim.x * blockDim.x, nullptr, nullptr);
 }
 
 // Coarsest solve x = A_c^{-1} r with the symmetric inverse formed from the Cholesky factor.

@@ -21,6 +21,7 @@
 #include "kernels_mrhs.cuh"
 #include "kernels_setup.cuh"
 #include "kernels_vcycle.cuh"
+#include "kernels_persistent.cuh"
 
 using namespace r3mg;
 
@@ -70,6 +71,7 @@ struct Level {
   SymView sym;
   bool sym_ok = false;
   int64_t sym_nnz = 0, sym_tvals = 0;   // stored upper values (padding excluded); transposed-pair values
+
   float* sym_vals = nullptr;
   float* sym_y = nullptr;
   float* sym_t = nullptr;
@@ -189,6 +191,16 @@ struct r3mg_hierarchy {
   double* L64 = nullptr;
   float* L32 = nullptr;
   double* ctmp = nullptr;             // the forward substitution's result (nc values, either precision)
+  // batched solves: 0 = the iteration loop as a graph of per-step kernels, 1 = one persistent
+  // cooperative kernel for the whole loop (r3mg_set_batch_mode)
+  int batch_mode = 0;
+  unsigned* pbar = nullptr;           // persistent solve: grid-barrier counter and generation
+  int* pany = nullptr;                // persistent solve: running problems per iteration
+  int pany_cap = 0;
+  cudaGraphExec_t pgraph = nullptr;   // persistent solve captured in a graph (memsets + the launch)
+  int pgraph_state = 0;
+  double pgraph_rtol = -1.0;
+  int pgraph_budget = -1;
   long long wait_cycles = 0;          // limit of the streamed kernels' mbarrier waits (0 = about 1 s)
   int withhold_first = 0;             // expiry-path test: withhold CTA 0's first descriptor copy
 };
@@ -322,6 +334,7 @@ int launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t
   const LevelView<T> v = view<T>(L);
   const bool fine = (L.b == 0);
   const Level::KConf& c = L.conf[sizeof(T) == 4 ? 1 : 0];
+
   // forms: 0 register, 2 persistent, 3 L2 prefetch, 5 software-pipelined, 6 pipelined + L2 prefetch
   const int pipe = (c.form == 2), pf = (c.form == 3 || c.form == 6), sp = (c.form == 5 || c.form == 6);
   const int nsm = L.nsm, nt = (c.nt == 128) ? 128 : 256, u = c.u;
@@ -938,6 +951,9 @@ T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing);
 // Captured graphs hold the Chebyshev coefficients, c0 and kernel configurations as launch
 // arguments: drop them whenever those change; the next solve recaptures.
 void drop_graphs(r3mg_hierarchy* h) {
+  if (h->pgraph) cudaGraphExecDestroy(h->pgraph);
+  h->pgraph = nullptr;
+  h->pgraph_state = 0;
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
   if (h->lgraph) cudaGraphExecDestroy(h->lgraph);
@@ -1126,6 +1142,7 @@ void build_device(r3mg_hierarchy* h, std::vector<HostPattern>& pats, HostFineLay
     }
     F.row_order = upload(h, ord);
     F.row_ptr = upload(h, lay.row_ptr);
+
     lay.idx.resize(lay.idx.size() + 16, 0);   // bulk copies of index runs round up to 16 bytes
     F.idx = upload(h, lay.idx);
     F.stored = lay.row_ptr[h->n];
@@ -1809,6 +1826,99 @@ T* vcycle_body_batch(r3mg_hierarchy* h, bool capturing) {
   return (T*)h->lv[0].d[cur[0]];
 }
 
+// The batched iteration loop as ONE cooperative launch (see kernels_persistent.cuh): the same
+// phases as the loop graph, separated by bounded grid barriers, skipping stopped problems.
+template <typename T>
+void launch_persistent_batch(r3mg_hierarchy* h, double rtol, int budget) {
+  cudaStream_t s = h->stream;
+  const int L = h->L;
+  if (L > kPMaxLevels) throw Fail{R3MG_E_LIMIT, "persistent batched solve: more than 8 levels"};
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  PBatchArgs<T> A{};
+  A.L = L; A.np = h->nprob; A.fcg = (h->prm.precision == 1) ? 1 : 0; A.b = h->b; A.fan = h->fan; A.maxit = budget;
+  A.n = h->n; A.rtol2 = rtol * rtol;
+  size_t smem = 0;
+  for (int l = 0; l < L; ++l) {
+    Level& V = h->lv[l];
+    A.lv[l] = view<T>(V);
+    A.G[l] = V.conf[pi].G;
+    A.x[l] = (T*)V.x; A.r[l] = (T*)V.r; A.d[l][0] = (T*)V.d[0]; A.d[l][1] = (T*)V.d[1];
+    A.dinv[l] = Dinv<T>(V);
+    A.P[l] = (l + 1 < L) ? Pmat<T>(h, l) : nullptr;
+    auto& B = h->bl[l];
+    A.rprob[l] = B.rprob;
+    A.preA[l] = B.preA; A.preC[l] = B.preC; A.postA[l] = B.postA; A.postC[l] = B.postC;
+    A.c0[l] = B.c0; A.npre[l] = B.npre; A.npost[l] = B.npost;
+    if (l + 1 < L) smem = std::max(smem, level_smem_bytes(view<T>(V)));
+  }
+  Level& F = h->lv[0];
+  A.box_of_tree = h->box_of_tree;
+  A.Ainv = Ainv<T>(h); A.moff = h->d_moff; A.mld = h->d_mld; A.cof = h->d_cof;
+  A.f64 = view<double>(F); A.G64 = F.conf[0].G;
+  smem = std::max(smem, level_smem_bytes(view<double>(F)));
+  A.cx = h->cx; A.cr = h->cr; A.cp = h->cp; A.cq = h->cq; A.cz = h->cz;
+  A.S = h->bs;
+  A.sb = h->bl[0].sb; A.se = h->bl[0].se; A.soff = h->bl[0].soff; A.nseg = h->bl[0].nseg; A.seg_part = h->seg_part;
+  if (!h->pbar) h->pbar = dalloc<unsigned>(h, 2);
+  if (h->pany_cap < budget + 1) {
+    h->pany = dalloc<int>(h, budget + 1);
+    h->pany_cap = budget + 1;
+    if (h->pgraph) { cudaGraphExecDestroy(h->pgraph); h->pgraph = nullptr; h->pgraph_state = 0; }
+  }
+  A.any_count = h->pany;
+  A.bar = GridBar{h->pbar, h->pbar + 1, h->tma_err, h->wait_cycles > 0 ? h->wait_cycles : kWaitCycles,
+                  h->withhold_first};
+  auto kern = k_batch_persistent<T>;
+  ensure_smem((const void*)kern, smem);
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem));
+  if (per_sm < 1) throw Fail{R3MG_E_LIMIT, "persistent batched solve: the kernel does not fit an SM"};
+  const int grid = h->nsm * per_sm;   // every CTA resident at once (cooperative launch)
+  auto enqueue = [&]() {
+    CK(cudaMemsetAsync(h->pbar, 0, 2 * sizeof(unsigned), s));
+    CK(cudaMemsetAsync(h->pany, 0, sizeof(int) * (budget + 1), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // all CTAs resident at once (the kernel's grid barrier)
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, kern, A));
+  };
+  // the launch (with the resets of its barrier and counters) captured once per (rtol, budget,
+  // wait setting) into a graph; the direct launch if the capture is not possible
+  if (h->pgraph_state == 1 && (h->pgraph_rtol != rtol || h->pgraph_budget != budget)) {
+    cudaGraphExecDestroy(h->pgraph);
+    h->pgraph = nullptr;
+    h->pgraph_state = 0;
+  }
+  if (h->pgraph_state == 0) {
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try { enqueue(); } catch (Fail&) { ok = false; }
+      if (cudaStreamEndCapture(s, &g) != cudaSuccess) ok = false;
+    }
+    if (ok && cudaGraphInstantiate(&h->pgraph, g, 0) == cudaSuccess) {
+      h->pgraph_state = 1;
+      h->pgraph_rtol = rtol;
+      h->pgraph_budget = budget;
+    } else {
+      h->pgraph_state = -1;
+      h->pgraph = nullptr;
+      cudaGetLastError();
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  if (h->pgraph_state == 1) CK(cudaGraphLaunch(h->pgraph, s));
+  else enqueue();
+  h->launches += 1;
+}
+
 // Batched PCG (FP64 V-cycle) or flexible CG (FP32 V-cycle) on tree-ordered cb / cx.  After a
 // host-launched start (residuals, activity flags, first V-cycle entry), the whole iteration loop
 // runs as one CUDA graph launch: a conditional WHILE node repeats one batched iteration until
@@ -1856,6 +1966,9 @@ r3mg_status krylov_batch(r3mg_hierarchy* h, double rtol, int maxit, int* iters, 
     k_bvc_init<T><<<gv, 256, 0, s>>>(h->cr, n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), B0.c0, B0.rprob);
     CK(cudaGetLastError());
     const int budget = maxit - *std::min_element(its_total.begin(), its_total.end());
+    if (h->batch_mode == 1) {
+      launch_persistent_batch<T>(h, rtol, budget);
+    } else {
     // the loop graph, captured once per (rtol, maxit)
     if (h->bgraph_state == 1 && (h->bgraph_rtol != rtol || h->bgraph_maxit != budget)) {
       cudaGraphExecDestroy(h->bgraph);
@@ -1907,6 +2020,7 @@ r3mg_status krylov_batch(r3mg_hierarchy* h, double rtol, int maxit, int* iters, 
       h->bgraph_maxit = budget;
     }
     CK(cudaGraphLaunch(h->bgraph, s));
+    }
     std::vector<int> itsh(np);
     int err = 0;
     CK(cudaMemcpyAsync(itsh.data(), S.its, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
@@ -1915,6 +2029,14 @@ r3mg_status krylov_batch(r3mg_hierarchy* h, double rtol, int maxit, int* iters, 
     if (err) {
       CK(cudaMemsetAsync(S.err, 0, sizeof(int), s));
       throw Fail{R3MG_E_BREAKDOWN, "batched CG breakdown: p^T A p <= 0 or non-finite scalar"};
+    }
+    if (h->batch_mode == 1) {
+      int terr = 0;
+      CK(cudaMemcpy(&terr, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (terr) {
+        CK(cudaMemset(h->tma_err, 0, sizeof(int)));
+        throw Fail{R3MG_E_TIMEOUT, "persistent batched solve: a bounded grid-barrier wait expired"};
+      }
     }
     for (int k = 0; k < np; ++k) its_total[k] += itsh[k];
   }
@@ -3309,6 +3431,7 @@ void r3mg_destroy(r3mg_hierarchy* h) {
   if (h->bgraph) cudaGraphExecDestroy(h->bgraph);
   if (h->lgraph) cudaGraphExecDestroy(h->lgraph);
   if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
+  if (h->pgraph) cudaGraphExecDestroy(h->pgraph);
   if (h->mr_host) cudaFreeHost(h->mr_host);
   for (auto& sl : h->slots) { cudaEventDestroy(sl.e0); cudaEventDestroy(sl.e1); }
   if (h->cg_slot.e0) { cudaEventDestroy(h->cg_slot.e0); cudaEventDestroy(h->cg_slot.e1); }
@@ -3577,6 +3700,14 @@ r3mg_status r3mg_set_coarse_mode(r3mg_hierarchy* h, int mode) {
     h->coarse_mode = mode;
     drop_graphs(h);   // captured V-cycles hold the old form
   });
+}
+
+r3mg_status r3mg_set_batch_mode(r3mg_hierarchy* h, int mode) {
+  if (!h || (mode != 0 && mode != 1)) return R3MG_E_ARG;
+  if (h->bl.empty()) { h->err = "set_batch_mode: not a batched hierarchy"; return R3MG_E_ARG; }
+  if (mode == 1 && h->L > kPMaxLevels) { h->err = "set_batch_mode: more than 8 levels"; return R3MG_E_LIMIT; }
+  h->batch_mode = mode;
+  return R3MG_OK;
 }
 
 r3mg_status r3mg_set_wait_limit(r3mg_hierarchy* h, long long cycles, int withhold_first_copy) {

@@ -438,6 +438,10 @@ class BatchHierarchy(Hierarchy):
         self.b = (p.pprime + 1) ** self.dim
         self.levels = self.info()["levels"]
 
+    def set_batch_mode(self, mode: int):
+        """0: the iteration loop as a graph of per-step kernels; 1: one persistent cooperative kernel."""
+        _check(lib().r3mg_set_batch_mode(self._h, int(mode)), self._h)
+
     def level_offsets(self, level: int) -> np.ndarray:
         out = np.empty(self.nprob + 1, np.int64)
         _check(lib().r3mg_batch_offsets(self._h, int(level), None, _p(out)), self._h)

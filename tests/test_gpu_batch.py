@@ -82,3 +82,51 @@ def test_batched_fcg_mixed(batch):
         assert np.linalg.norm(bs[k] - P.scipy() @ xk) <= 1e-8 * np.linalg.norm(bs[k]), k
         ref = O.pcg(P.scipy(), bs[k], lambda v: O.vcycle(Ho, v), rtol=1e-8)
         assert its[k] <= ref.iterations + 3
+
+
+def _pin_register(Hb):
+    """Pin the register form on every level (the persistent solve runs the register form) so that
+    both loop modes run identical level kernels."""
+    cfg = Hb.kernel_config()
+    for row in cfg[:-1]:
+        for key in ("f64", "f32"):
+            row[key] = {"form": "register", "lanes": row[key]["lanes"], "threads": 256}
+    Hb.set_kernel_config(cfg[:-1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_persistent_batched_solve_equals_graph_loop(batch, precision):
+    """The whole batched iteration loop in one persistent cooperative kernel gives every problem
+    the same iterates (same bits, same iteration counts) as the graph of per-step kernels; stopped
+    problems are skipped, so problems that converge early keep their solution untouched."""
+    probs, bs, H, Hm, orc = batch
+    Hb = Hm if precision else H
+    _pin_register(Hb)
+    b = torch.tensor(np.concatenate(bs), device="cuda")
+    Hb.set_batch_mode(0)
+    xg, itg, relg = Hb.pcg(b, rtol=1e-9)
+    Hb.set_batch_mode(1)
+    xp, itp, relp = Hb.pcg(b, rtol=1e-9)
+    xp2, itp2, _ = Hb.pcg(b, rtol=1e-9)        # the captured launch replayed
+    Hb.set_batch_mode(0)
+    assert np.array_equal(itg, itp) and np.array_equal(itp, itp2)
+    assert torch.equal(xg, xp) and torch.equal(xp, xp2)
+    assert np.all(relp <= 1e-9)
+    assert len(set(itp.tolist())) > 1          # problems stop at different iterations
+
+
+def test_persistent_batched_barrier_expiry_is_reported(batch):
+    """A grid-barrier wait that cannot complete (CTA 0 withholds its first arrival) runs out after
+    the wait limit: every CTA leaves, the solve reports R3MG_E_TIMEOUT, and the next solve works."""
+    import paper_2607_28235_b300 as R
+    probs, bs, H, Hm, orc = batch
+    b = torch.tensor(np.concatenate(bs), device="cuda")
+    H.set_batch_mode(1)
+    H.set_wait_limit(2_000_000, withhold_first_copy=True)
+    with pytest.raises(R.R3MGError) as e:
+        H.pcg(b, rtol=1e-9)
+    assert e.value.status == 10
+    H.set_wait_limit(0, withhold_first_copy=False)
+    x, its, rel = H.pcg(b, rtol=1e-9)
+    assert np.all(rel <= 1e-9)
+    H.set_batch_mode(0)

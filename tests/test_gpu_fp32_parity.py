@@ -45,6 +45,8 @@ pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 FORMS = ["register", "tma", "register_persistent", "register_l2_prefetch", "register_pipelined",
          "register_pipelined_l2_prefetch", "symmetric_block"]
+FINE_ONLY = set()               # forms of the fine level only
+COARSE_ONLY = {"symmetric_block"}   # forms of the coarse levels only
 
 
 def _hier(P, params, precision=1, **kw):
@@ -68,7 +70,7 @@ def _pin_form(H, form, levels, fp32=True):
     cfg = H.kernel_config()
     key = "f32" if fp32 else "f64"
     for lev in levels:
-        if form == "symmetric_block" and lev == 0:
+        if (form in COARSE_ONLY and lev == 0) or (form in FINE_ONLY and lev > 0):
             continue
         cfg[lev][key] = {"form": form, "lanes": cfg[lev][key]["lanes"] if form != "symmetric_block" else 16,
                          "threads": 512 if form == "tma" else (128 if form == "symmetric_block" else 256)}
@@ -116,8 +118,6 @@ def test_fp32_cheb_step_bounds(case, form):
     a, c = 0.37, 0.71
     a32, c32 = float(np.float32(a)), float(np.float32(c))
     for lev in range(L - 1):
-        if form == "symmetric_block" and lev == 0:
-            continue
         A = Ho.A[lev]
         n = A.shape[0]
         x, r, d = (rng.standard_normal(n).astype(np.float32).astype(np.float64) for _ in range(3))
