@@ -242,8 +242,11 @@ r3mg_status r3mg_level_apply_multi(r3mg_hierarchy* h, int level, int m, int fp32
  * through L1), 0 = coarse-level kernel with the box window staged in shared memory, 1 = coarse-
  * level kernel with the window staged and the block rows streamed into shared memory by the
  * copy engine (cp.async.bulk, bounded mbarrier waits: R3MG_E_TIMEOUT if one expires), 3 =
- * coarse-level FP32 kernel on the tensor cores (8 or 16 columns; TF32 head/tail splitting keeps
- * FP32 accuracy), 10 + slots (12, 14, 18) = fine-level flat row sweep on global column indices
+ * coarse-level FP32 kernel on the tensor cores through mma.sync (8 or 16 columns; TF32
+ * head/tail splitting keeps FP32 accuracy), 5 = coarse-level FP32 kernel on the 5th-generation
+ * tensor cores (tcgen05.mma into a TMEM accumulator, operands staged in shared memory; 16
+ * columns, boxes of at most 32 rows, the same TF32 head/tail splitting; its mbarrier waits are
+ * bounded as set by r3mg_set_wait_limit and an expiry gives R3MG_E_TIMEOUT), 10 + slots (12, 14, 18) = fine-level flat row sweep on global column indices
  * (built once, 4 bytes per stored entry), -1 = not tuned yet.  The setter pins one choice (R3MG_E_ARG for an invalid or untuned combination). */
 r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots);
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots);

@@ -22,6 +22,7 @@
 #include "kernels_setup.cuh"
 #include "kernels_vcycle.cuh"
 #include "kernels_persistent.cuh"
+#include "kernels_tcgen05.cuh"
 
 using namespace r3mg;
 
@@ -2302,14 +2303,43 @@ void mr_launch_mma(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep) {
   }
 }
 
+// 5th-generation tensor-core coarse block kernel (tcgen05, TMEM accumulator): FP32, 16 columns,
+// boxes of at most 32 rows, products without dot partials.
+template <typename T, int M, class Ep>
+constexpr bool mr_tc_ok() { return sizeof(T) == 4 && M == 16; }
+
+template <typename T, int M, class Ep>
+bool mr_tc_fits(const Level& A) { return mr_tc_ok<T, M, Ep>() && A.b > 0 && A.b <= kTcRows; }
+
+template <typename T, int M, class Ep>
+void mr_launch_tc(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep) {
+  if constexpr (mr_tc_ok<T, M, Ep>()) {
+    const LevelView<float> v = view<float>(A);
+    auto kern = k_mr_coarse_tc<M, Ep>;
+    const size_t sm = TcLayout<M>::kTotal;
+    ensure_smem((const void*)kern, sm);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (kMaxSmem + 1024) / (sm + 1024)));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * per_sm));
+    kern<<<grid, 128, sm, h->stream>>>(v, x, ep, h->tma_err, h->wait_cycles);
+    CK(cudaGetLastError());
+  }
+}
+
 // One level operator on M columns with S entry slots per row (on a coarse level S = 0: the
-// staged-window kernel, S = 1: the streamed kernel, S = 3: the tensor-core kernel); returns the
-// partial count.
+// staged-window kernel, S = 1: the streamed kernel, S = 3: the mma.sync tensor-core kernel,
+// S = 5: the tcgen05 tensor-core kernel); returns the partial count.
 template <typename T, int M, class Ep>
 int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part, int S) {
   const bool fine = (A.b == 0);
   cudaStream_t s = h->stream;
   constexpr int CL = M / Slice<T>::V;
+  if (!fine && S == 5) {
+    if (mr_tc_fits<T, M, Ep>(A) && part == nullptr) {
+      mr_launch_tc<T, M, Ep>(h, A, x, ep);
+      return 1;
+    }
+    S = 3;
+  }
   if (!fine && S == 3) {
     if (mr_mma_ok<T, M, Ep>() && part == nullptr) {
       mr_launch_mma<T, M, Ep>(h, A, x, ep);
@@ -2397,8 +2427,10 @@ void mr_tune(r3mg_hierarchy* h) {
     CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
     CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
     float best = 1e30f;
-    for (int S : {3, 1, 0, 2, 4, 8, 12, 14, 18}) {
-      if (S == 3) {
+    for (int S : {5, 3, 1, 0, 2, 4, 8, 12, 14, 18}) {
+      if (S == 5) {
+        if (!mr_tc_fits<T, M, MEpCheb<T, M>>(A)) continue;
+      } else if (S == 3) {
         if (A.b == 0 || !mr_mma_ok<T, M, MEpCheb<T, M>>()) continue;
       } else if (S > 8) {
         if (A.b != 0 || CL * (S - 10) > 32) continue;
@@ -3149,13 +3181,13 @@ r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots
 
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots) {
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
-  if (!(slots == 0 || slots == 1 || slots == 2 || slots == 3 || slots == 4 || slots == 8 || slots == 12 ||
-        slots == 14 || slots == 18)) {
-    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4, 8, 12, 14 or 18";
+  if (!(slots == 0 || slots == 1 || slots == 2 || slots == 3 || slots == 4 || slots == 5 || slots == 8 ||
+        slots == 12 || slots == 14 || slots == 18)) {
+    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4, 5, 8, 12, 14 or 18";
     return R3MG_E_ARG;
   }
   if (slots > 8 && h->lv[level].b != 0) { h->err = "set_block_config: the flat row sweep is for the fine level"; return R3MG_E_ARG; }
-  if ((slots <= 1 || slots == 3) && h->lv[level].b == 0) {
+  if ((slots <= 1 || slots == 3 || slots == 5) && h->lv[level].b == 0) {
     h->err = "set_block_config: the staged, streamed and tensor-core forms are for coarse levels";
     return R3MG_E_ARG;
   }
@@ -3167,8 +3199,12 @@ r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int sl
   if (h->mr_M == 0) { h->err = "set_block_config: no block solve has run yet (nothing tuned)"; return R3MG_E_ARG; }
   auto& Sv = h->mr_S[fp32 ? 1 : 0];
   if ((int)Sv.size() != h->L) { h->err = "set_block_config: this precision is not tuned yet"; return R3MG_E_ARG; }
+  if (slots == 5 && (!fp32 || h->mr_M != 16 || h->lv[level].b > kTcRows)) {
+    h->err = "set_block_config: the tcgen05 form is FP32 with 16 columns and boxes of at most 32 rows";
+    return R3MG_E_ARG;
+  }
   const int CL = h->mr_M / (fp32 ? 4 : 2);
-  if (slots != 3 && CL * (slots > 8 ? slots - 10 : slots) > 32) {
+  if (slots != 3 && slots != 5 && CL * (slots > 8 ? slots - 10 : slots) > 32) {
     h->err = "set_block_config: too many slots for the column count";
     return R3MG_E_ARG;
   }
