@@ -485,7 +485,11 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
  * slice, 4 = symmetric block form (coarse FP32 levels: only the upper blocks are streamed, each
  * used for both of its products), 5 = register-streamed with a software-pipelined row loop
  * (the next chunk of matrix entries is in flight while the current one is consumed), 6 = form 5
- * with the L2 prefetch; lanes per matrix row; threads per CTA;
+ * with the L2 prefetch, 7 = symmetric block form with each box's upper slice requested at once
+ * by one bulk copy into shared memory (cp.async.bulk on an mbarrier; slices larger than the
+ * stage are read as in form 4; bounded wait as set by r3mg_set_wait_limit, R3MG_E_TIMEOUT on
+ * expiry); lanes per matrix row (form 7: the resident CTAs per SM the stage is sized for,
+ * 1..8); threads per CTA;
  * the autotuner's measured time of one launch (0 when not tuned).  Any output may be NULL. */
 r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
                                float* tuned_ms);
@@ -525,8 +529,9 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
                                double* out_dev, void* stream);
 
 /* Pin the level-operator kernel of level l and precision (fp32 = 1 needs an FP32 V-cycle):
- * form 0..6 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32}, threads per CTA in
- * {128, 256} for the register forms and {256, 512, 1024} for the TMA form.  Replays a configuration chosen earlier (reproducible timing
+ * form 0..7 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32} (1..8 resident CTAs per
+ * SM for form 7), threads per CTA in {128, 256} for the register forms (128 for forms 4 and 7) and
+ * {256, 512, 1024} for the TMA form.  Replays a configuration chosen earlier (reproducible timing
  * and profiling).  Errors: R3MG_E_ARG for an unsupported combination.  Synchronises. */
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads);
 

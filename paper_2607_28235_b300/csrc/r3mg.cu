@@ -339,7 +339,9 @@ int launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t
   // forms: 0 register, 2 persistent, 3 L2 prefetch, 5 software-pipelined, 6 pipelined + L2 prefetch
   const int pipe = (c.form == 2), pf = (c.form == 3 || c.form == 6), sp = (c.form == 5 || c.form == 6);
   const int nsm = L.nsm, nt = (c.nt == 128) ? 128 : 256, u = c.u;
-  switch (c.G) {
+  // products on a level whose step takes the staged symmetric form (lanes = CTAs per SM) run on
+  // the register form with 16 lanes per row
+  switch (c.form == 7 ? 16 : c.G) {
     case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
     case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
     case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
@@ -430,6 +432,9 @@ TmaCtl tma_ctl(const r3mg_hierarchy* h) {
   return TmaCtl{h->tma_err, h->wait_cycles > 0 ? h->wait_cycles : kWaitCycles, h->withhold_first};
 }
 
+// the FP32 step of this level runs on the symmetric (upper-block) storage: form 4 streamed, 7 staged
+bool sym_form(const Level& A) { return A.sym_ok && (A.conf[1].form == 4 || A.conf[1].form == 7); }
+
 // Product y = A x (+ partial w . y) on either kernel form; partial count = grid of the kernel.
 template <typename T>
 bool tma_on(const Level& A) {
@@ -449,7 +454,7 @@ int level_apply_dot(r3mg_hierarchy* h, const Level& A, const T* x, T* y, const T
 template <typename T>
 void level_cheb(r3mg_hierarchy* h, const Level& A, T* x, T* r, T* d, T* dn, const T* dinv, T a, T c) {
   if constexpr (sizeof(T) == 4) {
-    if (A.conf[1].form == 4 && A.sym_ok) {
+    if (sym_form(A)) {
       sym_step(h, A, d, SymCheb{x, r, d, dn, dinv, a, c});
       return;
     }
@@ -540,6 +545,7 @@ void build_sym(r3mg_hierarchy* h, Level& A) {
   std::vector<int32_t> up_len(nb), dslot(nb);
   std::vector<std::vector<int64_t>> low(nb);
   int wmax = 0;
+  int64_t smax = 0;
   for (int64_t B = 0; B < nb; ++B) {
     const int64_t q0 = A.pat.ptr[B], nn = A.pat.ptr[B + 1] - q0;
     int64_t d = -1;
@@ -552,6 +558,7 @@ void build_sym(r3mg_hierarchy* h, Level& A) {
     up_base[B + 1] = up_base[B] + (int64_t)b * len;
     tp_off[B + 1] = tp_off[B] + (nup - 1);
     wmax = std::max(wmax, len);
+    smax = std::max<int64_t>(smax, (int64_t)b * len);
     for (int64_t s = d + 1; s < nn; ++s) low[A.pat.nbr[q0 + s]].push_back(tp_off[B] + (s - d - 1));
   }
   std::vector<int64_t> low_pair;
@@ -569,6 +576,7 @@ void build_sym(r3mg_hierarchy* h, Level& A) {
   V.low_ptr = upload(h, low_ptr);
   V.low_pair = upload(h, low_pair);
   V.win_max = wmax;
+  V.stage_max = (int)std::min<int64_t>(smax, 1 << 30);
   A.sym_vals = dalloc<float>(h, up_base[nb]);
   V.vals = A.sym_vals;
   A.sym_y = dalloc<float>(h, A.n);
@@ -579,10 +587,29 @@ void build_sym(r3mg_hierarchy* h, Level& A) {
   A.sym_ok = true;
 }
 
+// Shared-memory stage of the staged symmetric kernel for `cps` resident CTAs per SM: the CTA's
+// share of the SM's shared memory less the window, capped at the level's largest upper slice
+// (floats, multiple of 4; 0 when not even the window fits).
+int sym_stage_cap(const Level& A, int cps) {
+  const int64_t win = (A.sym.win_max + 3) & ~3;
+  const int64_t share = std::min<int64_t>((int64_t)kMaxSmem, (int64_t)228 * 1024 / std::max(1, cps) - 2048) / 4;
+  const int64_t cap = std::min<int64_t>(share - win, ((int64_t)A.sym.stage_max + 3) & ~3);
+  return cap < 4 * A.b ? 0 : (int)(cap & ~(int64_t)3);
+}
+
 void sym_step(r3mg_hierarchy* h, const Level& A, const float* d, SymCheb ep) {
-  const size_t sm = sizeof(float) * (size_t)A.sym.win_max;
-  ensure_smem((const void*)k_sym_block, sm);
-  k_sym_block<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
+  const int cap = A.conf[1].form == 7 ? sym_stage_cap(A, A.conf[1].G) : 0;
+  if (cap > 0) {
+    const TmaCtl c = tma_ctl(h);
+    const size_t sm = sizeof(float) * ((size_t)cap + (((size_t)A.sym.win_max + 3) & ~(size_t)3));
+    ensure_smem((const void*)k_sym_block_staged, sm);
+    k_sym_block_staged<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(
+        A.sym, d, A.sym_y, A.sym_t, cap, c.err, c.wait, c.withhold);
+  } else {
+    const size_t sm = sizeof(float) * (size_t)A.sym.win_max;
+    ensure_smem((const void*)k_sym_block, sm);
+    k_sym_block<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
+  }
   k_sym_finish<<<grid_for(A.n), 256, 0, h->stream>>>(A.sym, A.sym_y, A.sym_t, ep);
   CK(cudaGetLastError());
 }
@@ -914,7 +941,11 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
       }
     if (A.tma[pi].nitems > 0)
       for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f, 0});
-    if (sizeof(T) == 4 && A.sym_ok && G == 16 && !product) cand.push_back({4, G, 128, 0.f, 0});
+    if (sizeof(T) == 4 && A.sym_ok && G == 16 && !product) {
+      cand.push_back({4, G, 128, 0.f, 0});
+      for (int cps : {2, 3, 4, 5})   // staged form: the lanes field holds the resident CTAs per SM
+        if (sym_stage_cap(A, cps) > 0) cand.push_back({7, cps, 128, 0.f, 0});
+    }
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1));
@@ -1754,7 +1785,7 @@ void level_cheb_b(r3mg_hierarchy* h, const Level& A, int l, T* x, T* r, T* d, T*
   const double* ta = (post ? B.postA : B.preA) + (int64_t)st * np;
   const double* tc = (post ? B.postC : B.preC) + (int64_t)st * np;
   if constexpr (sizeof(T) == 4) {
-    if (A.conf[1].form == 4 && A.sym_ok) {
+    if (sym_form(A)) {
       SymCheb ep{x, r, d, dn, Dinv<T>(A), 0.f, 0.f};
       ep.A = ta; ep.C = tc; ep.rprob = B.rprob;
       sym_step(h, A, d, ep);
@@ -1842,7 +1873,7 @@ void launch_persistent_batch(r3mg_hierarchy* h, double rtol, int budget) {
   for (int l = 0; l < L; ++l) {
     Level& V = h->lv[l];
     A.lv[l] = view<T>(V);
-    A.G[l] = V.conf[pi].G;
+    A.G[l] = V.conf[pi].form == 7 ? 16 : V.conf[pi].G;   // form 7 keeps CTAs per SM in the lanes field
     A.x[l] = (T*)V.x; A.r[l] = (T*)V.r; A.d[l][0] = (T*)V.d[0]; A.d[l][1] = (T*)V.d[1];
     A.dinv[l] = Dinv<T>(V);
     A.P[l] = (l + 1 < L) ? Pmat<T>(h, l) : nullptr;
@@ -3386,7 +3417,7 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
         const Level& A = h->lv[kind - 1];
         const double es = f32 ? 4.0 : 8.0;
         const double ib = (A.b == 0) ? 2.0 : 0.0;
-        if (f32 && cols == 1.0 && A.conf[1].form == 4 && A.sym_ok) {
+        if (f32 && cols == 1.0 && sym_form(A)) {
           // symmetric block form: the upper blocks once, the transposed-pair values and the row
           // sums written and read back, and the step's vectors
           *bytes_per_launch = (double)A.sym_nnz * es + 2.0 * es * (double)A.sym_tvals + 2.0 * es * A.n +
@@ -3421,9 +3452,23 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
     if (h) h->err = "set_kernel_config: unroll 4 is an FP64 option (0 = default)";
     return R3MG_E_ARG;
   }
+  if (h && level >= 0 && level < h->L && form == 7) {   // staged symmetric form: lanes = CTAs per SM
+    Level& A = h->lv[level];
+    if (!fp32 || !A.sym_ok || lanes < 1 || lanes > 8 || threads != 128 || sym_stage_cap(A, lanes) == 0) {
+      h->err = "set_kernel_config: the staged symmetric form is FP32 on a symmetric coarse level, lanes = 1..8 "
+               "resident CTAs per SM (the stage sizing), 128 threads";
+      return R3MG_E_ARG;
+    }
+    if (h->prm.precision != 1) { h->err = "set_kernel_config: the hierarchy has no FP32 V-cycle"; return R3MG_E_ARG; }
+    return guarded(h, [&] {
+      CK(cudaStreamSynchronize(h->stream));
+      A.conf[1] = Level::KConf{7, lanes, threads, 0.f, 0};
+      drop_graphs(h);
+    });
+  }
   if (!h || level < 0 || level >= h->L || form < 0 || form > 6 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
       (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || (form == 1 && threads == 128)) {
-    if (h) h->err = "set_kernel_config: invalid level, form (0..6), lanes (4,8,16,32) or threads (128 register forms only, 256, 512, 1024)";
+    if (h) h->err = "set_kernel_config: invalid level, form (0..7), lanes (4,8,16,32; 1..8 for form 7) or threads (128 register forms only, 256, 512, 1024)";
     return R3MG_E_ARG;
   }
   Level& A = h->lv[level];
@@ -3445,7 +3490,11 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
   const Level::KConf& c = h->lv[level].conf[fp32 ? 1 : 0];
   const bool tma = c.form == 1 && h->lv[level].tma[fp32 ? 1 : 0].nitems > 0;
   if (form)
-    *form = tma ? 1 : (c.form == 2 || c.form == 3 || c.form == 5 || c.form == 6 || (c.form == 4 && h->lv[level].sym_ok) ? c.form : 0);
+    *form = tma ? 1
+                : (c.form == 2 || c.form == 3 || c.form == 5 || c.form == 6 ||
+                           ((c.form == 4 || c.form == 7) && h->lv[level].sym_ok)
+                       ? c.form
+                       : 0);
   if (lanes) *lanes = c.G;
   if (threads) *threads = tma ? c.nt : (c.nt == 128 ? 128 : 256);
   if (tuned_ms) *tuned_ms = c.ms;

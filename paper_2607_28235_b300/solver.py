@@ -16,7 +16,7 @@ from ._lib import R3MGError, _Params, lib
 
 # level-operator kernel forms, in the order of r3mg_kernel_config's codes
 FORMS = ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block", "register_pipelined",
-         "register_pipelined_l2_prefetch"]
+         "register_pipelined_l2_prefetch", "symmetric_block_staged"]
 
 
 def _p(a) -> ctypes.c_void_p:

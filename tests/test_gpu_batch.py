@@ -90,7 +90,7 @@ def _pin_register(Hb):
     cfg = Hb.kernel_config()
     for row in cfg[:-1]:
         for key in ("f64", "f32"):
-            row[key] = {"form": "register", "lanes": row[key]["lanes"], "threads": 256}
+            row[key] = {"form": "register", "lanes": row[key]["lanes"] if row[key]["lanes"] >= 4 else 16, "threads": 256}
     Hb.set_kernel_config(cfg[:-1])
 
 

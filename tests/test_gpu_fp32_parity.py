@@ -44,9 +44,19 @@ pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
 FORMS = ["register", "tma", "register_persistent", "register_l2_prefetch", "register_pipelined",
-         "register_pipelined_l2_prefetch", "symmetric_block"]
+         "register_pipelined_l2_prefetch", "symmetric_block", "symmetric_block_staged"]
 FINE_ONLY = set()               # forms of the fine level only
-COARSE_ONLY = {"symmetric_block"}   # forms of the coarse levels only
+SYMMETRIC = {"symmetric_block", "symmetric_block_staged"}   # Chebyshev steps only, coarse levels only
+COARSE_ONLY = SYMMETRIC
+PRODUCT_FORMS = [f for f in FORMS if f not in SYMMETRIC]
+
+
+def _lanes_threads(form, lanes):
+    if form == "symmetric_block":
+        return 16, 128
+    if form == "symmetric_block_staged":
+        return 4, 128                   # lanes field: resident CTAs per SM the stage is sized for
+    return lanes, 512 if form == "tma" else 256
 
 
 def _hier(P, params, precision=1, **kw):
@@ -72,8 +82,8 @@ def _pin_form(H, form, levels, fp32=True):
     for lev in levels:
         if (form in COARSE_ONLY and lev == 0) or (form in FINE_ONLY and lev > 0):
             continue
-        cfg[lev][key] = {"form": form, "lanes": cfg[lev][key]["lanes"] if form != "symmetric_block" else 16,
-                         "threads": 512 if form == "tma" else (128 if form == "symmetric_block" else 256)}
+        lanes, threads = _lanes_threads(form, cfg[lev][key]["lanes"] if cfg[lev][key]["lanes"] >= 4 else 16)
+        cfg[lev][key] = {"form": form, "lanes": lanes, "threads": threads}
     try:
         H.set_kernel_config(cfg[:-1])
     except Exception:
@@ -85,7 +95,7 @@ def _row_len(A):
     return np.diff(sp.csr_matrix(A).indptr)
 
 
-@pytest.mark.parametrize("form", FORMS[:-1])
+@pytest.mark.parametrize("form", PRODUCT_FORMS)
 def test_fp32_level_product_rowwise_bound(case, form):
     P, params, Ho = case
     H = _hier(P, params)
@@ -185,3 +195,34 @@ def test_fp32_vcycle_vs_oracle_each_form(case, form):
     r = np.random.default_rng(15).standard_normal(P.n)
     fp32_vcycle_check(H, Ho, r, form)
     H.close()
+
+
+@pytest.mark.parametrize("cps", [1, 4])
+def test_staged_symmetric_step_same_bits_as_streamed(case, cps):
+    """The staged symmetric kernel (one bulk copy of each box's upper slice into shared memory;
+    with a stage sized for 4 CTAs per SM the largest slices are read from global memory instead)
+    computes every box exactly as the streamed one: the Chebyshev step outputs agree bit for bit
+    on every coarse level."""
+    P, params, Ho = case
+    H1, H2 = _hier(P, params), _hier(P, params)
+    L = params["levels"]
+    ok = _pin_form(H1, "symmetric_block", range(1, L - 1))
+    cfg = H2.kernel_config()
+    for lev in range(1, L - 1):
+        cfg[lev]["f32"] = {"form": "symmetric_block_staged", "lanes": cps, "threads": 128}
+    try:
+        H2.set_kernel_config(cfg[:-1])
+    except RuntimeError:
+        ok = False
+    if not ok:
+        H1.close(); H2.close()
+        pytest.skip("no symmetric coarse level")
+    rng = np.random.default_rng(16)
+    for lev in range(1, L - 1):
+        n = Ho.A[lev].shape[0]
+        v = [torch.tensor(rng.standard_normal(n), device="cuda") for _ in range(3)]
+        o1 = [t.cpu().numpy() for t in H1.cheb_step(lev, *v, 0.37, 0.71)]
+        o2 = [t.cpu().numpy() for t in H2.cheb_step(lev, *v, 0.37, 0.71)]
+        for a, b in zip(o1, o2):
+            assert np.array_equal(a, b), lev
+    H1.close(); H2.close()

@@ -174,7 +174,7 @@ def test_kernel_forms_match_oracle(pair, form):
 
 
 @pytest.mark.parametrize("form", ["register", "tma", "register_persistent", "register_l2_prefetch", "symmetric_block",
-                                  "register_pipelined", "register_pipelined_l2_prefetch"])
+                                  "register_pipelined", "register_pipelined_l2_prefetch", "symmetric_block_staged"])
 def test_set_kernel_config_each_form(pair, form):
     """Every kernel form, pinned through r3mg_set_kernel_config, gives a converged mixed-precision
     PCG (the symmetric block form exists on coarse FP32 levels only)."""
@@ -183,15 +183,18 @@ def test_set_kernel_config_each_form(pair, form):
     cfg = Hf.kernel_config()
     for lev, row in enumerate(cfg[:-1]):
         for key in ("f64", "f32"):
-            if form == "symmetric_block" and (lev == 0 or key == "f64"):
+            if form.startswith("symmetric_block") and (lev == 0 or key == "f64"):
                 continue
-            row[key] = {"form": form, "lanes": row[key]["lanes"], "threads": 512}
+            if form == "symmetric_block_staged":    # lanes field: CTAs per SM
+                row[key] = {"form": form, "lanes": 1, "threads": 128}
+                continue
+            row[key] = {"form": form, "lanes": row[key]["lanes"] if row[key]["lanes"] >= 4 else 16, "threads": 512}
     try:
         Hf.set_kernel_config(cfg[:-1])
     except Exception as e:       # a form a level cannot host (windows too large for two buffers)
         pytest.skip(str(e))
     got = Hf.kernel_config()
-    first = 1 if form == "symmetric_block" else 0
+    first = 1 if form.startswith("symmetric_block") else 0
     assert all(got[l]["f32"]["form"] == form for l in range(first, len(cfg) - 1))
     x, it, rel = Hf.pcg(torch.tensor(P.b, device="cuda"), rtol=1e-10)
     assert np.linalg.norm(P.b - P.scipy() @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(P.b)

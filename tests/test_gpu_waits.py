@@ -50,3 +50,34 @@ def test_tma_level_kernel_wait_expiry_is_reported():
     assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
     assert H.device_status() == 0
     H.close()
+
+
+def test_staged_symmetric_wait_expiry_is_reported():
+    """The staged symmetric kernel's per-stage mbarrier wait runs out when CTA 0's first bulk copy
+    is withheld: the step reports R3MG_E_TIMEOUT once, and the next step is exact again."""
+    import paper_2607_28235_b300 as R
+    P, params = make(CASES[1])
+    H = R.Hierarchy(P.coords, P.rowptr, P.colidx, P.vals, precision=1, **params)
+    cfg = H.kernel_config()
+    lev = 1
+    cfg[lev]["f32"] = {"form": "symmetric_block_staged", "lanes": 1, "threads": 128}
+    try:
+        H.set_kernel_config(cfg[:-1])
+    except RuntimeError:
+        H.close()
+        pytest.skip("level 1 has no staged symmetric form")
+    n = H.info()["n"][lev]
+    rng = np.random.default_rng(52)
+    v = [torch.tensor(rng.standard_normal(n), device="cuda") for _ in range(3)]
+    ref = [t.cpu().numpy() for t in H.cheb_step(lev, *v, 0.37, 0.71)]
+    assert H.device_status() == 0
+    H.set_wait_limit(200000, withhold_first_copy=True)
+    H.cheb_step(lev, *v, 0.37, 0.71)
+    assert H.device_status() == 10
+    assert H.device_status() == 0
+    H.set_wait_limit(0, withhold_first_copy=False)
+    out = [t.cpu().numpy() for t in H.cheb_step(lev, *v, 0.37, 0.71)]
+    for a, b in zip(ref, out):
+        assert np.array_equal(a, b)
+    assert H.device_status() == 0
+    H.close()
