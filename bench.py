@@ -407,6 +407,11 @@ def run_multi(args):
     setup_m = time.perf_counter() - t0
     Bd = torch.tensor(B, device=dev)
     stream = torch.cuda.current_stream()
+    if args.pin_block:               # one block solve tunes every level, then the pins replace the choice
+        Hm.pcg_multi(Bd, rtol=w["rtol"])
+        for pin in args.pin_block:
+            lev, slots = (int(v) for v in pin.split(":"))
+            Hm.set_block_config(lev, slots, fp32=True)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -692,6 +697,8 @@ def run_ours(args):
             row["form"] = parts[1]
             if len(parts) > 2:
                 row["lanes"] = int(parts[2])
+            elif parts[1] != "symmetric_block_staged" and row["lanes"] < 4:
+                row["lanes"] = 16        # the tuned form kept CTAs per SM in the lanes field
             if len(parts) > 3:
                 row["threads"] = int(parts[3])
             H.set_kernel_config(cfg[:-1])
@@ -778,12 +785,28 @@ def run_ours(args):
     avg_ms = tk["ms"] / tk["launches"]
     achieved = tk["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
     kernel_name = f"{top}_{'f64' if top.startswith('cg') else 'f32'}"
+    kernel_src = "kernels_level.cuh"
+    if top.startswith("cheb_step_level"):    # the symmetric forms have summaries of their own
+        form = Hm.kernel_config()[int(top[len("cheb_step_level"):])]["f32"]["form"]
+        if form.startswith("symmetric_block"):
+            kernel_name += "_" + form
+            kernel_src = "kernels_level_sym.cuh"
     # share of the unprofiled solve time taken by each kind (event times of the profiled pass)
     share = {k: round(v["ms"] / (ms_mixed * args.steps), 4) for k, v in kinds.items()}
     kinds_d = {k: v for k, v in prof_d.items() if isinstance(v, dict) and v["launches"] > 0}
     top_d = max(kinds_d, key=lambda k: kinds_d[k]["ms"])
     td = kinds_d[top_d]
     avg_d = td["ms"] / td["launches"]
+    # the FP64 solve's top kernel is bound by the FP64 pipe: one FMA per stored value of its level
+    # against the FMA rate of this GPU, measured now by the library's probe (8 independent FMA chains)
+    rates = R.measure_fp64_rates()
+    lev_d = 0 if top_d.startswith("cg") else int(top_d[len("cheb_step_level"):])
+    fma = float(info["nnz"][lev_d])
+    fp64_roof = {"bound": "alu", "kernel": f"{top_d}_f64", "achieved": fma / (avg_d * 1e-3) / 1e12,
+                 "peak": rates["fma_tflops"] / 2, "unit": "T FMA/s",
+                 "frac": fma / (avg_d * 1e-3) / 1e12 / (rates["fma_tflops"] / 2),
+                 "peak_source": "measured FP64 FMA rate (r3mg_measure_fp64_rates)", "fma_per_launch": fma,
+                 "avg_launch_ms": avg_d}
     line = {
         "metric": METRIC, "value": ms_mixed, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
@@ -799,6 +822,7 @@ def run_ours(args):
         "fp64": {"ms": ms_fp64, "iterations": its_d[-1], "relres_check": chk_d,
                  "top_kernel": top_d, "top_kernel_avg_ms": avg_d,
                  "top_kernel_achieved_gbs": td["bytes_per_launch"] / (avg_d * 1e-3) / 1e9,
+                 "roofline": fp64_roof,
                  "kernel_config": [row["f64"] for row in Hd.kernel_config()],
                  "kernel_ms": {k: v["ms"] / max(v["launches"], 1) for k, v in kinds_d.items()}},
         "mixed_vs_fp64_speedup": ms_fp64 / ms_mixed, "mixed_vs_fp64_solution_reldiff": diff_md,
@@ -808,7 +832,7 @@ def run_ours(args):
                      "timing": "CUDA events around each launch of this kernel in a profiled pass of the same solves",
                      "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_launch": tk["bytes_per_launch"], "avg_launch_ms": avg_ms,
-                     "traffic": _traffic(kernel_name)},
+                     "traffic": _traffic(kernel_name, kernel_src)},
         "kernel_time_share": share,
         "kernel_config": Hm.kernel_config(),
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * 8 * P.n, "d2h_bytes_per_step": 8 * P.n,
@@ -836,6 +860,9 @@ def main():
                     help="level:form[:lanes[:threads]]: pin the FP32 level kernel of one level (repeatable)")
     ap.add_argument("--pin-form64", action="append", default=None,
                     help="level:form[:lanes[:threads]]: pin the FP64 level kernel of one level (repeatable)")
+    ap.add_argument("--pin-block", action="append", default=None,
+                    help="level:slots: pin the FP32 block kernel of one level in the block workloads (repeatable; "
+                         "slots as r3mg_set_block_config: 3 mma.sync, 5 tcgen05, ...)")
     ap.add_argument("--ncu-region", default="mixed", choices=["mixed", "fp64"],
                     help="which profiled pass lies between cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--workload", default="full", choices=["full", "small", "cells", "batch256", "rhs16",

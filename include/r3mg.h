@@ -488,8 +488,7 @@ r3mg_status r3mg_profile_read(r3mg_hierarchy* h, int kind, double* total_ms, int
  * with the L2 prefetch, 7 = symmetric block form with each box's upper slice requested at once
  * by one bulk copy into shared memory (cp.async.bulk on an mbarrier; slices larger than the
  * stage are read as in form 4; bounded wait as set by r3mg_set_wait_limit, R3MG_E_TIMEOUT on
- * expiry); lanes per matrix row (form 7: the resident CTAs per SM the stage is sized for,
- * 1..8); threads per CTA;
+ * expiry); lanes per matrix row (form 7: resident CTAs per SM, 1..8); threads per CTA;
  * the autotuner's measured time of one launch (0 when not tuned).  Any output may be NULL. */
 r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int* form, int* lanes, int* threads,
                                float* tuned_ms);

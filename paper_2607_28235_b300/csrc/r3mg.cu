@@ -433,6 +433,7 @@ TmaCtl tma_ctl(const r3mg_hierarchy* h) {
 }
 
 // the FP32 step of this level runs on the symmetric (upper-block) storage: form 4 streamed, 7 staged
+// (form 7 keeps its resident CTAs per SM in the lanes field)
 bool sym_form(const Level& A) { return A.sym_ok && (A.conf[1].form == 4 || A.conf[1].form == 7); }
 
 // Product y = A x (+ partial w . y) on either kernel form; partial count = grid of the kernel.
@@ -929,7 +930,7 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
   std::vector<Level::KConf> cand;
   for (int G : {4, 8, 16, 32}) {
     if (fine && G == 32) continue;
-    if (!fine && G < 16) continue;
+    if (!fine && G < 8 && sizeof(T) == 4) continue;   // coarse FP32 rows keep 16-byte loads per 8+ lanes
     for (int nt : {128, 256})
       for (int u : {0, 4}) {
         if (nt / G < 2) continue;
@@ -1873,7 +1874,7 @@ void launch_persistent_batch(r3mg_hierarchy* h, double rtol, int budget) {
   for (int l = 0; l < L; ++l) {
     Level& V = h->lv[l];
     A.lv[l] = view<T>(V);
-    A.G[l] = V.conf[pi].form == 7 ? 16 : V.conf[pi].G;   // form 7 keeps CTAs per SM in the lanes field
+    A.G[l] = V.conf[pi].form == 7 ? 16 : V.conf[pi].G;   // form 7: the lanes field holds CTAs per SM
     A.x[l] = (T*)V.x; A.r[l] = (T*)V.r; A.d[l][0] = (T*)V.d[0]; A.d[l][1] = (T*)V.d[1];
     A.dinv[l] = Dinv<T>(V);
     A.P[l] = (l + 1 < L) ? Pmat<T>(h, l) : nullptr;
@@ -3462,7 +3463,7 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
     if (h->prm.precision != 1) { h->err = "set_kernel_config: the hierarchy has no FP32 V-cycle"; return R3MG_E_ARG; }
     return guarded(h, [&] {
       CK(cudaStreamSynchronize(h->stream));
-      A.conf[1] = Level::KConf{7, lanes, threads, 0.f, 0};
+      A.conf[1] = Level::KConf{form, lanes, threads, 0.f, 0};
       drop_graphs(h);
     });
   }

@@ -55,7 +55,7 @@ def _lanes_threads(form, lanes):
     if form == "symmetric_block":
         return 16, 128
     if form == "symmetric_block_staged":
-        return 4, 128                   # lanes field: resident CTAs per SM the stage is sized for
+        return 4, 128                   # lanes field: resident CTAs per SM
     return lanes, 512 if form == "tma" else 256
 
 
@@ -197,8 +197,8 @@ def test_fp32_vcycle_vs_oracle_each_form(case, form):
     H.close()
 
 
-@pytest.mark.parametrize("cps", [1, 4])
-def test_staged_symmetric_step_same_bits_as_streamed(case, cps):
+@pytest.mark.parametrize("form,cps", [("symmetric_block_staged", 1), ("symmetric_block_staged", 4)])
+def test_staged_symmetric_step_same_bits_as_streamed(case, form, cps):
     """The staged symmetric kernel (one bulk copy of each box's upper slice into shared memory;
     with a stage sized for 4 CTAs per SM the largest slices are read from global memory instead)
     computes every box exactly as the streamed one: the Chebyshev step outputs agree bit for bit
@@ -209,7 +209,7 @@ def test_staged_symmetric_step_same_bits_as_streamed(case, cps):
     ok = _pin_form(H1, "symmetric_block", range(1, L - 1))
     cfg = H2.kernel_config()
     for lev in range(1, L - 1):
-        cfg[lev]["f32"] = {"form": "symmetric_block_staged", "lanes": cps, "threads": 128}
+        cfg[lev]["f32"] = {"form": form, "lanes": cps, "threads": 128}
     try:
         H2.set_kernel_config(cfg[:-1])
     except RuntimeError:

@@ -186,7 +186,7 @@ def test_set_kernel_config_each_form(pair, form):
             if form.startswith("symmetric_block") and (lev == 0 or key == "f64"):
                 continue
             if form == "symmetric_block_staged":    # lanes field: CTAs per SM
-                row[key] = {"form": form, "lanes": 1, "threads": 128}
+                row[key] = {"form": form, "lanes": 4, "threads": 128}
                 continue
             row[key] = {"form": form, "lanes": row[key]["lanes"] if row[key]["lanes"] >= 4 else 16, "threads": 512}
     try:
@@ -299,3 +299,37 @@ def test_coarse_substitution_form(pair, precision):
     assert rel <= 1e-10
     Hc.set_coarse_mode(0)
     Hc.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_every_lane_count_on_every_level(pair, fp32):
+    """The register kernel with 4, 8, 16 and 32 lanes per row (32 on coarse levels only) and 128
+    or 256 threads gives the oracle's level products on every
+    smoothed level: FP64 within 1e-12 of the largest entry of the result, FP32 within the
+    row-wise rounding bound (row entries + 2) 2^-24 (|A||x|)_i."""
+    P, params, H, Ho = pair
+    Hx = _hier(P, params, precision=1) if fp32 else H
+    key = "f32" if fp32 else "f64"
+    rng = np.random.default_rng(61)
+    L = params["levels"]
+    for lanes in (4, 8, 16, 32):
+        for threads in (128, 256):
+            cfg = Hx.kernel_config()
+            levels = [l for l in range(L - 1) if not (l == 0 and lanes == 32)]
+            for lev in levels:
+                cfg[lev][key] = {"form": "register", "lanes": lanes, "threads": threads}
+            Hx.set_kernel_config(cfg[:-1])
+            for lev in levels:
+                A = Ho.A[lev]
+                x = rng.standard_normal(A.shape[0])
+                if fp32:
+                    x = x.astype(np.float32).astype(np.float64)
+                y = Hx.level_apply(lev, torch.tensor(x, device="cuda"), fp32=fp32).cpu().numpy()
+                ref = A @ x
+                if fp32:
+                    bound = (np.diff(A.indptr) + 2) * 2.0 ** -24 * (abs(A) @ np.abs(x))
+                    assert np.all(np.abs(y - ref) <= bound), (lev, lanes, threads)
+                else:
+                    assert np.max(np.abs(y - ref)) <= 1e-12 * np.abs(ref).max(), (lev, lanes, threads)
+    if fp32:
+        Hx.close()
