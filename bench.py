@@ -806,7 +806,7 @@ def run_ours(args):
                  "peak": rates["fma_tflops"] / 2, "unit": "T FMA/s",
                  "frac": fma / (avg_d * 1e-3) / 1e12 / (rates["fma_tflops"] / 2),
                  "peak_source": "measured FP64 FMA rate (r3mg_measure_fp64_rates)", "fma_per_launch": fma,
-                 "avg_launch_ms": avg_d}
+                 "avg_launch_ms": avg_d, "traffic": _traffic(f"{top_d}_f64")}
     line = {
         "metric": METRIC, "value": ms_mixed, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
