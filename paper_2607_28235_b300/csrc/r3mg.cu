@@ -2352,19 +2352,39 @@ void mr_launch_tc(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep) {
     ensure_smem((const void*)kern, sm);
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (kMaxSmem + 1024) / (sm + 1024)));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm * per_sm));
-    kern<<<grid, 128, sm, h->stream>>>(v, x, ep, h->tma_err, h->wait_cycles);
+    kern<<<grid, 128, sm, h->stream>>>(v, x, ep, h->tma_err, tma_ctl(h).wait);
+    CK(cudaGetLastError());
+  }
+}
+
+template <typename T, int M, class Ep>
+void mr_launch_tc2(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep) {
+  if constexpr (mr_tc_ok<T, M, Ep>()) {
+    const LevelView<float> v = view<float>(A);
+    auto kern = k_mr_coarse_tc2<Ep>;
+    ensure_smem((const void*)kern, kT2SmemLaunch);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.nbox, (int64_t)h->nsm));
+    kern<<<grid, kT2Warps * 32, kT2SmemLaunch, h->stream>>>(v, x, ep, h->tma_err, tma_ctl(h).wait);
     CK(cudaGetLastError());
   }
 }
 
 // One level operator on M columns with S entry slots per row (on a coarse level S = 0: the
 // staged-window kernel, S = 1: the streamed kernel, S = 3: the mma.sync tensor-core kernel,
-// S = 5: the tcgen05 tensor-core kernel); returns the partial count.
+// S = 5: the tcgen05 tensor-core kernel, S = 6: the warp-specialised tcgen05 kernel with A in
+// TMEM); returns the partial count.
 template <typename T, int M, class Ep>
 int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part, int S) {
   const bool fine = (A.b == 0);
   cudaStream_t s = h->stream;
   constexpr int CL = M / Slice<T>::V;
+  if (!fine && S == 6) {
+    if (mr_tc_fits<T, M, Ep>(A) && part == nullptr) {
+      mr_launch_tc2<T, M, Ep>(h, A, x, ep);
+      return 1;
+    }
+    S = 5;
+  }
   if (!fine && S == 5) {
     if (mr_tc_fits<T, M, Ep>(A) && part == nullptr) {
       mr_launch_tc<T, M, Ep>(h, A, x, ep);
@@ -2459,8 +2479,8 @@ void mr_tune(r3mg_hierarchy* h) {
     CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
     CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
     float best = 1e30f;
-    for (int S : {5, 3, 1, 0, 2, 4, 8, 12, 14, 18}) {
-      if (S == 5) {
+    for (int S : {6, 5, 3, 1, 0, 2, 4, 8, 12, 14, 18}) {
+      if (S == 5 || S == 6) {
         if (!mr_tc_fits<T, M, MEpCheb<T, M>>(A)) continue;
       } else if (S == 3) {
         if (A.b == 0 || !mr_mma_ok<T, M, MEpCheb<T, M>>()) continue;
@@ -3213,13 +3233,13 @@ r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots
 
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots) {
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
-  if (!(slots == 0 || slots == 1 || slots == 2 || slots == 3 || slots == 4 || slots == 5 || slots == 8 ||
-        slots == 12 || slots == 14 || slots == 18)) {
-    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4, 5, 8, 12, 14 or 18";
+  if (!(slots == 0 || slots == 1 || slots == 2 || slots == 3 || slots == 4 || slots == 5 || slots == 6 ||
+        slots == 8 || slots == 12 || slots == 14 || slots == 18)) {
+    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4, 5, 6, 8, 12, 14 or 18";
     return R3MG_E_ARG;
   }
   if (slots > 8 && h->lv[level].b != 0) { h->err = "set_block_config: the flat row sweep is for the fine level"; return R3MG_E_ARG; }
-  if ((slots <= 1 || slots == 3 || slots == 5) && h->lv[level].b == 0) {
+  if ((slots <= 1 || slots == 3 || slots == 5 || slots == 6) && h->lv[level].b == 0) {
     h->err = "set_block_config: the staged, streamed and tensor-core forms are for coarse levels";
     return R3MG_E_ARG;
   }
@@ -3231,12 +3251,12 @@ r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int sl
   if (h->mr_M == 0) { h->err = "set_block_config: no block solve has run yet (nothing tuned)"; return R3MG_E_ARG; }
   auto& Sv = h->mr_S[fp32 ? 1 : 0];
   if ((int)Sv.size() != h->L) { h->err = "set_block_config: this precision is not tuned yet"; return R3MG_E_ARG; }
-  if (slots == 5 && (!fp32 || h->mr_M != 16 || h->lv[level].b > kTcRows)) {
+  if ((slots == 5 || slots == 6) && (!fp32 || h->mr_M != 16 || h->lv[level].b > kTcRows)) {
     h->err = "set_block_config: the tcgen05 form is FP32 with 16 columns and boxes of at most 32 rows";
     return R3MG_E_ARG;
   }
   const int CL = h->mr_M / (fp32 ? 4 : 2);
-  if (slots != 3 && slots != 5 && CL * (slots > 8 ? slots - 10 : slots) > 32) {
+  if (slots != 3 && slots != 5 && slots != 6 && CL * (slots > 8 ? slots - 10 : slots) > 32) {
     h->err = "set_block_config: too many slots for the column count";
     return R3MG_E_ARG;
   }

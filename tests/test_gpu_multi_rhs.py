@@ -181,8 +181,9 @@ def test_block_pcg_after_update_values(trio):
 @pytest.mark.parametrize("fp32", [False, True])
 def test_block_kernel_forms_on_coarse_levels(trio, fp32):
     """Every coarse-level block kernel (window gathered through L1 with 2/4/8 entry slots, window
-    staged in shared memory, block rows streamed by the copy engine, tensor cores through mma.sync
-    and through tcgen05 with a TMEM accumulator) gives the oracle's products."""
+    staged in shared memory, block rows streamed by the copy engine, tensor cores through mma.sync,
+    through tcgen05 with a TMEM accumulator, and through the warp-specialised tcgen05 kernel with
+    the A operand in TMEM) gives the oracle's products."""
     P, params, H, Hm, Ho = trio
     Hx = Hm if fp32 else H
     m = 16
@@ -195,22 +196,23 @@ def test_block_kernel_forms_on_coarse_levels(trio, fp32):
         ref = (A @ X.T).T
         absA = abs(A)
         k = np.diff(A.indptr)
-        for slots in (5, 3, 1, 0, 2, 4, 8):
+        for slots in (6, 5, 3, 1, 0, 2, 4, 8):
             if not fp32 and slots == 8:
                 continue                                    # FP64, 16 columns: 8 lanes per row slice
-            if not fp32 and slots in (3, 5):
+            if not fp32 and slots in (3, 5, 6):
                 with pytest.raises(RuntimeError):           # the tensor-core form is FP32 only
                     Hx.set_block_config(lev, slots, fp32=fp32)
                 continue
             Hx.set_block_config(lev, slots, fp32=fp32)
             assert Hx.block_config(fp32=fp32)[lev] == slots
             Y = Hx.level_apply_multi(lev, torch.tensor(X, device="cuda"), fp32=fp32).cpu().numpy()
+            assert Hx.device_status() == 0, (lev, slots)     # no bounded wait of the kernel ran out
             for c in range(m):
                 if fp32:
                     # FP32 dot-product rounding; the tensor-core form adds its TF32 head/tail
                     # splitting error (at most 3 * 2^-20 = 48 * 2^-24 per product, truncation) and
                     # tensor-core accumulation (taken as 2 units of 2^-24 per entry)
-                    kk = 2 * k + 64 if slots in (3, 5) else k + 2
+                    kk = 2 * k + 64 if slots in (3, 5, 6) else k + 2
                     bound = kk * 2.0 ** -24 * (absA @ np.abs(X[c]))
                     assert np.all(np.abs(Y[c] - ref[c]) <= bound), (lev, slots, c)
                 else:
