@@ -3,7 +3,8 @@
 Builds the Poisson systems the R-tree multilevel solver is applied to: the
 model problem of Section 2 (eqs. (poisson), (weakform), (discweakform)),
 continuous Q_p Lagrange elements on a structured, optionally perturbed
-[0,1]^d mesh, Dirichlet nodes eliminated.  This module holds none of the
+[0,1]^d mesh, or continuous P_p elements on its Kuhn triangulation (the
+simplicial elements of Section 5), Dirichlet nodes eliminated.  This module holds none of the
 multilevel method's arithmetic; the CPU oracle and the GPU library both
 consume what it returns, and neither is imported here.
 
@@ -51,6 +52,14 @@ def _load():
         lib.fem_l2_error.restype = ctypes.c_double
         lib.fem_gll01.argtypes = [ctypes.c_int, ctypes.c_void_p]
         lib.fem_gll01.restype = None
+        lib.fem_simplex_sizes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, i64p]
+        lib.fem_simplex_sizes.restype = ctypes.c_int
+        lib.fem_simplex_assemble.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_uint64, ctypes.c_int] + [ctypes.c_void_p] * 6
+        lib.fem_simplex_assemble.restype = ctypes.c_int
+        lib.fem_simplex_l2_error.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_uint64, ctypes.c_void_p]
+        lib.fem_simplex_l2_error.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -118,12 +127,40 @@ def poisson(dim: int, N: int, p: int, perturb: float = 0.0, seed: int = 0, kappa
                    meta={"kappa_modes": kappa_modes, "rhs": rhs})
 
 
+def poisson_simplex(dim: int, N: int, p: int, perturb: float = 0.0, seed: int = 0, rhs: str = "sine") -> Problem:
+    """Assemble -lap u = f on [0,1]^dim with continuous P_p elements on the Kuhn triangulation
+    of the N^dim mesh (every cell split into dim! simplices the same way; p <= 4 in 2D, <= 3 in
+    3D).  Support points are the equispaced barycentric lattice points of the affine simplices,
+    which together form the (N p + 1)^dim grid; boundary nodes are eliminated and the free nodes
+    numbered lexicographically as for Q_p.  perturb and seed move the interior cell vertices as
+    in poisson(); rhs as in poisson()."""
+    lib = _load()
+    n = ctypes.c_int64(); nnz = ctypes.c_int64()
+    if lib.fem_simplex_sizes(dim, N, p, ctypes.byref(n), ctypes.byref(nnz)) != 0:
+        raise ValueError("bad simplex mesh parameters")
+    n, nnz = int(n.value), int(nnz.value)
+    coords = np.empty((n, dim), np.float64)
+    rowptr = np.empty(n + 1, np.int64)
+    colidx = np.empty(nnz, np.int32)
+    vals = np.empty(nnz, np.float64)
+    b = np.empty(n, np.float64)
+    uex = np.empty(n, np.float64)
+    kind = {"sine": 0, "one": 1}[rhs]
+    rc = lib.fem_simplex_assemble(dim, N, p, float(perturb), int(seed) & (2**64 - 1), kind, coords.ctypes.data,
+                                  rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data, b.ctypes.data,
+                                  uex.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"fem_simplex_assemble failed ({rc})")
+    return Problem(dim, N, p, perturb, seed, coords, rowptr, colidx, vals, b, uex,
+                   meta={"kappa_modes": 0, "rhs": rhs, "element": "P"})
+
+
 def l2_error(prob: Problem, u: np.ndarray) -> float:
     """L2 error of the FE function with free coefficients u against prod sin(pi x_a)."""
     lib = _load()
     u = np.ascontiguousarray(u, dtype=np.float64)
-    return float(lib.fem_l2_error(prob.dim, prob.N, prob.p, float(prob.perturb), int(prob.seed) & (2**64 - 1),
-                                  u.ctypes.data))
+    f = lib.fem_simplex_l2_error if prob.meta.get("element") == "P" else lib.fem_l2_error
+    return float(f(prob.dim, prob.N, prob.p, float(prob.perturb), int(prob.seed) & (2**64 - 1), u.ctypes.data))
 
 
 def gll01(p: int) -> np.ndarray:
