@@ -32,22 +32,34 @@ struct LevelView {
   int win_max = 0;                    // largest window (padded to 4)
   int max_box_rows = 0;               // rows of the largest box (own-row staging)
   const int32_t* row_order = nullptr; // fine: per box, local rows longest first (balances the groups)
+  int keep = 0;                       // values fit half of L2: cached loads, so the next step of
+                                      // the same level finds them there (else streaming loads)
 };
 
 template <typename T>
 struct Vec4;
 template <>
 struct Vec4<float> {
-  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
-    float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {   // streamed (read once)
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4], int keep) {
+    const float4 a = keep ? __ldg(reinterpret_cast<const float4*>(p)) : __ldcs(reinterpret_cast<const float4*>(p));
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   }
 };
 template <>
 struct Vec4<double> {
-  static __device__ __forceinline__ void load(const double* p, double (&v)[4]) {
-    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
-    double2 c = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+  static __device__ __forceinline__ void load(const double* p, double (&v)[4]) {   // streamed (read once)
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldcs(q), c = __ldcs(q + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
+  }
+  static __device__ __forceinline__ void load(const double* p, double (&v)[4], int keep) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = keep ? __ldg(q) : __ldcs(q);
+    const double2 c = keep ? __ldg(q + 1) : __ldcs(q + 1);
     v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
   }
 };
@@ -161,12 +173,14 @@ template <typename T, int U, bool FINE>
 struct Chunk {
   T v[U][4];
   uint2 q[U];   // fine: packed indices; coarse: q[u].x = window position of the step's first entry
-  __device__ __forceinline__ void load(const T* vals, const uint16_t* idx, int64_t k, int64_t k0, int64_t k1, int G) {
+  __device__ __forceinline__ void load(const T* vals, const uint16_t* idx, int64_t k, int64_t k0, int64_t k1, int G,
+                                      int keep) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t kk = k + (int64_t)u * 4 * G;
       if (kk < k1) {
-        Vec4<T>::load(vals + kk, v[u]);
+        if constexpr (FINE) Vec4<T>::load(vals + kk, v[u]);   // the fine level never fits L2
+        else Vec4<T>::load(vals + kk, v[u], keep);
         if constexpr (FINE) q[u] = __ldcs(reinterpret_cast<const uint2*>(idx + kk));
         else q[u] = make_uint2((unsigned)(kk - k0), 0u);
       } else {
@@ -300,7 +314,7 @@ __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& e
       // U steps of 4 entries per lane are loaded before any is consumed: more bytes in flight
       for (int64_t k = k0 + 4 * lane; k < k1; k += 4 * G * U) {
         Chunk<T, U, FINE> c;
-        c.load(L.vals, L.idx, k, k0, k1, G);
+        c.load(L.vals, L.idx, k, k0, k1, G, L.keep);
         c.consume(win, a);
       }
       const T s = group_sum<G>(a[0] + a[1]);
@@ -312,7 +326,7 @@ __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& e
     if (lr >= 0) { k0 = rp[lr]; k1 = rp[lr + 1]; }
     int64_t k = k0 + 4 * lane;
     Chunk<T, U, FINE> cur;
-    if (nit > 0) cur.load(L.vals, L.idx, k, k0, k1, G);
+    if (nit > 0) cur.load(L.vals, L.idx, k, k0, k1, G, L.keep);
     for (int it = 0; it < nit; ++it) {
       T a[2] = {T(0), T(0)};
       const int lr_now = lr;
@@ -330,7 +344,7 @@ __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& e
           nk = nk0 + 4 * lane;
         }
         Chunk<T, U, FINE> nxt;
-        nxt.load(L.vals, L.idx, nk, nk0, nk1, G);   // loads nothing past the row's end
+        nxt.load(L.vals, L.idx, nk, nk0, nk1, G, L.keep);   // loads nothing past the row's end
         cur.consume(win, a);
         cur = nxt;
         k = nk;

@@ -252,6 +252,8 @@ LevelView<T> view(const Level& L) {
   else { v.vals = (const T*)L.v32; v.dinv = (const T*)L.dinv32; }
   v.max_slots = L.max_slots; v.win_max = L.win_max; v.max_box_rows = L.max_box_rows;
   v.row_order = L.row_order;
+  // a coarse level whose values fit half of L2 keeps them there between its consecutive steps
+  v.keep = (L.b > 0 && L.stored * (int64_t)sizeof(T) <= ((int64_t)64 << 20)) ? 1 : 0;
   return v;
 }
 
@@ -342,6 +344,11 @@ int launch_level(const Level& L, const T* xin, Ep ep, double* part, cudaStream_t
   // products on a level whose step takes the staged symmetric form (lanes = CTAs per SM) run on
   // the register form with 16 lanes per row
   switch (c.form == 7 ? 16 : c.G) {
+    case 2:   // two lanes per row: fine FP64 rows only (shorter reductions, finer row tails)
+      if constexpr (sizeof(T) == 8) {
+        if (fine) { launch_level_g<T, 2, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break; }
+      }
+      [[fallthrough]];
     case 4: fine ? launch_level_g<T, 4, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 4, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
     case 8: fine ? launch_level_g<T, 8, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 8, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
     case 16: fine ? launch_level_g<T, 16, true>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp) : launch_level_g<T, 16, false>(v, xin, ep, part, s, pipe, nsm, pf, nt, u, sp); break;
@@ -928,7 +935,8 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
   if (dn) CK(cudaMemsetAsync(dn, 0, nb, s));
   const bool fine = (A.b == 0);
   std::vector<Level::KConf> cand;
-  for (int G : {4, 8, 16, 32}) {
+  for (int G : {2, 4, 8, 16, 32}) {
+    if (G == 2 && !(fine && sizeof(T) == 8)) continue;
     if (fine && G == 32) continue;
     if (!fine && G < 8 && sizeof(T) == 4) continue;   // coarse FP32 rows keep 16-byte loads per 8+ lanes
     for (int nt : {128, 256})
@@ -1874,7 +1882,8 @@ void launch_persistent_batch(r3mg_hierarchy* h, double rtol, int budget) {
   for (int l = 0; l < L; ++l) {
     Level& V = h->lv[l];
     A.lv[l] = view<T>(V);
-    A.G[l] = V.conf[pi].form == 7 ? 16 : V.conf[pi].G;   // form 7: the lanes field holds CTAs per SM
+    // form 7 keeps CTAs per SM in the lanes field; the persistent kernel has no 2-lane rows
+    A.G[l] = V.conf[pi].form == 7 ? 16 : std::max(4, V.conf[pi].G);
     A.x[l] = (T*)V.x; A.r[l] = (T*)V.r; A.d[l][0] = (T*)V.d[0]; A.d[l][1] = (T*)V.d[1];
     A.dinv[l] = Dinv<T>(V);
     A.P[l] = (l + 1 < L) ? Pmat<T>(h, l) : nullptr;
@@ -1887,7 +1896,7 @@ void launch_persistent_batch(r3mg_hierarchy* h, double rtol, int budget) {
   Level& F = h->lv[0];
   A.box_of_tree = h->box_of_tree;
   A.Ainv = Ainv<T>(h); A.moff = h->d_moff; A.mld = h->d_mld; A.cof = h->d_cof;
-  A.f64 = view<double>(F); A.G64 = F.conf[0].G;
+  A.f64 = view<double>(F); A.G64 = std::max(4, F.conf[0].G);
   smem = std::max(smem, level_smem_bytes(view<double>(F)));
   A.cx = h->cx; A.cr = h->cr; A.cp = h->cp; A.cq = h->cq; A.cz = h->cz;
   A.S = h->bs;
@@ -3487,9 +3496,10 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
       drop_graphs(h);
     });
   }
-  if (!h || level < 0 || level >= h->L || form < 0 || form > 6 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32) ||
+  const bool two = lanes == 2 && level == 0 && !fp32 && (form == 0 || form == 2 || form == 3 || form == 5 || form == 6);
+  if (!h || level < 0 || level >= h->L || form < 0 || form > 6 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && !two) ||
       (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || (form == 1 && threads == 128)) {
-    if (h) h->err = "set_kernel_config: invalid level, form (0..7), lanes (4,8,16,32; 1..8 for form 7) or threads (128 register forms only, 256, 512, 1024)";
+    if (h) h->err = "set_kernel_config: invalid level, form (0..7), lanes (4,8,16,32; 2 on the FP64 fine level's register forms; 1..8 for form 7) or threads (128 register forms only, 256, 512, 1024)";
     return R3MG_E_ARG;
   }
   Level& A = h->lv[level];
