@@ -400,10 +400,18 @@ r3mg_status r3mg_set_coarse_mode(r3mg_hierarchy* h, int mode);
  * barrier whose waits are bounded (r3mg_set_wait_limit; on expiry the kernel returns and the
  * solve reports R3MG_E_TIMEOUT), and skip the work of problems that have stopped.  Every
  * problem's iterates are the same in both modes.  Level kernels run in the register form with the
- * lanes per row tuned for each level.  Errors: R3MG_E_ARG (not a batched hierarchy),
- * R3MG_E_LIMIT (more than 8 levels).
+ * lanes per row tuned for each level.  mode 2 (the default of a batched hierarchy): automatic --
+ * the first solve runs mode 0 and the second mode 1, each timed with CUDA events per iteration of
+ * the loop, and later solves take the faster (mode 0 alone beyond 8 levels); since both give the
+ * same iterates, the choice changes no result; setting mode 2 again restarts the measurement.  Errors: R3MG_E_ARG (not a batched hierarchy, mode
+ * outside 0..2), R3MG_E_LIMIT (mode 1 with more than 8 levels).
  */
 r3mg_status r3mg_set_batch_mode(r3mg_hierarchy* h, int mode);
+
+/* The batched loop's mode setting (0, 1, 2), the form the last solve used (0 or 1), and the
+ * per-iteration loop times measured by the automatic mode (ms; -1 where not measured yet).
+ * Any output may be NULL. */
+r3mg_status r3mg_get_batch_mode(const r3mg_hierarchy* h, int* mode, int* used, float* ms_graph, float* ms_persistent);
 
 /*
  * Limit of the bounded mbarrier waits of the copy-engine-streamed kernels on this hierarchy:

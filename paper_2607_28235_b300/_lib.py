@@ -121,6 +121,7 @@ def lib():
         "r3mg_set_wait_limit": (ip, [vp, ctypes.c_longlong, i32]),
         "r3mg_set_coarse_mode": (ip, [vp, i32]),
         "r3mg_set_batch_mode": (ip, [vp, i32]),
+        "r3mg_get_batch_mode": (ip, [vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_float), P(ctypes.c_float)]),
         "r3mg_wait_selftest": (ip, [ctypes.c_longlong, P(ctypes.c_int), vp]),
         "r3mg_setup_device": (ip, [i64, i32, vp, vp, vp, vp, P(_Params), vp, P(vp)]),
         "r3mg_last_error": (ctypes.c_char_p, [vp]),

@@ -193,8 +193,11 @@ struct r3mg_hierarchy {
   float* L32 = nullptr;
   double* ctmp = nullptr;             // the forward substitution's result (nc values, either precision)
   // batched solves: 0 = the iteration loop as a graph of per-step kernels, 1 = one persistent
-  // cooperative kernel for the whole loop (r3mg_set_batch_mode)
-  int batch_mode = 0;
+  // cooperative kernel for the whole loop (r3mg_set_batch_mode); 2 = automatic: the first two
+  // solves time one form each (per iteration of the loop), later solves take the faster
+  int batch_mode = 2;
+  float batch_ms_it[2] = {-1.f, -1.f};
+  int batch_used = 0;
   unsigned* pbar = nullptr;           // persistent solve: grid-barrier counter and generation
   int* pany = nullptr;                // persistent solve: running problems per iteration
   int pany_cap = 0;
@@ -2008,7 +2011,20 @@ r3mg_status krylov_batch(r3mg_hierarchy* h, double rtol, int maxit, int* iters, 
     k_bvc_init<T><<<gv, 256, 0, s>>>(h->cr, n, (T*)F.r, (T*)F.x, (T*)F.d[0], Dinv<T>(F), B0.c0, B0.rprob);
     CK(cudaGetLastError());
     const int budget = maxit - *std::min_element(its_total.begin(), its_total.end());
-    if (h->batch_mode == 1) {
+    int mode = h->batch_mode;
+    if (mode == 2) {   // automatic: time each form once, then keep the faster
+      if (h->L > kPMaxLevels || h->batch_ms_it[0] < 0.f) mode = 0;
+      else if (h->batch_ms_it[1] < 0.f) mode = 1;
+      else mode = h->batch_ms_it[1] < h->batch_ms_it[0] ? 1 : 0;
+    }
+    const bool timing = h->batch_mode == 2 && h->batch_ms_it[mode] < 0.f;
+    cudaEvent_t te0 = nullptr, te1 = nullptr;
+    if (timing) {
+      CK(cudaEventCreate(&te0)); CK(cudaEventCreate(&te1));
+      CK(cudaEventRecord(te0, s));
+    }
+    h->batch_used = mode;
+    if (mode == 1) {
       launch_persistent_batch<T>(h, rtol, budget);
     } else {
     // the loop graph, captured once per (rtol, maxit)
@@ -2063,16 +2079,24 @@ r3mg_status krylov_batch(r3mg_hierarchy* h, double rtol, int maxit, int* iters, 
     }
     CK(cudaGraphLaunch(h->bgraph, s));
     }
+    if (timing) CK(cudaEventRecord(te1, s));
     std::vector<int> itsh(np);
     int err = 0;
     CK(cudaMemcpyAsync(itsh.data(), S.its, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&err, S.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (timing) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, te0, te1));
+      const int itmax = *std::max_element(itsh.begin(), itsh.end());
+      if (itmax > 0) h->batch_ms_it[mode] = ms / (float)itmax;
+      cudaEventDestroy(te0); cudaEventDestroy(te1);
+    }
     if (err) {
       CK(cudaMemsetAsync(S.err, 0, sizeof(int), s));
       throw Fail{R3MG_E_BREAKDOWN, "batched CG breakdown: p^T A p <= 0 or non-finite scalar"};
     }
-    if (h->batch_mode == 1) {
+    if (mode == 1) {
       int terr = 0;
       CK(cudaMemcpy(&terr, h->tma_err, sizeof(int), cudaMemcpyDeviceToHost));
       if (terr) {
@@ -3818,11 +3842,21 @@ r3mg_status r3mg_set_coarse_mode(r3mg_hierarchy* h, int mode) {
   });
 }
 
+r3mg_status r3mg_get_batch_mode(const r3mg_hierarchy* h, int* mode, int* used, float* ms_graph, float* ms_persistent) {
+  if (!h) return R3MG_E_ARG;
+  if (mode) *mode = h->batch_mode;
+  if (used) *used = h->batch_used;
+  if (ms_graph) *ms_graph = h->batch_ms_it[0];
+  if (ms_persistent) *ms_persistent = h->batch_ms_it[1];
+  return R3MG_OK;
+}
+
 r3mg_status r3mg_set_batch_mode(r3mg_hierarchy* h, int mode) {
-  if (!h || (mode != 0 && mode != 1)) return R3MG_E_ARG;
+  if (!h || mode < 0 || mode > 2) return R3MG_E_ARG;
   if (h->bl.empty()) { h->err = "set_batch_mode: not a batched hierarchy"; return R3MG_E_ARG; }
   if (mode == 1 && h->L > kPMaxLevels) { h->err = "set_batch_mode: more than 8 levels"; return R3MG_E_LIMIT; }
   h->batch_mode = mode;
+  if (mode == 2) h->batch_ms_it[0] = h->batch_ms_it[1] = -1.f;   // measure both forms again
   return R3MG_OK;
 }
 

@@ -439,8 +439,17 @@ class BatchHierarchy(Hierarchy):
         self.levels = self.info()["levels"]
 
     def set_batch_mode(self, mode: int):
-        """0: the iteration loop as a graph of per-step kernels; 1: one persistent cooperative kernel."""
+        """0: the iteration loop as a graph of per-step kernels; 1: one persistent cooperative kernel;
+        2 (default): automatic, the faster of the two as timed on the first two solves."""
         _check(lib().r3mg_set_batch_mode(self._h, int(mode)), self._h)
+
+    def batch_mode(self) -> dict:
+        """Loop mode setting (0 graph, 1 persistent, 2 automatic), the form the last solve used, and
+        the automatic mode's per-iteration times of both forms (ms, -1 until measured)."""
+        m = ctypes.c_int(0); u = ctypes.c_int(0); g = ctypes.c_float(0); pk = ctypes.c_float(0)
+        _check(lib().r3mg_get_batch_mode(self._h, ctypes.byref(m), ctypes.byref(u), ctypes.byref(g), ctypes.byref(pk)),
+               self._h)
+        return {"mode": m.value, "used": u.value, "ms_per_iteration": {"graph": g.value, "persistent": pk.value}}
 
     def level_offsets(self, level: int) -> np.ndarray:
         out = np.empty(self.nprob + 1, np.int64)

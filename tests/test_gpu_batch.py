@@ -115,6 +115,29 @@ def test_persistent_batched_solve_equals_graph_loop(batch, precision):
     assert len(set(itp.tolist())) > 1          # problems stop at different iterations
 
 
+def test_automatic_batch_mode_times_both_forms(batch):
+    """The default loop mode runs the graph form on the first solve and the persistent form on the
+    second, timing each per loop iteration, and keeps the faster afterwards; every solve gives the
+    same bits."""
+    probs, bs, H, Hm, orc = batch
+    b = torch.tensor(np.concatenate(bs), device="cuda")
+    H.set_batch_mode(2)
+    m0 = H.batch_mode()
+    assert m0["mode"] == 2 and m0["ms_per_iteration"] == {"graph": -1.0, "persistent": -1.0}
+    xs = []
+    for k in range(3):
+        x, its, rel = H.pcg(b, rtol=1e-9)
+        xs.append(x)
+        m = H.batch_mode()
+        if k < 2:
+            assert m["used"] == k
+    t = m["ms_per_iteration"]
+    assert t["graph"] > 0 and t["persistent"] > 0
+    assert m["used"] == (1 if t["persistent"] < t["graph"] else 0)
+    assert torch.equal(xs[0], xs[1]) and torch.equal(xs[1], xs[2])
+    H.set_batch_mode(0)
+
+
 def test_persistent_batched_barrier_expiry_is_reported(batch):
     """A grid-barrier wait that cannot complete (CTA 0 withholds its first arrival) runs out after
     the wait limit: every CTA leaves, the solve reports R3MG_E_TIMEOUT, and the next solve works."""
