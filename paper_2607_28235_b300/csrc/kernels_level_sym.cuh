@@ -48,7 +48,7 @@ __device__ __forceinline__ float4 sym_ld(const float* p) {
 // memory) and the upper x window in `swin`: row partials reduced into ybuf, column sums of the
 // off-diagonal upper blocks into tbuf.  Shared by the streamed and the staged kernels, so both give
 // the same bits.
-template <bool SMEM>
+template <bool SMEM, int WAVE = 8>
 __device__ __forceinline__ void sym_box(const SymView& V, int64_t B, int W, int Wp, const float* swin,
                                         const float* base, float* __restrict__ ybuf, float* __restrict__ tbuf,
                                         float (&ysum)[kSymThreads / 32][32]) {
@@ -62,15 +62,15 @@ __device__ __forceinline__ void sym_box(const SymView& V, int64_t B, int W, int 
     const float4 xw = *reinterpret_cast<const float4*>(swin + 4 * c4);
     float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int q0r = 0; q0r < kSymMaxB; q0r += 8) {
+    for (int q0r = 0; q0r < kSymMaxB; q0r += WAVE) {
       if (q0r >= b) break;
-      float4 a[8];
+      float4 a[WAVE];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
+      for (int j = 0; j < WAVE; ++j)
         a[j] = (q0r + j < b) ? sym_ld<SMEM>(base + (int64_t)(q0r + j) * Wp + 4 * c4)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < WAVE; ++j) {
         const int q = q0r + j;
         yp[q] += a[j].x * xw.x + a[j].y * xw.y + a[j].z * xw.z + a[j].w * xw.w;
         const float xq = (q < b) ? swin[q] : 0.f;   // x_B: the diagonal slot opens the window
@@ -111,12 +111,13 @@ __device__ __forceinline__ void sym_box(const SymView& V, int64_t B, int W, int 
 // One CTA (128 threads) per box.  The box's upper window (x over the diagonal and upper
 // neighbour slots) is staged in shared memory; each thread owns 4 consecutive columns of the
 // box's upper rows (one 16-byte load per row, coalesced along the row), walks all b rows in
-// groups of 8 loads in flight, and keeps
+// waves of WAVE loads in flight (8, or 4 for fewer registers and more resident CTAs), and keeps
 //   * the row partials y_q += A[q, cols] . x_win[cols] for every row q (registers), and
 //   * the column sums t_cols = sum_q A[q, cols] x_B[q] (A_BB'^T x_B for its upper slots).
 // The row partials are reduced across each warp by a halving exchange (31 shuffles leave lane q
 // with row q's warp sum) and across the 4 warps in a fixed order, so the result is deterministic.
-__global__ void __launch_bounds__(kSymThreads) k_sym_block(SymView V, const float* __restrict__ xin,
+template <int WAVE>
+__global__ void __launch_bounds__(kSymThreads, WAVE == 4 ? 8 : 6) k_sym_block(SymView V, const float* __restrict__ xin,
                                                           float* __restrict__ ybuf, float* __restrict__ tbuf) {
   extern __shared__ __align__(16) float swin[];
   __shared__ float ysum[kSymThreads / 32][32];
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kSymThreads) k_sym_block(SymView V, const floa
     for (int t = W + tid; t < Wp; t += kSymThreads) swin[t] = 0.f;
     cp_async_wait_all();
     __syncthreads();
-    sym_box<false>(V, B, W, Wp, swin, V.vals + V.up_base[B], ybuf, tbuf, ysum);
+    sym_box<false, WAVE>(V, B, W, Wp, swin, V.vals + V.up_base[B], ybuf, tbuf, ysum);
     __syncthreads();   // the window and ysum are free for the next box
   }
 }

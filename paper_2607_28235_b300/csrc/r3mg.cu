@@ -617,9 +617,11 @@ void sym_step(r3mg_hierarchy* h, const Level& A, const float* d, SymCheb ep) {
     k_sym_block_staged<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(
         A.sym, d, A.sym_y, A.sym_t, cap, c.err, c.wait, c.withhold);
   } else {
+    // form 4: the lanes field selects the load wave (4 rows, else 8)
     const size_t sm = sizeof(float) * (size_t)A.sym.win_max;
-    ensure_smem((const void*)k_sym_block, sm);
-    k_sym_block<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
+    auto kern = A.conf[1].G == 4 ? k_sym_block<4> : k_sym_block<8>;
+    ensure_smem((const void*)kern, sm);
+    kern<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
   }
   k_sym_finish<<<grid_for(A.n), 256, 0, h->stream>>>(A.sym, A.sym_y, A.sym_t, ep);
   CK(cudaGetLastError());
@@ -955,6 +957,7 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
       for (int nt : {256, 512, 1024}) if (G >= 8) cand.push_back({1, G, nt, 0.f, 0});
     if (sizeof(T) == 4 && A.sym_ok && G == 16 && !product) {
       cand.push_back({4, G, 128, 0.f, 0});
+      cand.push_back({4, 4, 128, 0.f, 0});   // symmetric form with 4-row load waves
       for (int cps : {2, 3, 4, 5})   // staged form: the lanes field holds the resident CTAs per SM
         if (sym_stage_cap(A, cps) > 0) cand.push_back({7, cps, 128, 0.f, 0});
     }

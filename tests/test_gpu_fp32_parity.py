@@ -197,7 +197,8 @@ def test_fp32_vcycle_vs_oracle_each_form(case, form):
     H.close()
 
 
-@pytest.mark.parametrize("form,cps", [("symmetric_block_staged", 1), ("symmetric_block_staged", 4)])
+@pytest.mark.parametrize("form,cps", [("symmetric_block_staged", 1), ("symmetric_block_staged", 4),
+                                      ("symmetric_block", 4)])   # the last: 4-row load waves
 def test_staged_symmetric_step_same_bits_as_streamed(case, form, cps):
     """The staged symmetric kernel (one bulk copy of each box's upper slice into shared memory;
     with a stage sized for 4 CTAs per SM the largest slices are read from global memory instead)
