@@ -359,7 +359,7 @@ __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& e
 // PIPE: persistent CTAs with two stages (the next box staged while the current one computes).
 // PF: an L2 bulk prefetch of each box's matrix slice.  SP: software-pipelined row loop.
 template <typename T, int G, bool FINE, class Ep, int U, bool PIPE, bool PF, bool SP>
-__global__ void __launch_bounds__(256) level_kernel(LevelView<T> L, const T* __restrict__ xin, Ep ep,
+__global__ void __launch_bounds__(256, 4) level_kernel(LevelView<T> L, const T* __restrict__ xin, Ep ep,
                                                     double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8];
