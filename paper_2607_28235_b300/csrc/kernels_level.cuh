@@ -7,7 +7,8 @@
 // fine level and no index at all on coarse levels (dense b x b blocks stored row by row).
 // Rows of the box are spread over groups of G lanes; each lane loads 4 consecutive entries
 // per step with 16-byte vector loads; the G partial sums are combined by warp shuffles and
-// the group leader applies the epilogue (plain product, Chebyshev-Jacobi step, residual...).
+// the rows' sums (FP64: up to 8 partials per row) are parked in shared memory, and one thread
+// per row then applies the epilogue (plain product, Chebyshev-Jacobi step, residual...).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -114,7 +115,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- epilogues
-// Each gets (row, y = (A x)_row) from the group leader; `acc` is a per-thread partial sum
+// Each gets (row, y = (A x)_row) from one thread (the register kernels: a thread per row once the
+// box's rows are summed; the TMA form: the group leader); `acc` is a per-thread partial sum
 // folded into one value per CTA written to `part[blockIdx.x]` when the epilogue wants it.
 
 // Epilogues.  Each names up to kAuxMax own-row vectors (src(j), staged when stage(j)); the
@@ -153,17 +155,24 @@ struct TEpCheb {
   }
 };
 
+// FP64 rows park up to kParkLanes partial sums each, kParkStride apart (an odd stride of
+// doubles, so the epilogue pass's reads, one row per thread, meet at most 2-way bank conflicts)
+constexpr int kParkLanes = 8;
+constexpr int kParkStride = 9;
+
 // Shared-memory carve-up of one stage of the register kernels (byte offsets): the window,
-// the epilogue's own-row vectors, the box's row offsets (absolute entry positions, int64) and
-// (fine level) its row order, so that no row waits on a dependent global load for its bounds.
+// the epilogue's own-row vectors, the box's row offsets (absolute entry positions, int64),
+// (fine level) its row order, so that no row waits on a dependent global load for its bounds,
+// and the rows' parked (partial) sums, which the epilogue pass reads.
 struct LevelSmem {
-  size_t aux = 0, rp = 0, ord = 0, total = 0;
+  size_t aux = 0, rp = 0, ord = 0, ys = 0, total = 0;
   static __host__ __device__ size_t up16(size_t v) { return (v + 15) & ~(size_t)15; }
   __host__ __device__ LevelSmem(size_t elem, int win_max, int max_box_rows) {
     aux = up16(elem * (size_t)win_max);
     rp = aux + up16(elem * (size_t)kAuxMax * max_box_rows);
     ord = rp + up16(sizeof(int64_t) * ((size_t)max_box_rows + 1));
-    total = ord + up16(sizeof(int32_t) * (size_t)max_box_rows);
+    ys = ord + up16(sizeof(int32_t) * (size_t)max_box_rows);
+    total = ys + up16(elem * (size_t)(elem == 8 ? kParkStride : 1) * max_box_rows);
   }
 };
 
@@ -173,12 +182,15 @@ template <typename T, int U, bool FINE>
 struct Chunk {
   T v[U][4];
   uint2 q[U];   // fine: packed indices; coarse: q[u].x = window position of the step's first entry
+  int nv;       // steps that start before the row's end (a prefix of the U steps)
   __device__ __forceinline__ void load(const T* vals, const uint16_t* idx, int64_t k, int64_t k0, int64_t k1, int G,
                                       int keep) {
+    nv = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t kk = k + (int64_t)u * 4 * G;
       if (kk < k1) {
+        ++nv;
         if constexpr (FINE) Vec4<T>::load(vals + kk, v[u]);   // the fine level never fits L2
         else Vec4<T>::load(vals + kk, v[u], keep);
         if constexpr (FINE) q[u] = __ldcs(reinterpret_cast<const uint2*>(idx + kk));
@@ -190,17 +202,20 @@ struct Chunk {
       }
     }
   }
-  // FP64: two fused multiply-add chains (one FP64-pipe instruction per stored entry: the FP64
-  // pipe, not HBM, bounds the FP64 form; a product tree adds a multiply and an add per four
-  // entries).  FP32: a short product tree per step (shorter dependent chains).
+  // FP64: one fused multiply-add chain, one FP64-pipe instruction per stored entry (the FP64
+  // pipe, not HBM and not the chain's latency, bounds the FP64 form; a product tree adds a
+  // multiply and an add per four entries, a second chain an add per row), and steps wholly past
+  // the row's end are skipped rather than multiplied by zeros.  FP32: a short product tree per
+  // step, alternating two accumulators (shorter dependent chains).
   __device__ __forceinline__ void consume(const T* win, T (&acc)[2]) const {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       int ii[4];
       if constexpr (FINE) { ii[0] = q[u].x & 0xffff; ii[1] = q[u].x >> 16; ii[2] = q[u].y & 0xffff; ii[3] = q[u].y >> 16; }
       else { const int t = (int)q[u].x; ii[0] = t; ii[1] = t + 1; ii[2] = t + 2; ii[3] = t + 3; }
-      T& a = acc[u & 1];
+      T& a = acc[sizeof(T) == 8 ? 0 : (u & 1)];
       if constexpr (sizeof(T) == 8) {
+        if (u >= nv) break;
 #pragma unroll
         for (int j = 0; j < 4; ++j) a = fma_rn(v[u][j], win[ii[j]], a);
       } else {
@@ -280,7 +295,8 @@ __device__ __forceinline__ void level_stage(const LevelView<T>& L, const T* __re
 // The rows of a staged box: groups of G lanes per row, U steps of 4 entries per lane in flight;
 // SP: software-pipelined row loop (the next chunk -- of the same row, or the group's next row --
 // is loaded into registers before the current chunk is consumed, so loads stay in flight through
-// the arithmetic, the group reduction and the epilogue).
+// the arithmetic and the group reduction).  Every thread of the CTA calls it (the epilogue
+// pass follows a CTA barrier).
 template <typename T, int G, bool FINE, class Ep, int U, bool SP>
 __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& ep, const LevelSmem& lay, int64_t B,
                                               unsigned char* base, double& acc) {
@@ -294,6 +310,20 @@ __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& e
   for (int j = 0; j < kAuxMax; ++j) auxp[j] = reinterpret_cast<T*>(base + lay.aux) + j * L.max_box_rows;
   const int64_t* rp = reinterpret_cast<const int64_t*>(base + lay.rp);
   const int32_t* od = reinterpret_cast<const int32_t*>(base + lay.ord);
+  // A group folds its lanes' sums down to kPL partials and parks them in shared memory; after
+  // the rows, one thread per row adds its partials and applies the epilogue, so the epilogue's
+  // loads and stores are coalesced over consecutive rows.  FP64 stops the shuffle tree at
+  // kParkLanes partials: every FP64 instruction costs the FP64 pipe a whole warp's slot however
+  // few of its lanes are active, so a tree level costs G slots per row and a serial add one,
+  // and the epilogue's FP64 arithmetic runs on full warps instead of one lane per group.
+  constexpr int kPL = sizeof(T) == 8 ? (G < kParkLanes ? G : kParkLanes) : 1;
+  constexpr int kStride = sizeof(T) == 8 ? kParkStride : 1;
+  T* ys = reinterpret_cast<T*>(base + lay.ys);
+  auto finish = [&](int lr, T s) {
+#pragma unroll
+    for (int o = G / 2; o >= kPL; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, G);
+    if (lr >= 0 && lane < kPL) ys[lr * kStride + lane] = s;
+  };
   // local row of this group at row-loop iteration `it` (-1 past the box's end); rows are
   // taken longest first on the fine level (host-built order) so the groups finish together
   auto row_at = [&](int it) -> int {
@@ -317,8 +347,7 @@ __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& e
         c.load(L.vals, L.idx, k, k0, k1, G, L.keep);
         c.consume(win, a);
       }
-      const T s = group_sum<G>(a[0] + a[1]);
-      if (lr >= 0 && lane == 0) ep.post(r0 + lr, lr, s, auxp, acc);
+      finish(lr, sizeof(T) == 8 ? a[0] : a[0] + a[1]);   // FP64: one chain
     }
   } else {
     int lr = row_at(0);
@@ -350,9 +379,15 @@ __device__ __forceinline__ void level_compute(const LevelView<T>& L, const Ep& e
         k = nk;
         if (!same) { lr = nlr; k0 = nk0; k1 = nk1; break; }
       }
-      const T s = group_sum<G>(a[0] + a[1]);
-      if (lr_now >= 0 && lane == 0) ep.post(r0 + lr_now, lr_now, s, auxp, acc);
+      finish(lr_now, sizeof(T) == 8 ? a[0] : a[0] + a[1]);   // FP64: one chain
     }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    T y = ys[t * kStride];
+#pragma unroll
+    for (int j = 1; j < kPL; ++j) y += ys[t * kStride + j];
+    ep.post(r0 + t, t, y, auxp, acc);
   }
 }
 
