@@ -248,8 +248,13 @@ r3mg_status r3mg_level_apply_multi(r3mg_hierarchy* h, int level, int m, int fp32
  * columns, boxes of at most 32 rows, the same TF32 head/tail splitting; its mbarrier waits are
  * bounded as set by r3mg_set_wait_limit and an expiry gives R3MG_E_TIMEOUT), 6 = the same
  * product warp-specialised with the A operand in TMEM (tcgen05.st) and both operands fed by
- * cp.async.bulk six chunks ahead (one CTA per SM; same limits and wait bounds as 5), 10 + slots (12, 14, 18) = fine-level flat row sweep on global column indices
- * (built once, 4 bytes per stored entry), -1 = not tuned yet.  The setter pins one choice (R3MG_E_ARG for an invalid or untuned combination). */
+ * cp.async.bulk six chunks ahead (one CTA per SM; same limits and wait bounds as 5), 10 +
+ * slots (12, 14, 18) = fine-level flat row sweep on global column indices (built once, 4 bytes
+ * per stored entry), 20 = fine level in groups of rows with equal column lists (Q_p: the DoFs
+ * interior to one cell, face or edge; groups of 8, 4, 2 and 1 rows of one box, the column list
+ * stored once and the values entry-major, so one gathered slice of X serves the whole group;
+ * built once on first use, its values gathered again after r3mg_update_values), -1 = not tuned
+ * yet.  The setter pins one choice (R3MG_E_ARG for an invalid or untuned combination). */
 r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots);
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots);
 

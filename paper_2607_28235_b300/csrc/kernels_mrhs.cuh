@@ -624,6 +624,170 @@ __global__ void __launch_bounds__(256) k_mr_rows(const int64_t* __restrict__ row
   }
 }
 
+// ---- grouped fine level.  Rows of one box whose stored column lists are identical (with Q_p
+// elements: the degrees of freedom interior to one cell, or to one face, or to one edge) form a
+// group of R rows.  A group stores its column list once and its values entry-major (entry k of
+// its row r at k*R + r), so each gathered slice of X serves R rows instead of one.  Groups of
+// one size R in {1, 2, 4, 8} are launched together; larger sets of equal rows are split.
+
+// N consecutive values (N * sizeof(T) a multiple of 16 bytes, or one 8- or 4-byte value run;
+// the group layout aligns them), read once (streaming)
+template <int N>
+__device__ __forceinline__ void load_run(const float* p, float (&w)[N]) {
+  if constexpr (N >= 4) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(p) + q);
+      w[4 * q] = a.x; w[4 * q + 1] = a.y; w[4 * q + 2] = a.z; w[4 * q + 3] = a.w;
+    }
+  } else if constexpr (N == 2) {
+    const float2 a = __ldcs(reinterpret_cast<const float2*>(p));
+    w[0] = a.x; w[1] = a.y;
+  } else {
+    w[0] = __ldcs(p);
+  }
+}
+template <int N>
+__device__ __forceinline__ void load_run(const double* p, double (&w)[N]) {
+  if constexpr (N >= 2) {
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+      const double2 a = __ldcs(reinterpret_cast<const double2*>(p) + q);
+      w[2 * q] = a.x; w[2 * q + 1] = a.y;
+    }
+  } else {
+    w[0] = __ldcs(p);
+  }
+}
+// E consecutive column indices (E = 2 or 4; group entry lists start on multiples of 4)
+template <int E>
+__device__ __forceinline__ void load_cols(const int32_t* p, int (&c)[E]) {
+  if constexpr (E == 4) {
+    const int4 a = __ldcs(reinterpret_cast<const int4*>(p));
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+  } else {
+    const int2 a = __ldcs(reinterpret_cast<const int2*>(p));
+    c[0] = a.x; c[1] = a.y;
+  }
+}
+
+// Entry slots per group for R rows and CL lanes per row slice: fewer slots as R grows, so that
+// the slot reduction (R x V values per lane and level) stays small next to the R x V FMAs per entry.
+__host__ __device__ constexpr int mr_group_slots(int R, int CL) {
+  const int want = R == 1 ? 8 : (R == 8 ? 2 : 4);
+  return want * CL <= 32 ? want : 32 / CL;
+}
+
+// Entries per slot step: four for groups of one or two rows, two for larger groups (the R
+// accumulators and the step's R x E values share the registers).
+__host__ __device__ constexpr int mr_group_step(int R) { return R <= 2 ? 4 : 2; }
+
+// Level operator on M columns over the groups of one size R: CL lanes cover the M columns with
+// 16-byte slices, S slots split the group's entries E at a time; each step reads the E column
+// indices and R x E values once per slot and E slices of X per lane (all in flight together),
+// and multiplies them into R accumulators.  After the slot reduction, slot s finishes the
+// group's rows r = s, s + S, ... through the epilogue.
+template <typename T, int M, int R, class Ep>
+__global__ void __launch_bounds__(256) k_mr_grouped(int64_t ng, const int64_t* __restrict__ geoff,
+                                                    const int64_t* __restrict__ gvoff, const int32_t* __restrict__ grows,
+                                                    const int32_t* __restrict__ gcol, const T* __restrict__ gvals,
+                                                    const T* __restrict__ xin, Ep ep, double* __restrict__ part) {
+  constexpr int V = Slice<T>::V, CL = M / V, S = mr_group_slots(R, CL), LPR = CL * S, GPW = 32 / LPR;
+  constexpr int E = mr_group_step(R);
+  static_assert(M % V == 0 && 32 % LPR == 0, "lane layout");
+  __shared__ double red[8][M];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  const int cl = lane % CL, s = (lane / CL) % S, gw = lane / LPR;
+  double dacc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) dacc[v] = 0.0;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = wid * GPW; base < ng; base += nwt * GPW) {   // warp-uniform trip count
+    const int64_t g = base + gw;
+    const bool ok = g < ng;
+    int64_t e0 = 0, e1 = 0, v0 = 0;
+    if (ok) { e0 = geoff[g]; e1 = geoff[g + 1]; v0 = gvoff[g]; }
+    T acc[R][V];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[r][v] = T(0);
+    // group entry counts are multiples of 4, so a step never runs past the group's end
+    for (int64_t e = e0 + (int64_t)E * s; e < e1; e += (int64_t)E * S) {
+      int c[E];
+      load_cols<E>(gcol + e, c);
+      T w[R * E];
+      load_run<R * E>(gvals + v0 + (e - e0) * R, w);
+      Slice<T> xs[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) xs[q].ldg(xin + (int64_t)c[q] * M + cl * V);
+#pragma unroll
+      for (int q = 0; q < E; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[r][v] += w[q * R + r] * xs[q].v[v];
+    }
+#pragma unroll
+    for (int o = CL; o < LPR; o <<= 1)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[r][v] += __shfl_xor_sync(0xffffffffu, acc[r][v], o);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (ok && r % S == s) {
+        Slice<T> out;
+#pragma unroll
+        for (int v = 0; v < V; ++v) out.v[v] = acc[r][v];
+        ep.post(grows[g * R + r], cl * V, out, dacc);
+      }
+    }
+  }
+  if constexpr (Ep::kDot) {
+    if (part != nullptr) {
+#pragma unroll
+      for (int o = CL; o < 32; o <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; ++v) dacc[v] += __shfl_xor_sync(0xffffffffu, dacc[v], o);
+      if (lane < CL)
+#pragma unroll
+        for (int v = 0; v < V; ++v) red[warp][lane * V + v] = dacc[v];
+      __syncthreads();
+      if (threadIdx.x < M) {
+        double t = 0.0;
+        for (int w = 0; w < NW; ++w) t += red[w][threadIdx.x];
+        part[(int64_t)blockIdx.x * M + threadIdx.x] = t;
+      }
+    }
+  }
+}
+
+// The grouped layout's column lists and values, gathered from the per-row layout: one warp per
+// group; entry k of the group's row r is entry k of that row (equal lists, equal padding).
+// gcol_out may be null (values only, for the second precision).
+template <typename T>
+__global__ void __launch_bounds__(256) k_mr_group_gather(int R, int64_t ng, const int64_t* __restrict__ geoff,
+                                                         const int64_t* __restrict__ gvoff,
+                                                         const int32_t* __restrict__ grows,
+                                                         const int64_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ gidx, const T* __restrict__ vals,
+                                                         int32_t* __restrict__ gcol_out, T* __restrict__ gvals_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwt = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nwt) {
+    const int64_t e0 = geoff[g], K = geoff[g + 1] - e0, v0 = gvoff[g];
+    for (int r = 0; r < R; ++r) {
+      const int64_t k0 = row_ptr[grows[g * R + r]];
+      for (int64_t k = lane; k < K; k += 32) {
+        if (r == 0 && gcol_out) gcol_out[e0 + k] = gidx[k0 + k];
+        gvals_out[v0 + k * R + r] = vals[k0 + k];
+      }
+    }
+  }
+}
+
 // Global column of every stored fine-level entry: the window map of its box applied to its
 // 16-bit window index (padding entries keep window position 0, a valid row with value 0).
 template <typename T>

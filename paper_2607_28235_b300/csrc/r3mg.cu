@@ -175,6 +175,17 @@ struct r3mg_hierarchy {
   int prof_cols = 1;                  // columns of the last profiled solve (bytes per launch)
   int64_t mr_graph_kernels = 0;       // kernels in one block V-cycle
   int32_t* mr_gidx = nullptr;         // fine level: global column (tree row) of every stored entry
+  // grouped fine level for the block kernels (rows with equal column lists; k_mr_grouped), built
+  // on first use: classes of 8, 4, 2 and 1 rows per group, class-major
+  bool mrg_built = false;
+  int64_t mrg_ng[4] = {0, 0, 0, 0};   // groups per class
+  int64_t mrg_g0[4] = {0, 0, 0, 0};   // first group of each class
+  int64_t mrg_r0[4] = {0, 0, 0, 0};   // first row slot of each class in mrg_rows
+  int64_t* mrg_geoff = nullptr;       // groups + 1 offsets into mrg_col (entries per group)
+  int64_t* mrg_gvoff = nullptr;       // groups + 1 offsets into the grouped values
+  int32_t* mrg_rows = nullptr;        // R rows per group
+  int32_t* mrg_col = nullptr;         // the groups' column lists (global rows of the level)
+  void* mrg_vals[2] = {nullptr, nullptr};   // grouped values ([0] FP64, [1] FP32), entry-major
   int nsm = 148;
   int tma_ctas = 1;                   // TMA kernel CTAs per SM
   int64_t graph_kernels = 0;          // kernels in one replay of the V-cycle graph
@@ -1009,6 +1020,8 @@ void drop_graphs(r3mg_hierarchy* h) {
   h->graph_state = h->bgraph_state = h->lgraph_state = h->mgraph_state = 0;
 }
 
+void mr_regroup(r3mg_hierarchy* h);
+
 void numeric(r3mg_hierarchy* h, const double* vals_dev) {
   cudaStream_t s = h->stream;
   CK(cudaStreamSynchronize(s));
@@ -1077,6 +1090,7 @@ void numeric(r3mg_hierarchy* h, const double* vals_dev) {
       CK(cudaGetLastError());
     }
   }
+  mr_regroup(h);   // the grouped fine level's own copy of the values, if the block path built one
   CK(cudaStreamSynchronize(s));
 }
 
@@ -2292,6 +2306,168 @@ void mr_build_gidx(r3mg_hierarchy* h) {
   CK(cudaGetLastError());
 }
 
+// The grouped fine level (k_mr_grouped): within each box, rows are keyed by (length, FNV-1a
+// hash of the window index list) and sorted; runs of rows whose lists are equal (compared entry
+// by entry; equal lists have equal padding) are split into groups of 8, 4, 2 and 1 rows.  Built
+// once on the host from the per-row layout's window indices.
+constexpr int kMrGrouped = 20;          // block-config code of the grouped fine level
+constexpr int kMrGroupR[4] = {8, 4, 2, 1};
+
+void mr_build_groups(r3mg_hierarchy* h) {
+  if (h->mrg_built) return;
+  mr_build_gidx(h);
+  const Level& F = h->lv[0];
+  const LevelView<double> v = view<double>(F);
+  const int64_t n = F.n, nbox = F.nbox;
+  std::vector<int64_t> rp(n + 1), br(nbox + 1);
+  std::vector<uint16_t> ix(F.stored);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(rp.data(), v.row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(br.data(), v.box_row, sizeof(int64_t) * (nbox + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ix.data(), v.idx, sizeof(uint16_t) * F.stored, cudaMemcpyDeviceToHost));
+  auto same = [&](int64_t a, int64_t b) {
+    return rp[a + 1] - rp[a] == rp[b + 1] - rp[b] &&
+           std::equal(ix.begin() + rp[a], ix.begin() + rp[a + 1], ix.begin() + rp[b]);
+  };
+  // per box: its rows group by group, class by class, and its group count per class
+  std::vector<std::vector<int32_t>> order(nbox);
+  std::vector<int64_t> cnt(nbox * 4, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t B = 0; B < nbox; ++B) {
+    struct Key { int64_t len; uint64_t hash; int64_t row; };
+    std::vector<Key> key;
+    for (int64_t r = br[B]; r < br[B + 1]; ++r) {
+      uint64_t hsh = 1469598103934665603ull;
+      for (int64_t k = rp[r]; k < rp[r + 1]; ++k) { hsh ^= ix[k]; hsh *= 1099511628211ull; }
+      key.push_back({rp[r + 1] - rp[r], hsh, r});
+    }
+    std::sort(key.begin(), key.end(), [](const Key& a, const Key& b) {
+      return a.len != b.len ? a.len < b.len : a.hash != b.hash ? a.hash < b.hash : a.row < b.row;
+    });
+    std::vector<int32_t> cls[4];
+    auto emit = [&](const std::vector<int64_t>& run) {
+      size_t i = 0;
+      for (int c = 0; c < 4; ++c)
+        for (; run.size() - i >= (size_t)kMrGroupR[c]; i += kMrGroupR[c])
+          for (int q = 0; q < kMrGroupR[c]; ++q) cls[c].push_back((int32_t)run[i + q]);
+    };
+    for (size_t i = 0; i < key.size();) {
+      size_t j = i;
+      while (j < key.size() && key[j].len == key[i].len && key[j].hash == key[i].hash) ++j;
+      // rows [i, j) share the key; split them into lists that are really equal
+      std::vector<char> used(j - i, 0);
+      for (size_t a = i; a < j; ++a) {
+        if (used[a - i]) continue;
+        std::vector<int64_t> run{key[a].row};
+        for (size_t b = a + 1; b < j; ++b)
+          if (!used[b - i] && same(key[a].row, key[b].row)) { used[b - i] = 1; run.push_back(key[b].row); }
+        emit(run);
+      }
+      i = j;
+    }
+    for (int c = 0; c < 4; ++c) {
+      cnt[B * 4 + c] = (int64_t)cls[c].size() / kMrGroupR[c];
+      order[B].insert(order[B].end(), cls[c].begin(), cls[c].end());
+    }
+  }
+  // class-major numbering, boxes in order within a class
+  std::vector<int64_t> boff(nbox * 4);
+  int64_t g = 0, rows = 0;
+  for (int c = 0; c < 4; ++c) {
+    h->mrg_g0[c] = g;
+    h->mrg_r0[c] = rows;
+    for (int64_t B = 0; B < nbox; ++B) { boff[B * 4 + c] = g; g += cnt[B * 4 + c]; }
+    h->mrg_ng[c] = g - h->mrg_g0[c];
+    rows += h->mrg_ng[c] * kMrGroupR[c];
+  }
+  const int64_t NG = g;
+  std::vector<int32_t> grows(rows);
+  std::vector<int64_t> glen(NG);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t B = 0; B < nbox; ++B) {
+    size_t p = 0;
+    for (int c = 0; c < 4; ++c) {
+      const int R = kMrGroupR[c];
+      for (int64_t q = 0; q < cnt[B * 4 + c]; ++q, p += R) {
+        const int64_t gg = boff[B * 4 + c] + q;
+        for (int t = 0; t < R; ++t) grows[h->mrg_r0[c] + (gg - h->mrg_g0[c]) * R + t] = order[B][p + t];
+        glen[gg] = rp[order[B][p] + 1] - rp[order[B][p]];
+      }
+    }
+  }
+  // entry offsets, and value offsets with every class starting on a 16-value boundary (the
+  // kernels read a group entry's R values with 16-byte loads)
+  std::vector<int64_t> geoff(NG + 1), gvoff(NG + 1);
+  geoff[0] = gvoff[0] = 0;
+  int64_t ev = 0;
+  for (int c = 0; c < 4; ++c) {
+    ev = (ev + 15) & ~(int64_t)15;
+    for (int64_t q = h->mrg_g0[c]; q < h->mrg_g0[c] + h->mrg_ng[c]; ++q) {
+      gvoff[q] = ev;
+      ev += glen[q] * kMrGroupR[c];
+      geoff[q + 1] = geoff[q] + glen[q];
+    }
+  }
+  gvoff[NG] = ev;
+  h->mrg_geoff = dalloc<int64_t>(h, NG + 1);
+  h->mrg_gvoff = dalloc<int64_t>(h, NG + 1);
+  h->mrg_rows = dalloc<int32_t>(h, std::max<int64_t>(1, rows));
+  h->mrg_col = dalloc<int32_t>(h, std::max<int64_t>(1, geoff[NG]));
+  CK(cudaMemcpy(h->mrg_geoff, geoff.data(), sizeof(int64_t) * (NG + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->mrg_gvoff, gvoff.data(), sizeof(int64_t) * (NG + 1), cudaMemcpyHostToDevice));
+  if (rows > 0) CK(cudaMemcpy(h->mrg_rows, grows.data(), sizeof(int32_t) * rows, cudaMemcpyHostToDevice));
+  h->mrg_built = true;
+}
+
+// The grouped values of the fine level in precision T (and, with cols, the column lists),
+// gathered on the device from the per-row layout into dst.
+template <typename T>
+void mr_group_gather(r3mg_hierarchy* h, T* dst, bool cols) {
+  const LevelView<T> v = view<T>(h->lv[0]);
+  for (int c = 0; c < 4; ++c) {
+    if (h->mrg_ng[c] == 0) continue;
+    const int grid = (int)std::min<int64_t>((h->mrg_ng[c] + 7) / 8, (int64_t)h->nsm * 16);
+    k_mr_group_gather<T><<<grid, 256, 0, h->stream>>>(kMrGroupR[c], h->mrg_ng[c], h->mrg_geoff + h->mrg_g0[c],
+                                                      h->mrg_gvoff + h->mrg_g0[c], h->mrg_rows + h->mrg_r0[c],
+                                                      v.row_ptr, h->mr_gidx, v.vals, cols ? h->mrg_col : nullptr, dst);
+    CK(cudaGetLastError());
+  }
+}
+
+// Built on first use (the block tuner runs it before any graph capture), in place afterwards.
+template <typename T>
+void mr_group_vals(r3mg_hierarchy* h) {
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  if (h->mrg_vals[pi]) return;
+  mr_build_groups(h);
+  const int64_t NG = h->mrg_g0[3] + h->mrg_ng[3];
+  int64_t nvals = 0;
+  CK(cudaMemcpy(&nvals, h->mrg_gvoff + NG, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  T* gv = dalloc<T>(h, std::max<int64_t>(1, nvals));
+  mr_group_gather<T>(h, gv, h->mrg_vals[1 - pi] == nullptr);   // column lists are gathered once
+  h->mrg_vals[pi] = gv;
+}
+
+// New matrix values (numeric setup again): the grouped copies are gathered again in place, so
+// pointers held by launch arguments stay valid.
+void mr_regroup(r3mg_hierarchy* h) {
+  if (h->mrg_vals[0]) mr_group_gather<double>(h, (double*)h->mrg_vals[0], false);
+  if (h->mrg_vals[1]) mr_group_gather<float>(h, (float*)h->mrg_vals[1], false);
+}
+
+template <typename T, int M, int R, class Ep>
+int mr_launch_grouped(r3mg_hierarchy* h, int c, const T* x, Ep ep, double* part) {
+  constexpr int CL = M / Slice<T>::V, GPW = 32 / (CL * mr_group_slots(R, CL));
+  const int64_t ng = h->mrg_ng[c];
+  if (ng == 0) return 0;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ng + 8 * GPW - 1) / (8 * GPW), (int64_t)h->nsm * 2));
+  k_mr_grouped<T, M, R, Ep><<<grid, 256, 0, h->stream>>>(ng, h->mrg_geoff + h->mrg_g0[c], h->mrg_gvoff + h->mrg_g0[c],
+                                                         h->mrg_rows + h->mrg_r0[c], h->mrg_col,
+                                                         (const T*)h->mrg_vals[sizeof(T) == 4 ? 1 : 0], x, ep, part);
+  CK(cudaGetLastError());
+  return grid;
+}
+
 template <typename T, int M, int S, bool FINE, class Ep>
 void mr_launch(const Level& A, const T* x, Ep ep, double* part, cudaStream_t s, int grid) {
   const LevelView<T> v = view<T>(A);
@@ -2435,6 +2611,15 @@ int mr_level(r3mg_hierarchy* h, const Level& A, const T* x, Ep ep, double* part,
     }
     S = 2;
   }
+  if (fine && S == kMrGrouped) {   // groups of rows with equal column lists, one launch per group size
+    mr_group_vals<T>(h);
+    int np = 0;
+    np += mr_launch_grouped<T, M, 8, Ep>(h, 0, x, ep, part ? part + (int64_t)np * M : nullptr);
+    np += mr_launch_grouped<T, M, 4, Ep>(h, 1, x, ep, part ? part + (int64_t)np * M : nullptr);
+    np += mr_launch_grouped<T, M, 2, Ep>(h, 2, x, ep, part ? part + (int64_t)np * M : nullptr);
+    np += mr_launch_grouped<T, M, 1, Ep>(h, 3, x, ep, part ? part + (int64_t)np * M : nullptr);
+    return std::max(np, 1);
+  }
   if (fine && S > 8) {   // 10 + slots: the flat row sweep on global column indices
     mr_build_gidx(h);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + 7) / 8, (int64_t)h->nsm * 8));
@@ -2515,8 +2700,10 @@ void mr_tune(r3mg_hierarchy* h) {
     CK(cudaMemsetAsync(r, 0, sizeof(T) * A.n * M, s));
     CK(cudaMemsetAsync(d, 0, sizeof(T) * A.n * M, s));
     float best = 1e30f;
-    for (int S : {6, 5, 3, 1, 0, 2, 4, 8, 12, 14, 18}) {
-      if (S == 5 || S == 6) {
+    for (int S : {6, 5, 3, 1, 0, 2, 4, 8, 12, 14, 18, kMrGrouped}) {
+      if (S == kMrGrouped) {
+        if (A.b != 0) continue;
+      } else if (S == 5 || S == 6) {
         if (!mr_tc_fits<T, M, MEpCheb<T, M>>(A)) continue;
       } else if (S == 3) {
         if (A.b == 0 || !mr_mma_ok<T, M, MEpCheb<T, M>>()) continue;
@@ -2556,8 +2743,8 @@ int mr_S64(r3mg_hierarchy* h) {
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       float best = 1e30f;
-      for (int S : {2, 4, 8, 12, 14, 18}) {
-        if (CL * (S > 8 ? S - 10 : S) > 32) continue;
+      for (int S : {2, 4, 8, 12, 14, 18, kMrGrouped}) {
+        if (S != kMrGrouped && CL * (S > 8 ? S - 10 : S) > 32) continue;
         mr_level<double, M>(h, h->lv[0], h->mr_p, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S);
         CK(cudaEventRecord(e0, s));
         for (int k = 0; k < 3; ++k) mr_level<double, M>(h, h->lv[0], h->mr_p, MEpApply<double, M>{h->mr_q, nullptr}, nullptr, S);
@@ -3270,11 +3457,14 @@ r3mg_status r3mg_block_config(r3mg_hierarchy* h, int level, int fp32, int* slots
 r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int slots) {
   if (!h || level < 0 || level >= h->L) return R3MG_E_ARG;
   if (!(slots == 0 || slots == 1 || slots == 2 || slots == 3 || slots == 4 || slots == 5 || slots == 6 ||
-        slots == 8 || slots == 12 || slots == 14 || slots == 18)) {
-    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4, 5, 6, 8, 12, 14 or 18";
+        slots == 8 || slots == 12 || slots == 14 || slots == 18 || slots == kMrGrouped)) {
+    h->err = "set_block_config: slots must be 0, 1, 2, 3, 4, 5, 6, 8, 12, 14, 18 or 20";
     return R3MG_E_ARG;
   }
-  if (slots > 8 && h->lv[level].b != 0) { h->err = "set_block_config: the flat row sweep is for the fine level"; return R3MG_E_ARG; }
+  if (slots > 8 && h->lv[level].b != 0) {
+    h->err = "set_block_config: the flat row sweep and the grouped rows are for the fine level";
+    return R3MG_E_ARG;
+  }
   if ((slots <= 1 || slots == 3 || slots == 5 || slots == 6) && h->lv[level].b == 0) {
     h->err = "set_block_config: the staged, streamed and tensor-core forms are for coarse levels";
     return R3MG_E_ARG;
@@ -3292,7 +3482,7 @@ r3mg_status r3mg_set_block_config(r3mg_hierarchy* h, int level, int fp32, int sl
     return R3MG_E_ARG;
   }
   const int CL = h->mr_M / (fp32 ? 4 : 2);
-  if (slots != 3 && slots != 5 && slots != 6 && CL * (slots > 8 ? slots - 10 : slots) > 32) {
+  if (slots != 3 && slots != 5 && slots != 6 && slots != kMrGrouped && CL * (slots > 8 ? slots - 10 : slots) > 32) {
     h->err = "set_block_config: too many slots for the column count";
     return R3MG_E_ARG;
   }

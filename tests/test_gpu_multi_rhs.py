@@ -229,8 +229,9 @@ def test_block_kernel_forms_on_coarse_levels(trio, fp32):
 
 @pytest.mark.parametrize("fp32", [False, True])
 def test_block_kernel_forms_on_the_fine_level(trio, fp32):
-    """Fine-level block kernels: window map in shared memory (2/4/8 entry slots) and the flat
-    row sweep on global column indices (12/14/18) give the oracle's product."""
+    """Fine-level block kernels: window map in shared memory (2/4/8 entry slots), the flat row
+    sweep on global column indices (12/14/18) and the groups of rows with equal column lists (20)
+    give the oracle's product."""
     P, params, H, Hm, Ho = trio
     Hx = Hm if fp32 else H
     m = 16
@@ -241,7 +242,7 @@ def test_block_kernel_forms_on_the_fine_level(trio, fp32):
     ref = (A @ X.T).T
     absA = abs(A)
     k = np.diff(A.indptr)
-    for slots in (2, 4, 8, 12, 14, 18):
+    for slots in (2, 4, 8, 12, 14, 18, 20):
         if not fp32 and slots in (8, 18):
             continue                                       # FP64, 16 columns: 8 lanes per row slice
         Hx.set_block_config(0, slots, fp32=fp32)
@@ -258,6 +259,35 @@ def test_block_kernel_forms_on_the_fine_level(trio, fp32):
     Xs = Xs.cpu().numpy()
     for c in range(4):
         assert np.linalg.norm(B[c] - P.scipy() @ Xs[c]) <= 1e-10 * np.linalg.norm(B[c])
+
+
+def test_grouped_fine_level_follows_value_updates(trio):
+    """The grouped fine level keeps its own entry-major copy of the values; after new matrix values
+    (here 2 A, which scales every product exactly) the block product uses them, and the block
+    solve with the grouped form still converges."""
+    P, params, H, Hm, Ho = trio
+    m = 16
+    rng = np.random.default_rng(77)
+    X = torch.tensor(rng.standard_normal((m, P.n)), device="cuda")
+    for Hx, fp32 in ((H, False), (Hm, True)):
+        Hx.vcycle_multi(torch.tensor(rng.standard_normal((m, P.n)), device="cuda"))
+        Hx.set_block_config(0, 20, fp32=fp32)
+        assert Hx.block_config(fp32=fp32)[0] == 20
+        Y1 = Hx.level_apply_multi(0, X, fp32=fp32)
+        try:
+            Hx.update_values(torch.tensor(2.0 * P.vals, device="cuda"))
+            Y2 = Hx.level_apply_multi(0, X, fp32=fp32)
+        finally:
+            Hx.update_values(torch.tensor(P.vals, device="cuda"))
+        assert torch.equal(Y2, 2.0 * Y1)
+        assert torch.equal(Hx.level_apply_multi(0, X, fp32=fp32), Y1)
+        B = _rhs(P, m, 44)                       # 16 columns: the grouped form stays configured
+        Xs, its, rel = Hx.pcg_multi(torch.tensor(B, device="cuda"), rtol=1e-10)
+        assert Hx.block_config(fp32=fp32)[0] == 20
+        Xs = Xs.cpu().numpy()
+        for c in range(m):
+            assert np.linalg.norm(B[c] - P.scipy() @ Xs[c]) <= 1e-10 * np.linalg.norm(B[c])
+        Hx.set_block_config(0, 4, fp32=fp32)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
