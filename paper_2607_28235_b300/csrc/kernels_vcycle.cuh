@@ -80,6 +80,34 @@ __global__ void k_restrict_coarse(const T* __restrict__ Pt, const T* __restrict_
                               (int64_t)gridDim.x * blockDim.x, nullptr, nullptr);
 }
 
+// The same restriction with one CTA per parent box: the threads take the (child, q) pairs, each
+// summing its child's b products, and threads q < b add the fan partials in child order.  Every
+// output's fan * b products then run on fan threads instead of one (the single-hierarchy V-cycle;
+// the batched loops keep the thread-per-output body above, which their persistent kernel shares).
+// Dynamic shared memory: fan * b values of T.
+template <typename T, class NX>
+__global__ void __launch_bounds__(256) k_restrict_coarse_box(const T* __restrict__ Pt, const T* __restrict__ r,
+                                                           int64_t nparent, int b, int fan, NX nx) {
+  extern __shared__ __align__(16) unsigned char rc_raw[];
+  T* part = reinterpret_cast<T*>(rc_raw);
+  for (int64_t B = blockIdx.x; B < nparent; B += gridDim.x) {
+    for (int it = threadIdx.x; it < fan * b; it += blockDim.x) {
+      const int ci = it / b, q = it - ci * b;
+      const int64_t c = B * fan + ci;
+      T s = T(0);
+      for (int qp = 0; qp < b; ++qp) s += Pt[(c * b + qp) * b + q] * r[c * b + qp];
+      part[it] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < b) {
+      T t = T(0);
+      for (int ci = 0; ci < fan; ++ci) t += part[ci * b + threadIdx.x];
+      nx(B * b + threadIdx.x, t);
+    }
+    __syncthreads();
+  }
+}
+
 // Level 1 -> fine: d0[k] = sum_q P0[k][q] (x1 + d1)[box(k)*b + q]   (d1 may be null).
 template <typename T>
 __device__ __forceinline__ void prolong_fine_body(const T* __restrict__ P0, const int32_t* __restrict__ box_of,

@@ -758,7 +758,8 @@ T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
     if (l == 0)
       k_restrict_fine<T, NextInit<T>><<<(int)std::min<int64_t>(C.nbox, 148 * 64), 256, 0, s>>>(Pmat<T>(h, 0), r, A.box_row, C.nbox, h->b, nx);
     else
-      k_restrict_coarse<T, NextInit<T>><<<grid_for(C.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), r, C.nbox, h->b, h->fan, nx);
+      k_restrict_coarse_box<T, NextInit<T>><<<(int)std::min<int64_t>(C.nbox, (int64_t)h->nsm * 8), 256,
+                                              sizeof(T) * h->fan * h->b, s>>>(Pmat<T>(h, l), r, C.nbox, h->b, h->fan, nx);
     CK(cudaGetLastError());
     ++nk;
   }
