@@ -36,8 +36,11 @@ __device__ __forceinline__ void restrict_fine_body(const T* __restrict__ P0, con
   for (int64_t B = blockIdx.x; B < nbox; B += gridDim.x) {
     if (skip_row(rprob1, act, B * b)) continue;   // uniform across the CTA
     T s = T(0);
-    if (j < per)
+    if (j < per) {
+      // unrolled so that several rows' loads are in flight at once (the sum keeps its order)
+#pragma unroll 4
       for (int64_t i = box_row[B] + j; i < box_row[B + 1]; i += per) s += P0[i * b + q] * r[i];
+    }
     part[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x < b) {
@@ -118,6 +121,7 @@ __device__ __forceinline__ void prolong_fine_body(const T* __restrict__ P0, cons
     if (skip_row(rprob, act, k)) continue;
     const int64_t B = box_of[k];
     T s = T(0);
+#pragma unroll 4
     for (int q = 0; q < b; ++q) {
       const T e = x1[B * b + q] + (d1 ? d1[B * b + q] : T(0));
       s += P0[k * b + q] * e;
