@@ -137,6 +137,37 @@ __global__ void k_prolong_fine(const T* __restrict__ P0, const int32_t* __restri
                        (int64_t)gridDim.x * blockDim.x, nullptr, nullptr);
 }
 
+// The same prolongation with each warp's 32 rows of P0 (32 x b contiguous values) first copied
+// to shared memory by coalesced loads, so that a row's b values are not gathered at a stride of
+// b values across the warp; each row's sum keeps its order.  The single-hierarchy V-cycle; the
+// batched loops keep the body above.  Dynamic shared memory: 32 x b values of T per warp.
+template <typename T>
+__global__ void k_prolong_fine_staged(const T* __restrict__ P0, const int32_t* __restrict__ box_of,
+                                      const T* __restrict__ x1, const T* __restrict__ d1, int64_t n, int b,
+                                      T* __restrict__ d0) {
+  extern __shared__ __align__(16) unsigned char pf_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  T* wp = reinterpret_cast<T*>(pf_raw) + (int64_t)warp * 32 * b;
+  for (int64_t base = ((int64_t)blockIdx.x * NW + warp) * 32; base < n; base += (int64_t)gridDim.x * NW * 32) {
+    const int rows = (int)(n - base < 32 ? n - base : 32);
+    const T* src = P0 + base * b;
+    for (int t = lane; t < rows * b; t += 32) wp[t] = src[t];
+    __syncwarp();
+    if (lane < rows) {
+      const int64_t k = base + lane;
+      const int64_t B = box_of[k];
+      T s = T(0);
+#pragma unroll 4
+      for (int q = 0; q < b; ++q) {
+        const T e = x1[B * b + q] + (d1 ? d1[B * b + q] : T(0));
+        s += wp[lane * b + q] * e;
+      }
+      d0[k] = s;
+    }
+    __syncwarp();
+  }
+}
+
 // Level l+1 -> l: d_l[c][q'] = sum_q Pt[c][q'][q] (x + d)_{l+1}[parent(c)][q].
 template <typename T>
 __device__ __forceinline__ void prolong_coarse_body(const T* __restrict__ Pt, const T* __restrict__ x1,

@@ -775,7 +775,12 @@ T* vcycle_body(r3mg_hierarchy* h, bool capturing = false) {
     const T* d1 = coarsest ? nullptr : (const T*)C.d[cur[l + 1]];
     T* d = (T*)A.d[cur[l]];
     if (l == 0)
-      k_prolong_fine<T><<<grid_for(h->n), 256, 0, s>>>(Pmat<T>(h, 0), h->box_of_tree, x1, d1, h->n, h->b, d);
+      {
+        const size_t sm = sizeof(T) * 4 * 32 * h->b;   // four warps of 32 rows
+        ensure_smem((const void*)k_prolong_fine_staged<T>, sm);
+        k_prolong_fine_staged<T><<<(int)std::max<int64_t>(1, std::min<int64_t>((h->n + 127) / 128, (int64_t)h->nsm * 16)),
+                                   128, sm, s>>>(Pmat<T>(h, 0), h->box_of_tree, x1, d1, h->n, h->b, d);
+      }
     else
       k_prolong_coarse<T><<<grid_for(A.nbox * h->b), 256, 0, s>>>(Pmat<T>(h, l), x1, d1, A.nbox, h->b, h->fan, d);
     CK(cudaGetLastError());
