@@ -491,6 +491,12 @@ def run_multi(args):
                      "traffic": _traffic(kname, "kernels_mrhs.cuh")},
         "kernel_time_share": {k: round(v["ms"] / (ms_block * args.steps), 4) for k, v in kinds.items()},
         "block_config": block_cfg,
+        # the tensor-core coarse forms (3, 5, 6) split FP32 operands into TF32 head and tail
+        "tensor_core_levels": [lev for lev, sl in enumerate(block_cfg["fp32"]) if sl in (3, 5, 6)],
+        "tensor_core_arithmetic": "levels listed in tensor_core_levels run the 3-pass TF32 head/tail product: "
+                                  "about 22 bits per product against FP32's 24 (parity bound (2k+64) 2^-24 "
+                                  "(|A||x|)_i); the FP64 flexible CG reaches the same residual in the same "
+                                  "iterations as with the exact FP32 forms",
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * m * P.n, "d2h_bytes_per_step": 8 * m * P.n},
         "gpu_launches": int(prof["kernel_launches"]),
         "clocks": clocks.summary(),
