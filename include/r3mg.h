@@ -544,8 +544,9 @@ r3mg_status r3mg_sampled_outer(r3mg_hierarchy* h, const double* lam_dev, const d
 
 /* Pin the level-operator kernel of level l and precision (fp32 = 1 needs an FP32 V-cycle):
  * form 0..7 as reported by r3mg_kernel_config, lanes in {4, 8, 16, 32} (also 2 on the FP64 fine
- * level's register forms; 1..8 resident CTAs per SM for form 7), threads per CTA in {128, 256} for the register forms (128 for forms 4 and 7) and
- * {256, 512, 1024} for the TMA form.  Replays a configuration chosen earlier (reproducible timing
+ * level's register forms; 1..8 resident CTAs per SM for form 7), threads per CTA in {128, 256}
+ * for the register forms, {96, 128} for form 4 (96: one thread per four-column group of a 27-row
+ * box's 380-column upper window), 128 for form 7 and {256, 512, 1024} for the TMA form.  Replays a configuration chosen earlier (reproducible timing
  * and profiling).  Errors: R3MG_E_ARG for an unsupported combination.  Synchronises. */
 r3mg_status r3mg_set_kernel_config(r3mg_hierarchy* h, int level, int fp32, int form, int lanes, int threads);
 

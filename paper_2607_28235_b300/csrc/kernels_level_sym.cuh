@@ -48,17 +48,17 @@ __device__ __forceinline__ float4 sym_ld(const float* p) {
 // memory) and the upper x window in `swin`: row partials reduced into ybuf, column sums of the
 // off-diagonal upper blocks into tbuf.  Shared by the streamed and the staged kernels, so both give
 // the same bits.
-template <bool SMEM, int WAVE = 8>
+template <bool SMEM, int WAVE = 8, int NT = kSymThreads>
 __device__ __forceinline__ void sym_box(const SymView& V, int64_t B, int W, int Wp, const float* swin,
                                         const float* base, float* __restrict__ ybuf, float* __restrict__ tbuf,
-                                        float (&ysum)[kSymThreads / 32][32]) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = kSymThreads / 32;
+                                        float (&ysum)[NT / 32][32]) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = NT / 32;
   const int b = V.b;
   float yp[kSymMaxB];
 #pragma unroll
   for (int q = 0; q < kSymMaxB; ++q) yp[q] = 0.f;
   const int64_t tp = V.tp_off[B];
-  for (int c4 = tid; 4 * c4 < Wp; c4 += kSymThreads) {
+  for (int c4 = tid; 4 * c4 < Wp; c4 += NT) {
     const float4 xw = *reinterpret_cast<const float4*>(swin + 4 * c4);
     float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -108,20 +108,23 @@ __device__ __forceinline__ void sym_box(const SymView& V, int64_t B, int W, int 
   }
 }
 
-// One CTA (128 threads) per box.  The box's upper window (x over the diagonal and upper
-// neighbour slots) is staged in shared memory; each thread owns 4 consecutive columns of the
-// box's upper rows (one 16-byte load per row, coalesced along the row), walks all b rows in
-// waves of WAVE loads in flight (8, or 4 for fewer registers and more resident CTAs), and keeps
+// One CTA (NT = 128 threads, or 96: an interior box of a 27-row level has 95 four-column groups,
+// so 96 threads leave none idle and let more CTAs reside) per box.  The box's upper window (x over
+// the diagonal and upper neighbour slots) is staged in shared memory; each thread owns 4
+// consecutive columns of the box's upper rows (one 16-byte load per row, coalesced along the
+// row), walks all b rows in waves of WAVE loads in flight (8, or 4 for fewer registers and more
+// resident CTAs), and keeps
 //   * the row partials y_q += A[q, cols] . x_win[cols] for every row q (registers), and
 //   * the column sums t_cols = sum_q A[q, cols] x_B[q] (A_BB'^T x_B for its upper slots).
 // The row partials are reduced across each warp by a halving exchange (31 shuffles leave lane q
 // with row q's warp sum) and across the 4 warps in a fixed order, so the result is deterministic.
-template <int WAVE>
-__global__ void __launch_bounds__(kSymThreads, WAVE == 4 ? 8 : 6) k_sym_block(SymView V, const float* __restrict__ xin,
+template <int WAVE, int NT = kSymThreads>
+__global__ void __launch_bounds__(NT, (WAVE == 4 ? 8 : 6) * kSymThreads / NT) k_sym_block(SymView V,
+                                                          const float* __restrict__ xin,
                                                           float* __restrict__ ybuf, float* __restrict__ tbuf) {
   extern __shared__ __align__(16) float swin[];
-  __shared__ float ysum[kSymThreads / 32][32];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = kSymThreads / 32;
+  __shared__ float ysum[NT / 32][32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NW = NT / 32;
   const int b = V.b;
   for (int64_t B = blockIdx.x; B < V.nbox; B += gridDim.x) {
     const int64_t q0 = V.nbr_ptr[B];
@@ -131,10 +134,10 @@ __global__ void __launch_bounds__(kSymThreads, WAVE == 4 ? 8 : 6) k_sym_block(Sy
       const int64_t src = V.nbr[q0 + d + sI] * b;
       for (int t = lane; t < b; t += 32) cp_async_elem(swin + sI * b + t, xin + src + t);
     }
-    for (int t = W + tid; t < Wp; t += kSymThreads) swin[t] = 0.f;
+    for (int t = W + tid; t < Wp; t += NT) swin[t] = 0.f;
     cp_async_wait_all();
     __syncthreads();
-    sym_box<false, WAVE>(V, B, W, Wp, swin, V.vals + V.up_base[B], ybuf, tbuf, ysum);
+    sym_box<false, WAVE, NT>(V, B, W, Wp, swin, V.vals + V.up_base[B], ybuf, tbuf, ysum);
     __syncthreads();   // the window and ysum are free for the next box
   }
 }

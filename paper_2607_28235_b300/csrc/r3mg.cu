@@ -628,11 +628,13 @@ void sym_step(r3mg_hierarchy* h, const Level& A, const float* d, SymCheb ep) {
     k_sym_block_staged<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(
         A.sym, d, A.sym_y, A.sym_t, cap, c.err, c.wait, c.withhold);
   } else {
-    // form 4: the lanes field selects the load wave (4 rows, else 8)
+    // form 4: the lanes field selects the load wave (4 rows, else 8), the threads field 96 or 128
     const size_t sm = sizeof(float) * (size_t)A.sym.win_max;
-    auto kern = A.conf[1].G == 4 ? k_sym_block<4> : k_sym_block<8>;
+    const bool t96 = A.conf[1].nt == 96;
+    auto kern = A.conf[1].G == 4 ? (t96 ? k_sym_block<4, 96> : k_sym_block<4>)
+                                 : (t96 ? k_sym_block<8, 96> : k_sym_block<8>);
     ensure_smem((const void*)kern, sm);
-    kern<<<(int)std::max<int64_t>(1, A.nbox), kSymThreads, sm, h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
+    kern<<<(int)std::max<int64_t>(1, A.nbox), t96 ? 96 : kSymThreads, sm, h->stream>>>(A.sym, d, A.sym_y, A.sym_t);
   }
   k_sym_finish<<<grid_for(A.n), 256, 0, h->stream>>>(A.sym, A.sym_y, A.sym_t, ep);
   CK(cudaGetLastError());
@@ -975,6 +977,8 @@ void autotune_level(r3mg_hierarchy* h, Level& A, bool product) {
     if (sizeof(T) == 4 && A.sym_ok && G == 16 && !product) {
       cand.push_back({4, G, 128, 0.f, 0});
       cand.push_back({4, 4, 128, 0.f, 0});   // symmetric form with 4-row load waves
+      cand.push_back({4, G, 96, 0.f, 0});    // ... with 96 threads (no idle column group at b = 27)
+      cand.push_back({4, 4, 96, 0.f, 0});
       for (int cps : {2, 3, 4, 5})   // staged form: the lanes field holds the resident CTAs per SM
         if (sym_stage_cap(A, cps) > 0) cand.push_back({7, cps, 128, 0.f, 0});
     }
@@ -3721,8 +3725,9 @@ r3mg_status r3mg_set_kernel_config2(r3mg_hierarchy* h, int level, int fp32, int 
   }
   const bool two = lanes == 2 && level == 0 && !fp32 && (form == 0 || form == 2 || form == 3 || form == 5 || form == 6);
   if (!h || level < 0 || level >= h->L || form < 0 || form > 6 || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && !two) ||
-      (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || (form == 1 && threads == 128)) {
-    if (h) h->err = "set_kernel_config: invalid level, form (0..7), lanes (4,8,16,32; 2 on the FP64 fine level's register forms; 1..8 for form 7) or threads (128 register forms only, 256, 512, 1024)";
+      (threads != 128 && threads != 256 && threads != 512 && threads != 1024 && !(threads == 96 && form == 4)) ||
+      (form == 1 && threads == 128)) {
+    if (h) h->err = "set_kernel_config: invalid level, form (0..7), lanes (4,8,16,32; 2 on the FP64 fine level's register forms; 1..8 for form 7) or threads (128 register forms only, 256, 512, 1024; 96 or 128 for form 4)";
     return R3MG_E_ARG;
   }
   Level& A = h->lv[level];
@@ -3750,7 +3755,7 @@ r3mg_status r3mg_kernel_config(const r3mg_hierarchy* h, int level, int fp32, int
                        ? c.form
                        : 0);
   if (lanes) *lanes = c.G;
-  if (threads) *threads = tma ? c.nt : (c.nt == 128 ? 128 : 256);
+  if (threads) *threads = tma ? c.nt : (c.nt == 128 ? 128 : (c.nt == 96 && c.form == 4) ? 96 : 256);
   if (tuned_ms) *tuned_ms = c.ms;
   return R3MG_OK;
 }

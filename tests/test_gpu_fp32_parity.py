@@ -124,10 +124,15 @@ def test_fp32_cheb_step_bounds(case, form):
     if not _pin_form(H, form, range(L - 1)):
         H.close()
         pytest.skip(f"{form} cannot host this case's windows")
+    _cheb_step_checks(H, Ho, range(L - 1), form)
+    H.close()
+
+
+def _cheb_step_checks(H, Ho, levels, form):
     rng = np.random.default_rng(12)
     a, c = 0.37, 0.71
     a32, c32 = float(np.float32(a)), float(np.float32(c))
-    for lev in range(L - 1):
+    for lev in levels:
         A = Ho.A[lev]
         n = A.shape[0]
         x, r, d = (rng.standard_normal(n).astype(np.float32).astype(np.float64) for _ in range(3))
@@ -142,6 +147,25 @@ def test_fp32_cheb_step_bounds(case, form):
         dinv32 = (1.0 / A.diagonal()).astype(np.float32).astype(np.float64)
         exact = a32 * d + c32 * dinv32 * ro
         assert np.all(np.abs(do - exact) <= 5 * U32 * (np.abs(a32 * d) + np.abs(c32 * dinv32 * ro))), (lev, form)
+
+
+@pytest.mark.parametrize("lanes", [16, 4])   # 8-row and 4-row load waves
+def test_fp32_cheb_step_bounds_symmetric_96_threads(case, lanes):
+    """The symmetric form on 96-thread CTAs (one thread per four-column group of a 27-row box's
+    upper window) keeps the FP32 Chebyshev-step bounds on every coarse level."""
+    P, params, Ho = case
+    H = _hier(P, params)
+    L = params["levels"]
+    cfg = H.kernel_config()
+    for lev in range(1, L - 1):
+        cfg[lev]["f32"] = {"form": "symmetric_block", "lanes": lanes, "threads": 96}
+    try:
+        H.set_kernel_config(cfg[:-1])
+    except RuntimeError:
+        H.close()
+        pytest.skip("no symmetric coarse level")
+    assert all(H.kernel_config()[lev]["f32"]["threads"] == 96 for lev in range(1, L - 1))
+    _cheb_step_checks(H, Ho, range(1, L - 1), "symmetric_block/96")
     H.close()
 
 
