@@ -828,6 +828,7 @@ def run_ours(args):
         "fp64": {"ms": ms_fp64, "iterations": its_d[-1], "relres_check": chk_d,
                  "top_kernel": top_d, "top_kernel_avg_ms": avg_d,
                  "top_kernel_achieved_gbs": td["bytes_per_launch"] / (avg_d * 1e-3) / 1e9,
+                 "top_kernel_frac_of_fp64_bound": fp64_roof["frac"],
                  "roofline": fp64_roof,
                  "kernel_config": [row["f64"] for row in Hd.kernel_config()],
                  "kernel_ms": {k: v["ms"] / max(v["launches"], 1) for k, v in kinds_d.items()}},
