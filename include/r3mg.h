@@ -91,6 +91,22 @@ r3mg_status r3mg_partition(int64_t n, int dim, const double* coords_host, int le
                            int64_t* perm_out, int64_t* leaf_offsets_out, int* depth_out);
 
 /*
+ * The row groups of the block kernels' grouped fine level (block form 20; rows whose stored
+ * column lists are equal share each gathered slice of the right-hand sides), computed on the
+ * host from a windowed per-row layout.  Needs no GPU.  Within each box, rows with equal index
+ * lists form runs; a run, in increasing row order, is cut into groups of 8 rows, then 4, 2 and 1.
+ *   row_ptr (n+1, host): row r's window indices are idx[row_ptr[r] .. row_ptr[r+1]), row_ptr[0] = 0.
+ *   box_row (nbox+1, host): box B holds rows box_row[B] .. box_row[B+1]-1 (0 to n, non-decreasing).
+ *   idx (host, row_ptr[n] entries; may be NULL when that is 0): 16-bit window indices.
+ *   counts_out (4): the number of groups of 8, 4, 2 and 1 rows.
+ *   rows_out (n, int32): every row once, the groups of 8 first, then of 4, 2 and 1; within a
+ *     size, boxes in order; within a group, increasing rows.
+ * Errors: R3MG_E_ARG (null pointer, n < 0 or >= 2^31, nbox < 1, bad offsets), R3MG_E_OOM.
+ */
+r3mg_status r3mg_group_rows(int64_t n, const int64_t* row_ptr, int64_t nbox, const int64_t* box_row,
+                            const uint16_t* idx, int64_t* counts_out, int32_t* rows_out);
+
+/*
  * Build the hierarchy for the free-DoF system A (CSR, host memory) whose
  * support points are coords_host (n x dim, host).  Performs the partition
  * and the symbolic analysis on the host, then on the device: the P values

@@ -15,7 +15,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("Hierarchy", "BatchHierarchy", "partition", "partition_cells", "default_params", "measure_fp64_rates",
+    if name in ("Hierarchy", "BatchHierarchy", "partition", "partition_cells", "group_rows", "default_params", "measure_fp64_rates",
                 "wait_selftest"):
         from . import solver
         return getattr(solver, name)
@@ -25,4 +25,4 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["build", "Hierarchy", "BatchHierarchy", "partition", "partition_cells", "default_params", "R3MGSolve", "solve", "R3MGError", "SO_PATH"]
+__all__ = ["build", "Hierarchy", "BatchHierarchy", "partition", "partition_cells", "group_rows", "default_params", "R3MGSolve", "solve", "R3MGError", "SO_PATH"]

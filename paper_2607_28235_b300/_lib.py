@@ -78,6 +78,7 @@ def lib():
         "r3mg_setup": (ip, [i64, i32, vp, vp, vp, vp, P(_Params), vp, P(vp)]),
         "r3mg_setup_cells": (ip, [i64, i32, vp, vp, vp, vp, i64, vp, vp, P(_Params), vp, P(vp)]),
         "r3mg_partition_cells": (ip, [i64, i32, vp, i64, vp, vp, i32, i32, vp, vp, vp, vp, P(ctypes.c_int)]),
+        "r3mg_group_rows": (ip, [i64, vp, i64, vp, vp, vp, vp]),
         "r3mg_update_values": (ip, [vp, vp, vp]),
         "r3mg_vcycle": (ip, [vp, vp, vp, vp]),
         "r3mg_pcg": (ip, [vp, vp, vp, dbl, i32, P(ctypes.c_int), P(ctypes.c_double), vp]),

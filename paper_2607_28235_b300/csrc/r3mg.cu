@@ -2323,21 +2323,21 @@ void mr_build_gidx(r3mg_hierarchy* h) {
 constexpr int kMrGrouped = 20;          // block-config code of the grouped fine level
 constexpr int kMrGroupR[4] = {8, 4, 2, 1};
 
-void mr_build_groups(r3mg_hierarchy* h) {
-  if (h->mrg_built) return;
-  mr_build_gidx(h);
-  const Level& F = h->lv[0];
-  const LevelView<double> v = view<double>(F);
-  const int64_t n = F.n, nbox = F.nbox;
-  std::vector<int64_t> rp(n + 1), br(nbox + 1);
-  std::vector<uint16_t> ix(F.stored);
-  CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemcpy(rp.data(), v.row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(br.data(), v.box_row, sizeof(int64_t) * (nbox + 1), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(ix.data(), v.idx, sizeof(uint16_t) * F.stored, cudaMemcpyDeviceToHost));
+// Host grouping of a windowed per-row layout (rows of box B: box_row[B] .. box_row[B+1]-1, row
+// r's window indices idx[row_ptr[r] .. row_ptr[r+1])): per box, rows keyed by (length, hash),
+// sorted by (length, hash, row); each run of rows with equal lists, in increasing row order, is
+// cut into groups of 8, then 4, 2 and 1.  Output class-major (8, 4, 2, 1), boxes in order within a
+// class: the rows group by group, each group's entry count, and per class its group count, first
+// group and first row slot.
+struct RowGroups {
+  int64_t ng[4] = {0, 0, 0, 0}, g0[4] = {0, 0, 0, 0}, r0[4] = {0, 0, 0, 0};
+  std::vector<int32_t> rows;
+  std::vector<int64_t> len;
+};
+
+RowGroups group_rows_host(const int64_t* rp, int64_t nbox, const int64_t* br, const uint16_t* ix) {
   auto same = [&](int64_t a, int64_t b) {
-    return rp[a + 1] - rp[a] == rp[b + 1] - rp[b] &&
-           std::equal(ix.begin() + rp[a], ix.begin() + rp[a + 1], ix.begin() + rp[b]);
+    return rp[a + 1] - rp[a] == rp[b + 1] - rp[b] && std::equal(ix + rp[a], ix + rp[a + 1], ix + rp[b]);
   };
   // per box: its rows group by group, class by class, and its group count per class
   std::vector<std::vector<int32_t>> order(nbox);
@@ -2381,18 +2381,18 @@ void mr_build_groups(r3mg_hierarchy* h) {
     }
   }
   // class-major numbering, boxes in order within a class
+  RowGroups out;
   std::vector<int64_t> boff(nbox * 4);
   int64_t g = 0, rows = 0;
   for (int c = 0; c < 4; ++c) {
-    h->mrg_g0[c] = g;
-    h->mrg_r0[c] = rows;
+    out.g0[c] = g;
+    out.r0[c] = rows;
     for (int64_t B = 0; B < nbox; ++B) { boff[B * 4 + c] = g; g += cnt[B * 4 + c]; }
-    h->mrg_ng[c] = g - h->mrg_g0[c];
-    rows += h->mrg_ng[c] * kMrGroupR[c];
+    out.ng[c] = g - out.g0[c];
+    rows += out.ng[c] * kMrGroupR[c];
   }
-  const int64_t NG = g;
-  std::vector<int32_t> grows(rows);
-  std::vector<int64_t> glen(NG);
+  out.rows.assign(rows, 0);
+  out.len.assign(g, 0);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t B = 0; B < nbox; ++B) {
     size_t p = 0;
@@ -2400,11 +2400,29 @@ void mr_build_groups(r3mg_hierarchy* h) {
       const int R = kMrGroupR[c];
       for (int64_t q = 0; q < cnt[B * 4 + c]; ++q, p += R) {
         const int64_t gg = boff[B * 4 + c] + q;
-        for (int t = 0; t < R; ++t) grows[h->mrg_r0[c] + (gg - h->mrg_g0[c]) * R + t] = order[B][p + t];
-        glen[gg] = rp[order[B][p] + 1] - rp[order[B][p]];
+        for (int t = 0; t < R; ++t) out.rows[out.r0[c] + (gg - out.g0[c]) * R + t] = order[B][p + t];
+        out.len[gg] = rp[order[B][p] + 1] - rp[order[B][p]];
       }
     }
   }
+  return out;
+}
+
+void mr_build_groups(r3mg_hierarchy* h) {
+  if (h->mrg_built) return;
+  mr_build_gidx(h);
+  const Level& F = h->lv[0];
+  const LevelView<double> v = view<double>(F);
+  const int64_t n = F.n, nbox = F.nbox;
+  std::vector<int64_t> rp(n + 1), br(nbox + 1);
+  std::vector<uint16_t> ix(F.stored);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(rp.data(), v.row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(br.data(), v.box_row, sizeof(int64_t) * (nbox + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ix.data(), v.idx, sizeof(uint16_t) * F.stored, cudaMemcpyDeviceToHost));
+  const RowGroups grp = group_rows_host(rp.data(), nbox, br.data(), ix.data());
+  for (int c = 0; c < 4; ++c) { h->mrg_ng[c] = grp.ng[c]; h->mrg_g0[c] = grp.g0[c]; h->mrg_r0[c] = grp.r0[c]; }
+  const int64_t NG = (int64_t)grp.len.size(), rows = (int64_t)grp.rows.size();
   // entry offsets, and value offsets with every class starting on a 16-value boundary (the
   // kernels read a group entry's R values with 16-byte loads)
   std::vector<int64_t> geoff(NG + 1), gvoff(NG + 1);
@@ -2412,10 +2430,10 @@ void mr_build_groups(r3mg_hierarchy* h) {
   int64_t ev = 0;
   for (int c = 0; c < 4; ++c) {
     ev = (ev + 15) & ~(int64_t)15;
-    for (int64_t q = h->mrg_g0[c]; q < h->mrg_g0[c] + h->mrg_ng[c]; ++q) {
+    for (int64_t q = grp.g0[c]; q < grp.g0[c] + grp.ng[c]; ++q) {
       gvoff[q] = ev;
-      ev += glen[q] * kMrGroupR[c];
-      geoff[q + 1] = geoff[q] + glen[q];
+      ev += grp.len[q] * kMrGroupR[c];
+      geoff[q + 1] = geoff[q] + grp.len[q];
     }
   }
   gvoff[NG] = ev;
@@ -2425,7 +2443,7 @@ void mr_build_groups(r3mg_hierarchy* h) {
   h->mrg_col = dalloc<int32_t>(h, std::max<int64_t>(1, geoff[NG]));
   CK(cudaMemcpy(h->mrg_geoff, geoff.data(), sizeof(int64_t) * (NG + 1), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->mrg_gvoff, gvoff.data(), sizeof(int64_t) * (NG + 1), cudaMemcpyHostToDevice));
-  if (rows > 0) CK(cudaMemcpy(h->mrg_rows, grows.data(), sizeof(int32_t) * rows, cudaMemcpyHostToDevice));
+  if (rows > 0) CK(cudaMemcpy(h->mrg_rows, grp.rows.data(), sizeof(int32_t) * rows, cudaMemcpyHostToDevice));
   h->mrg_built = true;
 }
 
@@ -3146,6 +3164,26 @@ r3mg_status r3mg_partition(int64_t n, int dim, const double* coords_host, int le
   std::memcpy(perm_out, P.perm.data(), sizeof(int64_t) * n);
   if (leaf_offsets_out) std::memcpy(leaf_offsets_out, P.leaf_off.data(), sizeof(int64_t) * P.leaf_off.size());
   if (depth_out) *depth_out = P.depth;
+  return R3MG_OK;
+}
+
+r3mg_status r3mg_group_rows(int64_t n, const int64_t* row_ptr, int64_t nbox, const int64_t* box_row,
+                            const uint16_t* idx, int64_t* counts_out, int32_t* rows_out) {
+  if (!row_ptr || !box_row || !counts_out || (n > 0 && !rows_out)) { g_last_error = "group_rows: null pointer"; return R3MG_E_ARG; }
+  if (n < 0 || nbox < 1 || n > INT32_MAX || row_ptr[0] != 0 || box_row[0] != 0 || box_row[nbox] != n) {
+    g_last_error = "group_rows: need n >= 0 rows (below 2^31), nbox >= 1, row_ptr[0] = 0 and box_row from 0 to n";
+    return R3MG_E_ARG;
+  }
+  for (int64_t B = 0; B < nbox; ++B)
+    if (box_row[B + 1] < box_row[B]) { g_last_error = "group_rows: box_row must not decrease"; return R3MG_E_ARG; }
+  for (int64_t r = 0; r < n; ++r)
+    if (row_ptr[r + 1] < row_ptr[r]) { g_last_error = "group_rows: row_ptr must not decrease"; return R3MG_E_ARG; }
+  if (row_ptr[n] > 0 && !idx) { g_last_error = "group_rows: null pointer"; return R3MG_E_ARG; }
+  try {
+    const RowGroups grp = group_rows_host(row_ptr, nbox, box_row, idx);
+    for (int c = 0; c < 4; ++c) counts_out[c] = grp.ng[c];
+    if (n > 0) std::memcpy(rows_out, grp.rows.data(), sizeof(int32_t) * n);
+  } catch (std::bad_alloc&) { g_last_error = "host allocation failed"; return R3MG_E_OOM; }
   return R3MG_OK;
 }
 

@@ -73,6 +73,19 @@ def partition_cells(coords: np.ndarray, cell_ptr: np.ndarray, cell_pts: np.ndarr
     return perm, off[:nb + 1].copy(), lo[:nb * d].reshape(nb, d).copy(), hi[:nb * d].reshape(nb, d).copy(), depth.value
 
 
+def group_rows(row_ptr: np.ndarray, box_row: np.ndarray, idx: np.ndarray):
+    """Host-only row groups of the grouped block form: (counts of groups of 8, 4, 2, 1 rows, rows in group order)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    br = np.ascontiguousarray(box_row, dtype=np.int64)
+    ix = np.ascontiguousarray(idx, dtype=np.uint16)
+    n = len(rp) - 1
+    counts = np.zeros(4, np.int64)
+    rows = np.empty(max(n, 1), np.int32)
+    _check(lib().r3mg_group_rows(n, _p(rp), len(br) - 1, _p(br), _p(ix) if len(ix) else None, _p(counts),
+                                 _p(rows)))
+    return counts, rows[:n].copy()
+
+
 def wait_selftest(limit_cycles: int) -> tuple:
     """(status, expired): a one-CTA kernel whose mbarrier wait can only run out (status 10 = E_TIMEOUT)."""
     e = ctypes.c_int(0)

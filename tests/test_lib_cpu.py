@@ -136,3 +136,76 @@ def test_null_handles_and_pointers_are_argument_errors(lib):
     assert lib.r3mg_set_block_config(null, 0, 1, 4) == E_ARG
     assert lib.r3mg_level0_apply_noalloc(null, one, one, null) == E_ARG
     lib.r3mg_destroy(null)            # a no-op
+
+
+def _expected_groups(rp, br, ix):
+    """Brute force of the grouping rule: per box, rows with equal index lists in increasing row
+    order, cut into groups of 8, then 4, 2 and 1; per size, boxes in order."""
+    per_size = {8: [], 4: [], 2: [], 1: []}
+    for B in range(len(br) - 1):
+        runs = {}
+        for r in range(br[B], br[B + 1]):
+            runs.setdefault(tuple(ix[rp[r]:rp[r + 1]].tolist()), []).append(r)
+        box = {8: [], 4: [], 2: [], 1: []}
+        for run in runs.values():
+            i = 0
+            for R_ in (8, 4, 2, 1):
+                while len(run) - i >= R_:
+                    box[R_].append(tuple(run[i:i + R_]))
+                    i += R_
+        for R_ in (8, 4, 2, 1):
+            per_size[R_].append(sorted(box[R_]))
+    return per_size
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_group_rows_vs_brute_force(lib, seed):
+    """Host grouping of the block kernels' grouped fine level: every row once, each group one index
+    list inside one box, sizes 8/4/2/1 cut in increasing row order, sizes then boxes in order."""
+    rng = np.random.default_rng(seed)
+    nbox = 5
+    lists, box_row = [], [0]
+    for B in range(nbox):
+        base = [rng.integers(0, 200, size=4 * rng.integers(1, 6)).astype(np.uint16) for _ in range(4)]
+        # a box's rows: repeats of a few lists (runs of 1 .. 19 rows), interleaved, plus distinct rows
+        # of equal length (same key length, different contents)
+        rows = []
+        for j, lst in enumerate(base):
+            rows += [lst] * int(rng.integers(1, 20))
+        rows += [np.concatenate([base[0][:-1], [np.uint16(199 - k)]]) for k in range(3)]
+        order = rng.permutation(len(rows))
+        lists += [rows[k] for k in order]
+        box_row.append(len(lists))
+    rp = np.zeros(len(lists) + 1, np.int64)
+    rp[1:] = np.cumsum([len(x) for x in lists])
+    ix = np.concatenate(lists).astype(np.uint16)
+    br = np.array(box_row, np.int64)
+    counts, rows = R.group_rows(rp, br, ix)
+    assert sorted(rows.tolist()) == list(range(len(lists)))
+    want = _expected_groups(rp, br, ix)
+    pos = 0
+    for c, R_ in enumerate((8, 4, 2, 1)):
+        assert counts[c] == sum(len(b) for b in want[R_])
+        got = [tuple(rows[pos + k * R_: pos + (k + 1) * R_].tolist()) for k in range(int(counts[c]))]
+        pos += int(counts[c]) * R_
+        # boxes in order within a size, and within a box the expected set of groups
+        k = 0
+        for B, groups in enumerate(want[R_]):
+            mine = sorted(got[k:k + len(groups)])
+            assert mine == groups, (R_, B)
+            for g in mine:
+                assert all(br[B] <= r < br[B + 1] for r in g)
+            k += len(groups)
+
+
+def test_group_rows_errors(lib):
+    rp = np.array([0, 4, 8], np.int64)
+    ix = np.zeros(8, np.uint16)
+    with pytest.raises(R.R3MGError) as e:
+        R.group_rows(rp, np.array([0, 1], np.int64), ix)        # boxes cover 1 of 2 rows
+    assert e.value.name == "E_ARG"
+    with pytest.raises(R.R3MGError) as e:
+        R.group_rows(np.array([0, 4, 2], np.int64), np.array([0, 2], np.int64), ix)   # decreasing row_ptr
+    assert e.value.name == "E_ARG"
+    counts, rows = R.group_rows(rp, np.array([0, 2], np.int64), ix)   # two equal rows: one group of 2
+    assert counts.tolist() == [0, 0, 1, 0] and rows.tolist() == [0, 1]
